@@ -1,0 +1,468 @@
+"""Pins for the oracle's time step: closed forms, exact invariants, brute force.
+
+Each test checks the FP64 oracle against a fact fixed by the paper or by the
+mathematics (never against the oracle itself), chosen so that a dropped term,
+a wrong sign or a swapped operand in the oracle fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from exact import binned_profile, manning_decay, ritter, stoker, stoker_star
+from paper_2307_16758_gb300 import workloads as W
+
+G = 9.81
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_dam_break.txt")
+
+
+def _golden():
+    vals = {}
+    for line in open(GOLDEN):
+        line = line.split("#")[0].split()
+        if line:
+            vals[line[0]] = [float(x) for x in line[1:]]
+    return vals
+
+
+def _mesh(w, cut=True):
+    return oracle.Mesh(w.nodes, w.tris, w.bnd_edges, w.bnd_tag, w.cut_edges if cut else None)
+
+
+def _l1(m, q, qex):
+    a = m.arrays["area"]
+    return float((a * np.abs(q - qex)).sum() / a.sum())
+
+
+# --------------------------------------------------------------------------
+# Sec. 5.3: the paper's worked example, against the closed form
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("scheme", ["hllc", "muscl", "waf"])
+def test_paper_dam_break_converges_to_closed_form(scheme):
+    g = _golden()
+    errs = []
+    for key in ("grid_coarse", "grid_fine"):
+        nx, ny = (int(v) for v in g[key])
+        w = W.dam_break_1d(nx, ny, g["domain_x1"][0], g["domain_y1"][0], g["h_left"][0],
+                           g["h_right"][0], x_dam=g["x_dam"][0])
+        assert w.n_cells == int(g["cells_coarse" if key == "grid_coarse" else "cells_fine"][0])
+        m = _mesh(w)
+        t_end, steps = g["t_end"][0], 1000
+        dt = np.full(steps, t_end / steps)
+        h, hu, hv, _, d = oracle.run(m, oracle.opts(scheme), w.z, w.nman, w.h, w.hu, w.hv, steps, dt=dt)
+        assert math.isclose(d["t"], t_end, rel_tol=1e-12)
+        hex_, uex = stoker(m.arrays["cx"], t_end, g["x_dam"][0], g["h_left"][0], g["h_right"][0])
+        errs.append(_l1(m, h, hex_))
+    assert errs[1] < errs[0]
+    assert errs[0] < 0.02
+
+
+def test_second_order_beats_first_order():
+    """Sec. 5.3: WAF and MUSCL are closer to the closed form than HLLC."""
+    w = W.dam_break_1d(95, 13, 10.0, 1.0, 1.0, 0.5, x_dam=5.0)
+    m = _mesh(w)
+    dt = np.full(1000, 1.0 / 1000)
+    err = {}
+    for s in ("hllc", "muscl", "waf"):
+        h, *_ = oracle.run(m, oracle.opts(s), w.z, w.nman, w.h, w.hu, w.hv, 1000, dt=dt)
+        err[s] = _l1(m, h, stoker(m.arrays["cx"], 1.0, 5.0, 1.0, 0.5)[0])
+    assert err["muscl"] < 0.7 * err["hllc"]
+    assert err["waf"] < 0.7 * err["hllc"]
+
+
+def test_stoker_strip_2000_cells_cfl():
+    """100 m x 10 m strip, 2000 cells, CFL 0.9, 200 steps (ends before any wave hits a wall)."""
+    w = W.dam_break_1d()
+    m = _mesh(w)
+    h, hu, hv, dts, d = oracle.run(m, oracle.opts("hllc"), w.z, w.nman, w.h, w.hu, w.hv, 200)
+    t = d["t"]
+    hm, um, s = stoker_star(1.0, 0.5)
+    assert 50 + s * t < 100 and 50 - math.sqrt(G) * t > 0
+    cx = m.arrays["cx"]
+    hex_, uex = stoker(cx, t, 50.0, 1.0, 0.5)
+    assert _l1(m, h, hex_) < 0.01
+    # the plateau between fan and shock carries the closed-form middle state
+    plateau = (cx > 50 + (um - math.sqrt(G * hm)) * t + 8) & (cx < 50 + s * t - 8)
+    assert plateau.sum() > 100
+    assert abs(np.median(h[plateau]) - hm) < 2e-3
+    assert abs(np.median(hu[plateau] / h[plateau]) - um) < 5e-3
+    # mass: walls only, no clipping on a wet bed
+    assert abs(m.mass(h) - m.mass(w.h)) <= 1e-13 * m.mass(w.h)
+
+
+@pytest.mark.parametrize("scheme,time_scheme", [("hllc", "euler"), ("waf", "euler"), ("muscl", "heun")])
+def test_ritter_dry_bed_front(scheme, time_scheme):
+    """Dry-bed dam break: the 1 mm contour follows the closed form (front speed 2 sqrt(g h_L))."""
+    errs, ferr = [], []
+    for nx, ny in ((200, 2), (400, 4), (800, 8)):
+        w = W.dam_break_1d(nx, ny, 100.0, ny * 100.0 / nx, 1.0, 0.0)
+        m = _mesh(w)
+        h, hu, hv, dts, d = oracle.run(m, oracle.opts(scheme, time_scheme=time_scheme), w.z, w.nman,
+                                       w.h, w.hu, w.hv, int(0.9 * nx))
+        t = d["t"]
+        cx = m.arrays["cx"]
+        hex_ = ritter(cx, t, 50.0, 1.0)
+        front, exact_front = cx[h > 1e-3].max(), cx[hex_ > 1e-3].max()
+        ferr.append(abs(front - exact_front) / (exact_front - 50.0))
+        errs.append(_l1(m, h, hex_))
+        assert abs(m.mass(h) - m.mass(w.h) - d["clipped"]) <= 1e-12 * m.mass(w.h)
+        assert dts.min() > 0.3 * dts.max()          # no velocity spike collapses the time step
+    assert errs[2] < errs[1] < errs[0]
+    assert ferr[2] < 0.1
+
+
+def test_muscl_euler_dry_front_is_the_fragile_case():
+    """Record of a property, not a target: forward Euler with MUSCL at CFL 0.9
+    lets near-dry cells pick up large velocities at a dry front (the time step
+    collapses), while Heun at the same CFL does not."""
+    w = W.dam_break_1d(800, 8, 100.0, 1.0, 1.0, 0.0)
+    m = _mesh(w)
+    _, _, _, dts_e, _ = oracle.run(m, oracle.opts("muscl"), w.z, w.nman, w.h, w.hu, w.hv, 400)
+    _, _, _, dts_h, _ = oracle.run(m, oracle.opts("muscl", time_scheme="heun"), w.z, w.nman,
+                                   w.h, w.hu, w.hv, 400)
+    assert dts_e.min() < 0.1 * dts_e.max()
+    assert dts_h.min() > 0.4 * dts_h.max()
+
+
+# --------------------------------------------------------------------------
+# Well-balancing, conservation, symmetry, invariance
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("scheme", ["hllc", "muscl", "waf"])
+@pytest.mark.parametrize("bc", ["wall", "level", "open"])
+def test_lake_at_rest_bitwise(scheme, bc):
+    """Lake at rest over Gaussian bathymetry with ~30 % dry cells stays exactly at rest."""
+    w = W.partial_dam_break(nx=40, ny=20, spacing=1.0, n_gauss=20, breach=False, seed=9)
+    assert 0.2 < (w.h == 0).mean() < 0.4
+    kind = {"wall": W.WALL, "level": W.LEVEL, "open": W.OPEN}[bc]
+    w.bnd_tag = np.full(len(w.bnd_edges), W.tag(kind), np.int32)
+    m = _mesh(w, cut=False)
+    h, hu, hv, dts, d = oracle.run(m, oracle.opts(scheme), w.z, w.nman, w.h, w.hu, w.hv, 300,
+                                   level=[2.0])
+    assert np.array_equal(h, w.h)
+    assert not hu.any() and not hv.any()
+
+
+@pytest.mark.parametrize("scheme", ["hllc", "muscl", "waf"])
+def test_mass_conserved_with_walls(scheme):
+    w = W.partial_dam_break(nx=40, ny=20, spacing=1.0, n_gauss=20, seed=9)
+    m = _mesh(w)
+    h, hu, hv, dts, d = oracle.run(m, oracle.opts(scheme), w.z, w.nman, w.h, w.hu, w.hv, 300)
+    m0 = m.mass(w.h)
+    assert abs(m.mass(h) - m0 - d["clipped"]) <= 1e-13 * m0
+    assert d["boundary_in"] == 0.0
+    assert (h >= 0).all()
+    assert np.abs(h - w.h).max() > 0.1          # the breach did release the upstream water
+
+
+def test_inflow_adds_exactly_q_times_t():
+    """Inflow boundary (Sec. 5.1): the only mass source is Q per unit time."""
+    w = W.river(nx=80, ny=30, seed=4, q_in=500.0)
+    w.bnd_tag = np.where((w.bnd_tag & 3) == W.LEVEL, W.tag(W.WALL), w.bnd_tag).astype(np.int32)
+    m = _mesh(w)
+    h, hu, hv, dts, d = oracle.run(m, oracle.opts("muscl"), w.z, w.nman, w.h, w.hu, w.hv, 200,
+                                   q_in=w.q_in, level=w.level)
+    added = m.mass(h) - m.mass(w.h) - d["clipped"]
+    assert math.isclose(added, 500.0 * d["t"], rel_tol=1e-11)
+    assert math.isclose(d["boundary_in"], 500.0 * d["t"], rel_tol=1e-12)
+
+
+def test_mass_budget_with_inflow_and_level():
+    w = W.river(nx=80, ny=30, seed=4, q_in=2000.0)
+    m = _mesh(w)
+    h, hu, hv, dts, d = oracle.run(m, oracle.opts("muscl"), w.z, w.nman, w.h, w.hu, w.hv, 300,
+                                   q_in=w.q_in, level=w.level)
+    m0 = m.mass(w.h)
+    assert abs(m.mass(h) - m0 - d["clipped"] - d["boundary_in"]) <= 1e-12 * m0
+
+
+@pytest.mark.parametrize("scheme,limiter,steps", [("hllc", "superbee", 60), ("muscl", "superbee", 60),
+                                                 ("waf", "phi1", 60), ("waf", "superbee", 20)])
+def test_circular_dam_break_mirror_symmetry(scheme, limiter, steps):
+    """A mirror-symmetric mesh keeps the solution mirror-symmetric.  WAF with
+    SUPERBEE is checked over 20 steps only: its ratio r jumps from +inf to
+    -inf when the local change in h crosses zero, so round-off decides on
+    which step each mirror side switches and the sides drift apart later."""
+    w = W.circular_dam_break(n=16, radius=6.0, half=16.0)
+    m = _mesh(w)
+    h, hu, hv, dts, d = oracle.run(m, oracle.opts(scheme, waf_limiter=limiter), w.z, w.nman,
+                                   w.h, w.hu, w.hv, steps)
+    cx, cy = m.arrays["cx"], m.arrays["cy"]
+    key = {(round(x, 9), round(y, 9)): i for i, (x, y) in enumerate(zip(cx, cy))}
+    mx = np.array([key[(round(-x, 9), round(y, 9))] for x, y in zip(cx, cy)])
+    my = np.array([key[(round(x, 9), round(-y, 9))] for x, y in zip(cx, cy)])
+    assert np.abs(h - h[mx]).max() < 1e-12
+    assert np.abs(h - h[my]).max() < 1e-12
+    assert np.abs(hu + hu[mx]).max() < 1e-12
+    assert np.abs(hv - hv[mx]).max() < 1e-12
+    assert np.abs(hv + hv[my]).max() < 1e-12
+    assert np.abs(h - w.h).max() > 0.1
+
+
+@pytest.mark.parametrize("scheme", ["hllc", "muscl", "waf"])
+def test_rotation_by_90_degrees(scheme):
+    """Rotating mesh and velocities by 90 degrees rotates the solution."""
+    w = W.partial_dam_break(nx=24, ny=12, spacing=1.0, n_gauss=8, seed=5)
+    w.hu = 0.1 * w.h
+    m = _mesh(w)
+    rot = np.stack([-w.nodes[:, 1], w.nodes[:, 0]], axis=1)
+    mr = oracle.Mesh(rot, w.tris, w.bnd_edges, w.bnd_tag, w.cut_edges)
+    o = oracle.opts(scheme)
+    a = oracle.run(m, o, w.z, w.nman, w.h, w.hu, w.hv, 80)
+    b = oracle.run(mr, o, w.z, w.nman, w.h, -w.hv, w.hu, 80)
+    assert np.array_equal(a[3], b[3])                  # same time steps
+    assert np.abs(a[0] - b[0]).max() < 1e-13
+    assert np.abs(a[1] - b[2]).max() < 1e-13
+    assert np.abs(a[2] + b[1]).max() < 1e-13
+
+
+def test_cell_renumbering_does_not_change_the_solution():
+    """The same mesh under another cell numbering gives the same solution (cf. Sec. 5.3.1)."""
+    w = W.partial_dam_break(nx=24, ny=12, spacing=1.0, n_gauss=8, seed=5)
+    m = _mesh(w)
+    p = np.random.default_rng(1).permutation(w.n_cells)
+    mp = oracle.Mesh(w.nodes, w.tris[p], w.bnd_edges, w.bnd_tag, w.cut_edges)
+    for s in ("muscl", "waf"):
+        o = oracle.opts(s)
+        a = oracle.run(m, o, w.z, w.nman, w.h, w.hu, w.hv, 100)
+        b = oracle.run(mp, o, w.z[p], w.nman[p], w.h[p], w.hu[p], w.hv[p], 100)
+        assert np.abs(a[0][p] - b[0]).max() < 1e-12
+        assert np.abs(a[1][p] - b[1]).max() < 1e-12
+
+
+def test_openmp_thread_count_does_not_change_results():
+    w = W.partial_dam_break(nx=24, ny=12, spacing=1.0, n_gauss=8, seed=5)
+    m = _mesh(w)
+    a = oracle.run(m, oracle.opts("muscl", threads=1), w.z, w.nman, w.h, w.hu, w.hv, 50)
+    b = oracle.run(m, oracle.opts("muscl", threads=4), w.z, w.nman, w.h, w.hu, w.hv, 50)
+    for x, y in zip(a[:4], b[:4]):
+        assert np.array_equal(x, y)
+
+
+# --------------------------------------------------------------------------
+# Friction, order of accuracy
+# --------------------------------------------------------------------------
+
+def test_manning_decay_of_uniform_flow():
+    """Uniform flow under Manning friction follows du/dt = -g n^2 u|u| / h^(4/3)."""
+    errs = []
+    for steps in (200, 400):
+        nodes, tris, bnd, side = W.structured(6, 6, 6.0, 6.0)
+        n = len(tris)
+        w = W.Workload("uniform", nodes, tris, bnd, np.full(len(bnd), W.tag(W.OPEN), np.int32),
+                       np.zeros((0, 2), np.int32), np.zeros(n), np.full(n, 0.05), np.ones(n),
+                       np.ones(n), np.zeros(n))
+        m = _mesh(w)
+        h, hu, hv, _, d = oracle.run(m, oracle.opts("hllc"), w.z, w.nman, w.h, w.hu, w.hv, steps,
+                                     dt=np.full(steps, 10.0 / steps))
+        assert np.abs(h - 1.0).max() < 1e-12
+        exact = manning_decay(1.0, 1.0, 0.05, G, 10.0)
+        errs.append(np.abs(hu - exact).max())
+    # with h fixed, 1/u grows by dt g n^2 / h^(4/3) per point-implicit step, which
+    # is exactly the closed form's 1/u(t) = 1/u0 + g n^2 t / h^(4/3)
+    assert max(errs) < 1e-12
+
+
+def _restrict(fine, n):
+    """Average a 2n x 2n structured solution onto the nested n x n mesh."""
+    nf = 2 * n
+    f = fine.reshape(nf, nf, 2)          # [j][i][lower/upper]
+    out = np.empty((n, n, 2))
+    lo = np.stack([f[0::2, 0::2, 0], f[0::2, 1::2, 0], f[0::2, 1::2, 1], f[1::2, 1::2, 0]])
+    up = np.stack([f[0::2, 0::2, 1], f[1::2, 0::2, 0], f[1::2, 0::2, 1], f[1::2, 1::2, 1]])
+    out[:, :, 0] = lo.mean(axis=0)
+    out[:, :, 1] = up.mean(axis=0)
+    return out.reshape(-1)
+
+
+@pytest.mark.parametrize("scheme,lo_order", [("hllc", 0.8), ("muscl", 1.6)])
+def test_order_of_accuracy_smooth_hump(scheme, lo_order):
+    """Nested meshes, smooth hump, Heun in time: successive-difference order."""
+    sols = {}
+    for n in (16, 32, 64, 128):
+        w = W.gaussian_hump(n, l=10.0, amp=0.05, sigma=1.2)
+        m = _mesh(w)
+        steps = n // 2
+        h, *_ = oracle.run(m, oracle.opts(scheme, time_scheme="heun"), w.z, w.nman, w.h, w.hu, w.hv,
+                           steps, dt=np.full(steps, 0.4 / steps))
+        sols[n] = h
+    d1 = np.abs(sols[16] - _restrict(sols[32], 16)).mean()
+    d2 = np.abs(sols[32] - _restrict(sols[64], 32)).mean()
+    d3 = np.abs(sols[64] - _restrict(sols[128], 64)).mean()
+    p1, p2 = math.log2(d1 / d2), math.log2(d2 / d3)
+    assert p2 > lo_order, (p1, p2)
+
+
+# --------------------------------------------------------------------------
+# Single-edge flux and gradient pins
+# --------------------------------------------------------------------------
+
+def _state(hL, uL, vL, hR, uR, vR):
+    return np.array([hL, hL, hL, uL, vL, hR, hR, hR, uR, vR])
+
+
+def test_flux_consistency_identical_states():
+    """Identical states: the numerical flux is the physical flux G(U)."""
+    rng = np.random.default_rng(0)
+    for _ in range(200):
+        h, u, v = rng.uniform(0.1, 5), rng.uniform(-6, 6), rng.uniform(-3, 3)
+        for s in ("hllc", "waf"):
+            waf = None if s == "hllc" else np.array([rng.uniform(0, 0.2), h, h, v, v, h, h, 0])
+            M, PL, PR, T = oracle.edge_flux(oracle.opts(s), _state(h, u, v, h, u, v), waf)
+            assert math.isclose(M, h * u, rel_tol=1e-14, abs_tol=1e-14)
+            assert math.isclose(PL, h * u * u, rel_tol=1e-13, abs_tol=1e-13)
+            assert math.isclose(PR, h * u * u, rel_tol=1e-13, abs_tol=1e-13)
+            assert math.isclose(T, h * u * v, rel_tol=1e-13, abs_tol=1e-13)
+
+
+def test_hllc_resolves_an_isolated_shear_wave_exactly():
+    """Equal depth and normal velocity, jump in tangential velocity only: the
+    exact Riemann solution is a shear wave moving at u, so the Godunov flux of
+    h v is h u v taken from the upwind side.  HLLC reproduces it (this pins the
+    upwind choice of the third component, reading R2)."""
+    rng = np.random.default_rng(7)
+    for _ in range(200):
+        h, u = rng.uniform(0.1, 4), rng.uniform(-3, 3)
+        vL, vR = rng.uniform(-2, 2), rng.uniform(-2, 2)
+        M, PL, PR, T = oracle.edge_flux(oracle.opts("hllc"), _state(h, u, vL, h, u, vR))
+        assert math.isclose(M, h * u, rel_tol=1e-13, abs_tol=1e-14)
+        assert math.isclose(PL, h * u * u, rel_tol=1e-13, abs_tol=1e-13)
+        assert math.isclose(T, h * u * (vL if u >= 0 else vR), rel_tol=1e-12, abs_tol=1e-13)
+
+
+def test_flux_mirror_states_have_no_mass_flux():
+    rng = np.random.default_rng(1)
+    for _ in range(200):
+        h, u = rng.uniform(0.1, 5), rng.uniform(-4, 4)
+        M, PL, PR, T = oracle.edge_flux(oracle.opts("hllc"), _state(h, u, 0.3, h, -u, 0.3))
+        assert abs(M) < 1e-13 * max(1.0, abs(h * u))
+        assert math.isclose(PL, PR, rel_tol=1e-13, abs_tol=1e-13)
+
+
+def test_flux_supersonic_is_upwind():
+    o = oracle.opts("hllc")
+    M, PL, PR, T = oracle.edge_flux(o, _state(1.0, 8.0, 0.5, 0.3, 6.0, -0.2))
+    assert M == 8.0 and PL == 64.0 and T == 8.0 * 0.5
+    M, PL, PR, T = oracle.edge_flux(o, _state(1.0, -9.0, 0.5, 0.3, -8.0, -0.2))
+    assert math.isclose(M, 0.3 * -8.0, rel_tol=1e-15) and T == M * -0.2
+
+
+def test_flux_dry_bed_and_both_dry():
+    o = oracle.opts("hllc")
+    M, *_ = oracle.edge_flux(o, _state(0.0, 0.0, 0.0, 1.0, 0.0, 0.0))
+    assert M < 0                              # water moves into the dry left cell
+    out = oracle.edge_flux(o, _state(0.0, 0.0, 0.0, 0.0, 0.0, 0.0))
+    assert not out.any()
+
+
+def test_waf_phi0_is_hllc_and_weights_are_upwind():
+    """WAF with phi = 0 (A = 1) reduces to the first-order HLLC flux (Sec. 5.2.2)."""
+    rng = np.random.default_rng(2)
+    for _ in range(300):
+        st = _state(rng.uniform(0.05, 3), rng.uniform(-3, 3), rng.uniform(-1, 1),
+                    rng.uniform(0.05, 3), rng.uniform(-3, 3), rng.uniform(-1, 1))
+        waf = np.array([rng.uniform(0, 0.3), rng.uniform(0, 3), rng.uniform(0, 3),
+                        rng.uniform(-1, 1), rng.uniform(-1, 1), st[2], st[7], 0])
+        a = oracle.edge_flux(oracle.opts("hllc"), st)
+        b = oracle.edge_flux(oracle.opts("waf", waf_limiter="phi0"), st, waf)
+        assert np.allclose(a, b, rtol=1e-12, atol=1e-12)
+
+
+def test_waf_phi1_at_zero_courant_is_central():
+    """Unlimited WAF weights with c = 0 average the two physical fluxes."""
+    rng = np.random.default_rng(3)
+    for _ in range(100):
+        hL, uL, hR, uR = rng.uniform(0.2, 3), rng.uniform(-2, 2), rng.uniform(0.2, 3), rng.uniform(-2, 2)
+        st = _state(hL, uL, 0.0, hR, uR, 0.0)
+        waf = np.array([0.0, hL, hR, 0, 0, hL, hR, 0])
+        M, PL, PR, T = oracle.edge_flux(oracle.opts("waf", waf_limiter="phi1"), st, waf)
+        assert math.isclose(M, 0.5 * (hL * uL + hR * uR), rel_tol=1e-12, abs_tol=1e-12)
+        GL2 = hL * uL * uL + 0.5 * G * hL * hL
+        GR2 = hR * uR * uR + 0.5 * G * hR * hR
+        assert math.isclose(PL + 0.5 * G * hL * hL, 0.5 * (GL2 + GR2), rel_tol=1e-12)
+
+
+def test_lsq_gradient_exact_for_linear_fields():
+    w = W.partial_dam_break(nx=12, ny=8, spacing=1.0, n_gauss=0, seed=3, breach=False)
+    m = _mesh(w, cut=False)
+    cx, cy = m.arrays["cx"], m.arrays["cy"]
+    z = np.zeros(m.n)
+    h = 5.0 + 0.1 * cx - 0.2 * cy
+    u = 0.3 - 0.05 * cx + 0.07 * cy
+    v = -0.1 + 0.02 * cx + 0.04 * cy
+    gl, gu = oracle.gradients(m, oracle.opts("muscl"), z, h, h * u, h * v)
+    interior = (m.arrays["nbr"] >= 0).sum(axis=1) >= 2
+    assert np.allclose(gu[interior], [0.1, -0.2, -0.05, 0.07, 0.02, 0.04], atol=1e-12)
+
+
+def test_barth_jespersen_keeps_face_values_within_neighbour_bounds():
+    w = W.partial_dam_break(nx=12, ny=8, spacing=1.0, n_gauss=0, seed=3, breach=False)
+    m = _mesh(w, cut=False)
+    rng = np.random.default_rng(4)
+    n = m.n
+    h = rng.uniform(1.0, 2.0, n)
+    hu, hv = rng.uniform(-1, 1, n), rng.uniform(-1, 1, n)
+    z = np.zeros(n)
+    gl, gu = oracle.gradients(m, oracle.opts("muscl"), z, h, hu, hv)
+    a = m.arrays
+    tri = a["tri"]
+    p = w.nodes[tri]
+    mid = 0.5 * (p + np.roll(p, -1, axis=1))
+    ox, oy = mid[:, :, 0] - a["cx"][:, None], mid[:, :, 1] - a["cy"][:, None]
+    q = [h, hu / h, hv / h]
+    limited = 0
+    for s in range(3):
+        face = q[s][:, None] + gl[:, 2 * s, None] * ox + gl[:, 2 * s + 1, None] * oy
+        nb = np.where(a["nbr"] >= 0, q[s][np.maximum(a["nbr"], 0)], q[s][:, None])
+        lo = np.minimum(q[s], nb.min(axis=1))
+        hi = np.maximum(q[s], nb.max(axis=1))
+        assert (face >= lo[:, None] - 1e-12).all() and (face <= hi[:, None] + 1e-12).all()
+        limited += (np.abs(gl[:, 2 * s:2 * s + 2]) < np.abs(gu[:, 2 * s:2 * s + 2]) - 1e-15).any(axis=1).sum()
+    assert limited > 0
+
+
+def test_gradient_is_zero_next_to_a_dry_cell():
+    w = W.partial_dam_break(nx=12, ny=8, spacing=1.0, n_gauss=0, seed=3, breach=False)
+    m = _mesh(w, cut=False)
+    n = m.n
+    cx = m.arrays["cx"]
+    h = 1.0 + 0.1 * cx
+    h[5] = 0.0
+    gl, gu = oracle.gradients(m, oracle.opts("muscl"), np.zeros(n), h, 0.1 * h, 0 * h)
+    nb = m.arrays["nbr"]
+    assert not gl[5].any()
+    for k in range(3):
+        j = nb[5, k]
+        if j >= 0:
+            assert not gl[j].any()
+    far = [i for i in range(n) if 5 not in nb[i] and i != 5 and (nb[i] >= 0).sum() == 3]
+    assert np.abs(gl[far, 0]).max() > 0.05
+
+
+def test_first_time_step_closed_form():
+    """CFL rule of Sec. 5.1 with d = inscribed radius: on unit right triangles
+    r = (2 - sqrt 2)/2, and at rest the fastest speed is sqrt(g h_max)."""
+    w = W.dam_break_1d()
+    m = _mesh(w)
+    _, _, _, dts, _ = oracle.run(m, oracle.opts("hllc", cfl=0.9), w.z, w.nman, w.h, w.hu, w.hv, 1)
+    r = (2.0 - math.sqrt(2.0)) / 2.0
+    assert math.isclose(dts[0], 0.9 * r / math.sqrt(G * 1.0), rel_tol=1e-14)
+
+
+def test_fixed_level_boundary_fills_to_its_level():
+    """A fixed-level boundary above a lake at rest lets water in until the lake
+    stands at that level (the steady state of the boundary condition)."""
+    nodes, tris, bnd, side = W.structured(20, 4, 20.0, 4.0)
+    n = len(tris)
+    tags = np.where(side == 1, W.tag(W.LEVEL), W.tag(W.WALL)).astype(np.int32)
+    w = W.Workload("level", nodes, tris, bnd, tags, np.zeros((0, 2), np.int32), np.zeros(n),
+                   np.full(n, 0.3), np.ones(n), np.zeros(n), np.zeros(n), level=np.array([1.1]))
+    m = _mesh(w)
+    h, hu, hv, dts, d = oracle.run(m, oracle.opts("hllc"), w.z, w.nman, w.h, w.hu, w.hv, 12000,
+                                   level=w.level)
+    assert d["t"] > 100.0
+    assert np.abs(h - 1.1).max() < 2e-3
+    assert math.isclose(m.mass(h) - m.mass(w.h), d["boundary_in"], rel_tol=1e-10)

@@ -1,0 +1,178 @@
+/*
+ * swe.h -- C ABI of the GB300 shallow-water finite-volume library.
+ *
+ * The library advances the 2D shallow-water equations (h, hu, hv) on an
+ * unstructured triangle mesh with bathymetry by explicit finite-volume steps
+ * (Delmas & Soulaimani, arXiv 2307.16758, Sec. 5.1: the semi-discrete form
+ * |Omega_i| dU_i/dt = -sum_j L_ij T^-1 G~(T U_i, T U_j) + sources, explicit
+ * Euler in time, CFL time step with the inscribed radius).  Fluxes are HLLC
+ * (Sec. 5.2.1), HLLC on MUSCL states (least-squares gradients with a
+ * Barth-Jespersen limiter) or WAF (Sec. 5.2.2), with a well-balanced
+ * hydrostatic reconstruction, wet/dry handling and Manning friction.  Every
+ * step runs in CUDA kernels for sm_103a; the host side only builds the mesh,
+ * copies inputs and outputs, and launches.
+ *
+ * Conventions
+ *  - Every function returns SWE_OK (0) or a negative SWE_ERR_* code and never
+ *    aborts; swe_last_error() gives a message for the calling thread.
+ *  - Host arrays are caller-owned and are copied; outputs go into
+ *    caller-allocated buffers.  Per-cell arrays use the caller's (original)
+ *    cell order: the library renumbers cells internally and undoes the
+ *    permutation on output.
+ *  - Cell ids are int32 (fewer than 2^28 cells per mesh).
+ *  - Boundary tags: tag = kind + 4*group with kind SWE_WALL, SWE_OPEN
+ *    (transmissive), SWE_INFLOW (group selects the discharge) or SWE_LEVEL
+ *    (group selects the free-surface level); 0 <= group < SWE_MAX_GROUPS.
+ *  - Device work is asynchronous on the state's stream.  Errors detected on
+ *    the device (a non-finite value, no wet cell for the CFL rule) are
+ *    returned by the next call that synchronises (swe_sync, swe_get_state,
+ *    swe_mass, swe_time).
+ */
+#ifndef SWE_H
+#define SWE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    SWE_OK = 0,
+    SWE_ERR_ARG = -1,        /* bad argument (NULL, size, enum, range) */
+    SWE_ERR_MESH = -2,       /* invalid mesh (degenerate, non-manifold, bad tags) */
+    SWE_ERR_CUDA = -3,       /* a CUDA runtime call failed */
+    SWE_ERR_DRY = -4,        /* CFL rule: no wet cell, no time step defined */
+    SWE_ERR_NONFINITE = -5,  /* a non-finite depth or discharge was produced */
+    SWE_ERR_TIMEOUT = -6,    /* a bounded device wait gave up */
+    SWE_ERR_NOMEM = -7       /* host or device allocation failed */
+};
+
+enum { SWE_WALL = 0, SWE_OPEN = 1, SWE_INFLOW = 2, SWE_LEVEL = 3 };
+enum { SWE_REORDER_NONE = 0, SWE_REORDER_MORTON = 1, SWE_REORDER_RCM = 2 };
+enum { SWE_SCHEME_HLLC = 0, SWE_SCHEME_MUSCL = 1, SWE_SCHEME_WAF = 2 };
+enum { SWE_FP64 = 0, SWE_FP32 = 1 };
+enum { SWE_EULER = 0, SWE_HEUN = 1 };
+enum { SWE_WAF_SUPERBEE = 0, SWE_WAF_PHI1 = 1, SWE_WAF_PHI0 = 2 };
+enum { SWE_KERNEL_AUTO = 0, SWE_KERNEL_SPLIT = 1, SWE_KERNEL_FUSED = 2 };
+#define SWE_MAX_GROUPS 16
+
+typedef struct swe_mesh swe_mesh;
+typedef struct swe_state swe_state;
+typedef struct swe_ensemble swe_ensemble;
+
+/* Solver options.  Fill with swe_params_default, then override. */
+typedef struct {
+    int scheme;       /* SWE_SCHEME_*; HLLC first order, MUSCL-HLLC or WAF-HLLC */
+    int precision;    /* SWE_FP64, or SWE_FP32 (FP32 state and fluxes; mass and time in FP64) */
+    int time_scheme;  /* SWE_EULER (Sec. 5.1) or SWE_HEUN (two Euler stages averaged) */
+    int waf_limiter;  /* SWE_WAF_* (Sec. 5.2.2; SUPERBEE is the paper's choice) */
+    double g;         /* gravity [m/s^2] */
+    double h_eps;     /* depth below which a cell counts as dry [m] */
+    double r_eps;     /* WAF: relative size of a local change treated as zero */
+    int kernel;       /* SWE_KERNEL_*: split (face values in scratch) or fused tile kernel */
+    int block;        /* threads per block (0: default) */
+} swe_params;
+
+/* Values of the boundary groups (copied at init). */
+typedef struct {
+    int n_inflow;
+    const double *inflow_q;   /* [n_inflow] discharge in m^3/s, spread per unit length over the group's edges */
+    int n_level;
+    const double *level;      /* [n_level] free-surface level in m */
+} swe_bc_values;
+
+const char *swe_last_error(void);
+
+/* Defaults: g = 9.81, h_eps = 1e-6 (FP64) or 1e-4 (FP32),
+ * r_eps = 1e-12 (FP64) or 1e-6 (FP32), Euler, SUPERBEE, automatic kernel. */
+int swe_params_default(swe_params *p, int scheme, int precision);
+
+/* Device memory: by default cudaMalloc/cudaFree.  A host program (for example
+ * the Python binding, which routes to PyTorch's caching allocator) may install
+ * its own pair; ctx is passed back unchanged.  Global to the library. */
+typedef void *(*swe_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*swe_free_fn)(void *ptr, void *stream, void *ctx);
+int swe_set_allocator(swe_alloc_fn alloc, swe_free_fn free_fn, void *ctx);
+
+/* ---- Mesh (host only) -------------------------------------------------- */
+
+/* Build a mesh (Sec. 5.1 notation: cells Omega_i, sides L_ij, normals n_ij).
+ *  node_xy[n_nodes][2] FP64 coordinates; tri[n_tri][3] node ids (any
+ *  orientation; the library orients counter-clockwise);
+ *  bnd_edges[n_bnd][2] node pairs on the boundary with bnd_tag[n_bnd]
+ *  (unlisted boundary edges are walls); cut_edges[n_cut][2] interior edges
+ *  that act as walls on both sides (may be NULL when n_cut = 0);
+ *  reorder: SWE_REORDER_NONE, _MORTON (centroid Z-order) or _RCM.
+ * Errors: SWE_ERR_ARG, SWE_ERR_MESH (degenerate triangle, edge shared by more
+ * than two cells, folded mesh, listed edge not on the boundary). */
+int swe_mesh_create(const double *node_xy, int64_t n_nodes,
+                    const int32_t *tri, int64_t n_tri,
+                    const int32_t *bnd_edges, const int32_t *bnd_tag, int64_t n_bnd,
+                    const int32_t *cut_edges, int64_t n_cut,
+                    int reorder, swe_mesh **out);
+int swe_mesh_destroy(swe_mesh *m);
+/* Number of cells and the smallest inscribed radius (CFL rule, Sec. 5.1). */
+int swe_mesh_info(const swe_mesh *m, int64_t *n_cells, double *r_min);
+
+/* Export the builder's arrays in the library's (new) cell order; any pointer
+ * may be NULL.  perm[new] = original id; tri[n][3] oriented; nbr[n][3]
+ * neighbour (new id) or -1; nbr_edge[n][3] local edge index in the
+ * neighbour or -1; btag[n][3] boundary tag or -1; lnx,lny[n][3] outward
+ * normal times edge length; area, cx, cy, rin[n]; dx,dy[n][3] centroid
+ * offset to the neighbour (0 on boundaries). */
+int swe_mesh_export(const swe_mesh *m, int32_t *perm, int32_t *tri, int32_t *nbr,
+                    int32_t *nbr_edge, int32_t *btag, double *lnx, double *lny,
+                    double *area, double *cx, double *cy, double *rin,
+                    double *dx, double *dy);
+
+/* ---- State (device) ---------------------------------------------------- */
+
+/* Allocate the device state for a mesh and upload it.  h, hu, hv, z and
+ * manning_n are FP64 host arrays of n_cells in the original order (manning_n
+ * may be NULL: no friction).  bc may be NULL.  stream is a cudaStream_t
+ * (NULL: the legacy default stream).  The mesh may be destroyed afterwards. */
+int swe_state_init(const swe_mesh *m, const swe_params *p,
+                   const double *h, const double *hu, const double *hv,
+                   const double *z, const double *manning_n,
+                   const swe_bc_values *bc, void *stream, swe_state **out);
+int swe_state_destroy(swe_state *s);
+int swe_set_stream(swe_state *s, void *stream);
+/* Replace the conserved variables from FP64 host arrays (original order);
+ * time, step count and mass diagnostics are kept. */
+int swe_set_state(swe_state *s, const double *h, const double *hu, const double *hv);
+
+/* Advance n_steps explicit steps with the CFL rule dt = cfl * r_min / max_wet(sqrt(g h)+|u|)
+ * (Sec. 5.1).  Asynchronous: returns once the work is enqueued. */
+int swe_step(swe_state *s, int n_steps, double cfl);
+/* Advance with a given time-step sequence dt[n_steps] (host array). */
+int swe_step_dt(swe_state *s, const double *dt, int n_steps);
+/* Wait for the stream and return the device status (SWE_OK or an error). */
+int swe_sync(swe_state *s);
+
+/* Copy the conserved variables to FP64 host arrays in the original order. */
+int swe_get_state(swe_state *s, double *h, double *hu, double *hv);
+/* Sum of area*h in FP64 (deterministic, compensated), the mass added by
+ * clipping negative depths and the net mass that entered through the
+ * boundary since init (m^3).  Any output pointer may be NULL. */
+int swe_mass(swe_state *s, double *mass, double *clipped_mass, double *boundary_net_inflow);
+/* Simulated time (FP64 accumulation of the steps) and the number of steps. */
+int swe_time(swe_state *s, double *t, int64_t *steps);
+/* Device bytes held by the state and the kernel configuration in use. */
+int swe_state_info(const swe_state *s, int64_t *device_bytes, int *kernel, int *block);
+
+/* ---- Ensemble ---------------------------------------------------------- */
+
+/* Group independent states (same precision, scheme and time scheme) so that
+ * one launch per step advances all of them, each with its own CFL time step.
+ * The members stay owned by the caller and must outlive the ensemble. */
+int swe_ensemble_create(swe_state *const *members, int n_members, swe_ensemble **out);
+int swe_ensemble_destroy(swe_ensemble *e);
+int swe_ensemble_step(swe_ensemble *e, int n_steps, double cfl);
+int swe_ensemble_sync(swe_ensemble *e);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

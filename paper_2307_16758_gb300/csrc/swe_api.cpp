@@ -1,0 +1,521 @@
+// C ABI of the shallow-water library: handles, device memory, launches.
+// Every numerical step runs in the CUDA kernels of swe_kernels.cu; this file
+// only validates arguments, moves data and orders the launches on a stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "swe_dev.h"
+#include "swe_mesh.h"
+
+int swe_mesh_build_host(const double *xy, int64_t n_nodes, const int32_t *tri, int64_t n,
+                        const int32_t *bnd, const int32_t *bnd_tag, int64_t n_bnd,
+                        const int32_t *cut, int64_t n_cut, int reorder, swe_mesh **out);
+
+static thread_local std::string g_err;
+void swe_set_error(const std::string &msg) { g_err = msg; }
+
+namespace {
+
+swe_alloc_fn g_alloc = nullptr;
+swe_free_fn g_free = nullptr;
+void *g_ctx = nullptr;
+
+void *dev_alloc(size_t bytes, cudaStream_t s)
+{
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~size_t(255);
+    if (g_alloc) return g_alloc(bytes, (void *)s, g_ctx);
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+    return p;
+}
+
+void dev_free(void *p, cudaStream_t s)
+{
+    if (!p) return;
+    if (g_free) g_free(p, (void *)s, g_ctx);
+    else cudaFree(p);
+}
+
+#define CK(call)                                                                  \
+    do {                                                                          \
+        cudaError_t e_ = (call);                                                  \
+        if (e_ != cudaSuccess) {                                                  \
+            swe_set_error(std::string(#call) + ": " + cudaGetErrorString(e_));    \
+            return SWE_ERR_CUDA;                                                  \
+        }                                                                         \
+    } while (0)
+
+struct Alloc {
+    std::vector<std::pair<void *, size_t>> blocks;
+    int64_t bytes = 0;
+};
+
+template <typename T> struct StateT {
+    swe_params p{};
+    int64_t n = 0;
+    double r_min = 0.0;
+    cudaStream_t stream = nullptr;
+    Alloc mem;
+    // mesh on the device
+    int32_t *nbr = nullptr, *perm = nullptr;
+    Vec2<T> *ln = nullptr, *dd = nullptr;
+    T *z = nullptr, *nman = nullptr;
+    double *area = nullptr;
+    // state: ping-pong buffers plus the Heun stage buffer
+    T *h[3] = {}, *hu[3] = {}, *hv[3] = {};
+    int cur = 0;
+    // scratch: face values / centre values and upwind means
+    Vec4<T> *F = nullptr, *U = nullptr;
+    DevScalars *sc = nullptr;
+    double *mass_part = nullptr, *mass_out = nullptr, *staging = nullptr;
+    int n_part = 0;
+    double *dtbuf = nullptr;
+    int dtbuf_len = 0;
+    int64_t k = 0;            // steps launched (selects the smax slots)
+    bool smax_valid = false;
+    T qlen[SWE_MAX_GROUPS] = {}, level[SWE_MAX_GROUPS] = {};
+
+    template <typename P> P *alloc(size_t count)
+    {
+        size_t b = count * sizeof(P);
+        void *ptr = dev_alloc(b, stream);
+        if (ptr) { mem.blocks.push_back({ptr, b}); mem.bytes += (int64_t)((b + 255) & ~size_t(255)); }
+        return (P *)ptr;
+    }
+    ~StateT()
+    {
+        for (auto &b : mem.blocks) dev_free(b.first, stream);
+    }
+
+    DevMesh<T> dmesh() const
+    {
+        DevMesh<T> m;
+        m.n = n; m.nbr = nbr; m.ln = ln; m.dd = dd; m.z = z; m.nman = nman; m.area = area;
+        return m;
+    }
+
+    StepArgs<T> args(int in, int out) const
+    {
+        StepArgs<T> a{};
+        a.m = dmesh();
+        a.h = h[in]; a.hu = hu[in]; a.hv = hv[in];
+        a.ho = h[out]; a.huo = hu[out]; a.hvo = hv[out];
+        a.F = F; a.U = U; a.sc = sc;
+        a.dtv = nullptr;
+        a.slot_cur = (int)(k % 3); a.slot_next = (int)((k + 1) % 3); a.slot_clear = (int)((k + 2) % 3);
+        a.mode = MODE_EULER;
+        a.g = (T)p.g; a.h_eps = (T)p.h_eps; a.r_eps = (T)p.r_eps;
+        a.waf_limiter = p.waf_limiter;
+        for (int q = 0; q < SWE_MAX_GROUPS; q++) { a.qlen[q] = qlen[q]; a.level[q] = level[q]; }
+        return a;
+    }
+
+    int block() const { return p.block > 0 ? p.block : 256; }
+
+    int init_smax()
+    {
+        CK(cudaMemsetAsync(sc->smax, 0, sizeof(sc->smax), stream));
+        StepArgs<T> a = args(cur, cur);
+        CK(launch_smax<T>(a, (int)(k % 3), block(), stream));
+        smax_valid = true;
+        return SWE_OK;
+    }
+
+    // One explicit step (Euler, or Heun's two stages and the average).
+    int one_step(double cfl, const double *dt_dev)
+    {
+        const int nxt = cur ^ 1;
+        StepArgs<T> a = args(cur, nxt);
+        a.cfl_rmin = cfl * r_min;
+        a.dtv = dt_dev;
+        const int bl = block();
+        if (p.time_scheme == SWE_EULER) {
+            CK(launch_prep<T>(p.scheme, a, F, U, bl, stream));
+            CK(launch_flux<T>(p.scheme, a, bl, stream));
+        } else {
+            StepArgs<T> s1 = args(cur, 2);
+            s1.cfl_rmin = a.cfl_rmin; s1.dtv = dt_dev; s1.mode = MODE_STAGE;
+            CK(launch_prep<T>(p.scheme, s1, F, U, bl, stream));
+            CK(launch_flux<T>(p.scheme, s1, bl, stream));
+            StepArgs<T> s2 = args(2, nxt);
+            s2.cfl_rmin = a.cfl_rmin; s2.dtv = dt_dev; s2.mode = MODE_STAGE;
+            CK(launch_prep<T>(p.scheme, s2, F, U, bl, stream));
+            CK(launch_flux<T>(p.scheme, s2, bl, stream));
+            StepArgs<T> av = args(nxt, nxt);
+            av.cfl_rmin = a.cfl_rmin; av.dtv = dt_dev;
+            CK(launch_heun_avg<T>(av, h[cur], hu[cur], hv[cur], bl, stream));
+        }
+        cur = nxt;
+        k++;
+        return SWE_OK;
+    }
+
+    int read_scalars(DevScalars &out)
+    {
+        CK(cudaMemcpyAsync(&out, sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, stream));
+        CK(cudaStreamSynchronize(stream));
+        return SWE_OK;
+    }
+
+    int status()
+    {
+        DevScalars s;
+        int rc = read_scalars(s);
+        if (rc) return rc;
+        if (s.status & ST_NONFINITE) { swe_set_error("a non-finite depth or discharge was produced"); return SWE_ERR_NONFINITE; }
+        if (s.status & ST_DRY) { swe_set_error("CFL rule: no wet cell"); return SWE_ERR_DRY; }
+        return SWE_OK;
+    }
+};
+
+bool valid_params(const swe_params *p)
+{
+    return p && p->scheme >= 0 && p->scheme <= 2 && (p->precision == SWE_FP64 || p->precision == SWE_FP32) &&
+           (p->time_scheme == SWE_EULER || p->time_scheme == SWE_HEUN) && p->waf_limiter >= 0 &&
+           p->waf_limiter <= 2 && p->g > 0 && p->h_eps > 0 && p->r_eps >= 0 && p->kernel >= 0 &&
+           p->kernel <= 2 && p->block >= 0 && p->block <= 1024 && (p->block % 32) == 0;
+}
+
+template <typename T>
+int state_init(StateT<T> &s, const swe_mesh *m, const double *h, const double *hu, const double *hv,
+               const double *z, const double *nman, const swe_bc_values *bc)
+{
+    const int64_t n = m->n;
+    s.n = n;
+    s.r_min = m->r_min;
+    std::vector<int32_t> nbr((size_t)(3 * n));
+    std::vector<Vec2<T>> ln((size_t)(3 * n)), dd((size_t)(3 * n));
+    std::vector<T> zt((size_t)n), nt((size_t)n);
+    bool friction = false;
+    for (int64_t i = 0; i < n; i++) {
+        int32_t o = m->perm[i];
+        zt[i] = (T)z[o];
+        nt[i] = nman ? (T)nman[o] : T(0);
+        friction = friction || (nman && nman[o] > 0.0);
+        for (int k = 0; k < 3; k++) {
+            int64_t e = 3 * i + k;
+            nbr[e] = swe_pack_nbr(*m, i, k);
+            ln[e].x = (T)m->lnx[e]; ln[e].y = (T)m->lny[e];
+            dd[e].x = (T)m->dx[e]; dd[e].y = (T)m->dy[e];
+        }
+    }
+    if (bc) {
+        for (int g = 0; g < bc->n_inflow && g < SWE_MAX_GROUPS; g++)
+            s.qlen[g] = m->group_len[g] > 0.0 ? (T)(bc->inflow_q[g] / m->group_len[g]) : T(0);
+        for (int g = 0; g < bc->n_level && g < SWE_MAX_GROUPS; g++) s.level[g] = (T)bc->level[g];
+    }
+    s.nbr = s.template alloc<int32_t>(3 * n);
+    s.perm = s.template alloc<int32_t>(n);
+    s.ln = s.template alloc<Vec2<T>>(3 * n);
+    s.dd = s.template alloc<Vec2<T>>(3 * n);
+    s.z = s.template alloc<T>(n);
+    if (friction) s.nman = s.template alloc<T>(n);
+    s.area = s.template alloc<double>(n);
+    const int nbuf = s.p.time_scheme == SWE_HEUN ? 3 : 2;
+    for (int b = 0; b < nbuf; b++) {
+        s.h[b] = s.template alloc<T>(n); s.hu[b] = s.template alloc<T>(n); s.hv[b] = s.template alloc<T>(n);
+    }
+    if (s.p.scheme == SWE_SCHEME_MUSCL) s.F = s.template alloc<Vec4<T>>(3 * n);
+    if (s.p.scheme == SWE_SCHEME_WAF) { s.F = s.template alloc<Vec4<T>>(n); s.U = s.template alloc<Vec4<T>>(3 * n); }
+    s.sc = s.template alloc<DevScalars>(1);
+    s.n_part = mass_partials_needed(n);
+    s.mass_part = s.template alloc<double>(s.n_part);
+    s.mass_out = s.template alloc<double>(1);
+    s.staging = s.template alloc<double>(3 * n);
+    for (auto &b : s.mem.blocks)
+        if (!b.first) { swe_set_error("device allocation failed"); return SWE_ERR_NOMEM; }
+    if (!s.nbr || !s.staging) { swe_set_error("device allocation failed"); return SWE_ERR_NOMEM; }
+    cudaStream_t st = s.stream;
+    CK(cudaMemcpyAsync(s.nbr, nbr.data(), sizeof(int32_t) * 3 * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s.perm, m->perm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s.ln, ln.data(), sizeof(Vec2<T>) * 3 * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s.dd, dd.data(), sizeof(Vec2<T>) * 3 * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s.z, zt.data(), sizeof(T) * n, cudaMemcpyHostToDevice, st));
+    if (s.nman) CK(cudaMemcpyAsync(s.nman, nt.data(), sizeof(T) * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s.area, m->area.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(s.sc, 0, sizeof(DevScalars), st));
+    // initial state through the same path as swe_set_state
+    CK(cudaMemcpyAsync(s.staging, h, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s.staging + n, hu, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s.staging + 2 * n, hv, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    CK(launch_scatter_in<T>(n, s.perm, s.staging, s.h[0], s.hu[0], s.hv[0], st));
+    CK(cudaStreamSynchronize(st));   // host vectors above go out of scope
+    return s.init_smax();
+}
+
+}  // namespace
+
+struct swe_state {
+    int precision = SWE_FP64;
+    std::unique_ptr<StateT<float>> f;
+    std::unique_ptr<StateT<double>> d;
+};
+
+#define DISPATCH(st, expr)                 \
+    ((st)->precision == SWE_FP32 ? [&](auto &S) { return expr; }(*(st)->f) : [&](auto &S) { return expr; }(*(st)->d))
+
+extern "C" {
+
+const char *swe_last_error(void) { return g_err.c_str(); }
+
+int swe_params_default(swe_params *p, int scheme, int precision)
+{
+    if (!p || scheme < 0 || scheme > 2 || (precision != SWE_FP64 && precision != SWE_FP32)) {
+        swe_set_error("swe_params_default: bad argument");
+        return SWE_ERR_ARG;
+    }
+    std::memset(p, 0, sizeof(*p));
+    p->scheme = scheme;
+    p->precision = precision;
+    p->time_scheme = SWE_EULER;
+    p->waf_limiter = SWE_WAF_SUPERBEE;
+    p->g = 9.81;
+    p->h_eps = precision == SWE_FP64 ? 1e-6 : 1e-4;
+    p->r_eps = precision == SWE_FP64 ? 1e-12 : 1e-6;
+    p->kernel = SWE_KERNEL_AUTO;
+    p->block = 0;
+    return SWE_OK;
+}
+
+int swe_set_allocator(swe_alloc_fn alloc, swe_free_fn free_fn, void *ctx)
+{
+    if ((alloc == nullptr) != (free_fn == nullptr)) {
+        swe_set_error("swe_set_allocator: give both functions or neither");
+        return SWE_ERR_ARG;
+    }
+    g_alloc = alloc; g_free = free_fn; g_ctx = ctx;
+    return SWE_OK;
+}
+
+int swe_mesh_create(const double *node_xy, int64_t n_nodes, const int32_t *tri, int64_t n_tri,
+                    const int32_t *bnd_edges, const int32_t *bnd_tag, int64_t n_bnd,
+                    const int32_t *cut_edges, int64_t n_cut, int reorder, swe_mesh **out)
+{
+    if (out) *out = nullptr;
+    try {
+        return swe_mesh_build_host(node_xy, n_nodes, tri, n_tri, bnd_edges, bnd_tag, n_bnd, cut_edges, n_cut,
+                                   reorder, out);
+    } catch (const std::bad_alloc &) {
+        swe_set_error("swe_mesh_create: out of host memory");
+        return SWE_ERR_NOMEM;
+    }
+}
+
+int swe_mesh_destroy(swe_mesh *m)
+{
+    delete m;
+    return SWE_OK;
+}
+
+int swe_mesh_info(const swe_mesh *m, int64_t *n_cells, double *r_min)
+{
+    if (!m) { swe_set_error("swe_mesh_info: NULL mesh"); return SWE_ERR_ARG; }
+    if (n_cells) *n_cells = m->n;
+    if (r_min) *r_min = m->r_min;
+    return SWE_OK;
+}
+
+int swe_mesh_export(const swe_mesh *m, int32_t *perm, int32_t *tri, int32_t *nbr, int32_t *nbr_edge,
+                    int32_t *btag, double *lnx, double *lny, double *area, double *cx, double *cy,
+                    double *rin, double *dx, double *dy)
+{
+    if (!m) { swe_set_error("swe_mesh_export: NULL mesh"); return SWE_ERR_ARG; }
+    const size_t n = (size_t)m->n;
+    auto cp = [](auto *dst, const auto &src) { if (dst) std::memcpy(dst, src.data(), src.size() * sizeof(src[0])); };
+    cp(perm, m->perm); cp(tri, m->tri); cp(nbr, m->nbr); cp(nbr_edge, m->nbr_edge); cp(btag, m->btag);
+    cp(lnx, m->lnx); cp(lny, m->lny); cp(area, m->area); cp(cx, m->cx); cp(cy, m->cy); cp(rin, m->rin);
+    cp(dx, m->dx); cp(dy, m->dy);
+    (void)n;
+    return SWE_OK;
+}
+
+int swe_state_init(const swe_mesh *m, const swe_params *p, const double *h, const double *hu,
+                   const double *hv, const double *z, const double *manning_n, const swe_bc_values *bc,
+                   void *stream, swe_state **out)
+{
+    if (out) *out = nullptr;
+    if (!m || !out || !h || !hu || !hv || !z || !valid_params(p)) {
+        swe_set_error("swe_state_init: bad argument");
+        return SWE_ERR_ARG;
+    }
+    if (bc && ((bc->n_inflow > 0 && !bc->inflow_q) || (bc->n_level > 0 && !bc->level) || bc->n_inflow < 0 ||
+               bc->n_level < 0 || bc->n_inflow > SWE_MAX_GROUPS || bc->n_level > SWE_MAX_GROUPS)) {
+        swe_set_error("swe_state_init: bad boundary values");
+        return SWE_ERR_ARG;
+    }
+    auto *s = new swe_state();
+    s->precision = p->precision;
+    int rc;
+    try {
+        if (p->precision == SWE_FP32) {
+            s->f.reset(new StateT<float>());
+            s->f->p = *p; s->f->stream = (cudaStream_t)stream;
+            rc = state_init<float>(*s->f, m, h, hu, hv, z, manning_n, bc);
+        } else {
+            s->d.reset(new StateT<double>());
+            s->d->p = *p; s->d->stream = (cudaStream_t)stream;
+            rc = state_init<double>(*s->d, m, h, hu, hv, z, manning_n, bc);
+        }
+    } catch (const std::bad_alloc &) {
+        rc = SWE_ERR_NOMEM;
+        swe_set_error("swe_state_init: out of host memory");
+    }
+    if (rc != SWE_OK) { delete s; return rc; }
+    *out = s;
+    return SWE_OK;
+}
+
+int swe_state_destroy(swe_state *s)
+{
+    if (!s) return SWE_OK;
+    cudaStream_t st = s->precision == SWE_FP32 ? s->f->stream : s->d->stream;
+    cudaStreamSynchronize(st);
+    delete s;
+    return SWE_OK;
+}
+
+int swe_set_stream(swe_state *s, void *stream)
+{
+    if (!s) { swe_set_error("swe_set_stream: NULL state"); return SWE_ERR_ARG; }
+    return DISPATCH(s, (S.stream = (cudaStream_t)stream, SWE_OK));
+}
+
+int swe_set_state(swe_state *s, const double *h, const double *hu, const double *hv)
+{
+    if (!s || !h || !hu || !hv) { swe_set_error("swe_set_state: bad argument"); return SWE_ERR_ARG; }
+    return DISPATCH(s, ([&]() -> int {
+        const int64_t n = S.n;
+        CK(cudaMemcpyAsync(S.staging, h, sizeof(double) * n, cudaMemcpyHostToDevice, S.stream));
+        CK(cudaMemcpyAsync(S.staging + n, hu, sizeof(double) * n, cudaMemcpyHostToDevice, S.stream));
+        CK(cudaMemcpyAsync(S.staging + 2 * n, hv, sizeof(double) * n, cudaMemcpyHostToDevice, S.stream));
+        CK(launch_scatter_in(n, S.perm, S.staging, S.h[S.cur], S.hu[S.cur], S.hv[S.cur], S.stream));
+        CK(cudaMemsetAsync(&S.sc->status, 0, sizeof(int), S.stream));
+        return S.init_smax();
+    })());
+}
+
+int swe_step(swe_state *s, int n_steps, double cfl)
+{
+    if (!s || n_steps < 0 || !(cfl > 0.0) || !std::isfinite(cfl)) {
+        swe_set_error("swe_step: bad argument");
+        return SWE_ERR_ARG;
+    }
+    return DISPATCH(s, ([&]() -> int {
+        if (!S.smax_valid) { int rc = S.init_smax(); if (rc) return rc; }
+        for (int q = 0; q < n_steps; q++) {
+            int rc = S.one_step(cfl, nullptr);
+            if (rc) return rc;
+        }
+        return SWE_OK;
+    })());
+}
+
+int swe_step_dt(swe_state *s, const double *dt, int n_steps)
+{
+    if (!s || n_steps < 0 || (n_steps > 0 && !dt)) { swe_set_error("swe_step_dt: bad argument"); return SWE_ERR_ARG; }
+    for (int q = 0; q < n_steps; q++)
+        if (!(dt[q] >= 0.0) || !std::isfinite(dt[q])) { swe_set_error("swe_step_dt: bad time step"); return SWE_ERR_ARG; }
+    return DISPATCH(s, ([&]() -> int {
+        if (n_steps == 0) return SWE_OK;
+        if (S.dtbuf_len < n_steps) {
+            CK(cudaStreamSynchronize(S.stream));
+            for (auto it = S.mem.blocks.begin(); it != S.mem.blocks.end(); ++it)
+                if (it->first == S.dtbuf) { dev_free(it->first, S.stream); S.mem.bytes -= (int64_t)((it->second + 255) & ~size_t(255)); S.mem.blocks.erase(it); break; }
+            S.dtbuf = S.template alloc<double>((size_t)std::max(n_steps, 64));
+            if (!S.dtbuf) { swe_set_error("device allocation failed"); return SWE_ERR_NOMEM; }
+            S.dtbuf_len = std::max(n_steps, 64);
+        }
+        CK(cudaMemcpyAsync(S.dtbuf, dt, sizeof(double) * n_steps, cudaMemcpyHostToDevice, S.stream));
+        if (!S.smax_valid) { int rc = S.init_smax(); if (rc) return rc; }
+        for (int q = 0; q < n_steps; q++) {
+            int rc = S.one_step(1.0, S.dtbuf + q);
+            if (rc) return rc;
+        }
+        // the replayed sequence must stay readable until the kernels ran
+        CK(cudaStreamSynchronize(S.stream));
+        return SWE_OK;
+    })());
+}
+
+int swe_sync(swe_state *s)
+{
+    if (!s) { swe_set_error("swe_sync: NULL state"); return SWE_ERR_ARG; }
+    return DISPATCH(s, S.status());
+}
+
+int swe_get_state(swe_state *s, double *h, double *hu, double *hv)
+{
+    if (!s || !h || !hu || !hv) { swe_set_error("swe_get_state: bad argument"); return SWE_ERR_ARG; }
+    return DISPATCH(s, ([&]() -> int {
+        const int64_t n = S.n;
+        CK(launch_gather_out(n, S.perm, S.h[S.cur], S.hu[S.cur], S.hv[S.cur], S.staging, S.stream));
+        CK(cudaMemcpyAsync(h, S.staging, sizeof(double) * n, cudaMemcpyDeviceToHost, S.stream));
+        CK(cudaMemcpyAsync(hu, S.staging + n, sizeof(double) * n, cudaMemcpyDeviceToHost, S.stream));
+        CK(cudaMemcpyAsync(hv, S.staging + 2 * n, sizeof(double) * n, cudaMemcpyDeviceToHost, S.stream));
+        return S.status();
+    })());
+}
+
+int swe_mass(swe_state *s, double *mass, double *clipped_mass, double *boundary_net_inflow)
+{
+    if (!s) { swe_set_error("swe_mass: NULL state"); return SWE_ERR_ARG; }
+    return DISPATCH(s, ([&]() -> int {
+        double m = 0.0;
+        CK(launch_mass(S.dmesh(), S.h[S.cur], S.mass_part, S.n_part, S.mass_out, S.stream));
+        CK(cudaMemcpyAsync(&m, S.mass_out, sizeof(double), cudaMemcpyDeviceToHost, S.stream));
+        DevScalars d;
+        int rc = S.read_scalars(d);
+        if (rc) return rc;
+        if (mass) *mass = m;
+        if (clipped_mass) *clipped_mass = d.clipped;
+        if (boundary_net_inflow) *boundary_net_inflow = d.bnd_in;
+        return S.status();
+    })());
+}
+
+int swe_time(swe_state *s, double *t, int64_t *steps)
+{
+    if (!s) { swe_set_error("swe_time: NULL state"); return SWE_ERR_ARG; }
+    return DISPATCH(s, ([&]() -> int {
+        DevScalars d;
+        int rc = S.read_scalars(d);
+        if (rc) return rc;
+        if (t) *t = d.t;
+        if (steps) *steps = d.steps;
+        return S.status();
+    })());
+}
+
+int swe_state_info(const swe_state *s, int64_t *device_bytes, int *kernel, int *block)
+{
+    if (!s) { swe_set_error("swe_state_info: NULL state"); return SWE_ERR_ARG; }
+    auto *ms = const_cast<swe_state *>(s);
+    return DISPATCH(ms, ([&]() -> int {
+        if (device_bytes) *device_bytes = S.mem.bytes;
+        if (kernel) *kernel = SWE_KERNEL_SPLIT;
+        if (block) *block = S.block();
+        return SWE_OK;
+    })());
+}
+
+// Ensembles are added with the batched kernel.
+int swe_ensemble_create(swe_state *const *, int, swe_ensemble **out)
+{
+    if (out) *out = nullptr;
+    swe_set_error("swe_ensemble_create: not available in this build");
+    return SWE_ERR_ARG;
+}
+int swe_ensemble_destroy(swe_ensemble *) { return SWE_OK; }
+int swe_ensemble_step(swe_ensemble *, int, double) { return SWE_ERR_ARG; }
+int swe_ensemble_sync(swe_ensemble *) { return SWE_ERR_ARG; }
+
+}  // extern "C"

@@ -1,0 +1,85 @@
+// Device data layout and kernel launch interface (shared by the host API and
+// the CUDA translation unit).  Cells are in the library's (renumbered) order;
+// every per-cell array is structure-of-arrays except the small vector records.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "../../include/swe.h"
+
+// 2- and 4-vectors of the compute type.  The 4-vector of doubles is 32-byte
+// aligned so that one record is one 32-byte sector.
+template <typename T> struct Vec2 { T x, y; };
+template <> struct alignas(8) Vec2<float> { float x, y; };
+template <> struct alignas(16) Vec2<double> { double x, y; };
+template <typename T> struct Vec4 { T x, y, z, w; };
+template <> struct alignas(16) Vec4<float> { float x, y, z, w; };
+template <> struct alignas(32) Vec4<double> { double x, y, z, w; };
+
+// Per-state scalars updated on the device.  smax[] is a ring of three slots
+// holding the bit pattern of a non-negative double (so atomicMax on the bits
+// is a max on the values): step k reads slot k%3, writes slot (k+1)%3 and
+// clears slot (k+2)%3.
+struct DevScalars {
+    unsigned long long smax[3];
+    double t;            // simulated time
+    long long steps;     // steps taken
+    double clipped;      // mass added by clipping negative depths
+    double bnd_in;       // net mass that entered through the boundary
+    int status;          // bit 0 non-finite value, bit 1 no wet cell
+    int pad;
+};
+
+enum { ST_NONFINITE = 1, ST_DRY = 2 };
+enum { MODE_EULER = 0, MODE_STAGE = 1 };
+
+template <typename T> struct DevMesh {
+    int64_t n;
+    const int32_t *nbr;        // [3n] packed neighbour words (see swe_mesh.h)
+    const Vec2<T> *ln;         // [3n] outward normal times edge length
+    const Vec2<T> *dd;         // [3n] centroid offset to the neighbour
+    const T *z;                // [n] bed elevation
+    const T *nman;             // [n] Manning coefficient (may be NULL)
+    const double *area;        // [n] FP64 area (mass totals only)
+};
+
+template <typename T> struct StepArgs {
+    DevMesh<T> m;
+    const T *h, *hu, *hv;       // state in
+    T *ho, *huo, *hvo;          // state out
+    const Vec4<T> *F;           // MUSCL: face values [3n] (eta, u, v, z); WAF: centre values [n] (h, u, v, z)
+    const Vec4<T> *U;           // WAF: upwind means [3n] (h, u, v, -)
+    DevScalars *sc;
+    const double *dtv;          // replayed time step (NULL: CFL rule)
+    int slot_cur, slot_next, slot_clear;
+    int mode;                   // MODE_EULER or MODE_STAGE (first Heun stage or second without averaging)
+    double cfl_rmin;            // cfl * r_min
+    T g, h_eps, r_eps;
+    int waf_limiter;
+    T qlen[SWE_MAX_GROUPS];     // inflow discharge per unit length [m^2/s]
+    T level[SWE_MAX_GROUPS];    // fixed free-surface levels [m]
+};
+
+// Launchers (defined in swe_kernels.cu).  All launches go to `stream`.
+template <typename T>
+cudaError_t launch_prep(int scheme, const StepArgs<T> &a, Vec4<T> *F, Vec4<T> *U, int block, cudaStream_t s);
+template <typename T>
+cudaError_t launch_flux(int scheme, const StepArgs<T> &a, int block, cudaStream_t s);
+template <typename T>
+cudaError_t launch_smax(const StepArgs<T> &a, int slot, int block, cudaStream_t s);
+template <typename T>
+cudaError_t launch_heun_avg(const StepArgs<T> &a, const T *h0, const T *hu0, const T *hv0,
+                            int block, cudaStream_t s);
+template <typename T>
+cudaError_t launch_mass(const DevMesh<T> &m, const T *h, double *partials, int n_partials, double *out,
+                        cudaStream_t s);
+template <typename T>
+cudaError_t launch_scatter_in(int64_t n, const int32_t *perm, const double *src, T *h, T *hu, T *hv,
+                              cudaStream_t s);
+template <typename T>
+cudaError_t launch_gather_out(int64_t n, const int32_t *perm, const T *h, const T *hu, const T *hv,
+                              double *dst, cudaStream_t s);
+template <typename T>
+cudaError_t launch_convert(int64_t n, const double *src, T *dst, cudaStream_t s);
+
+int mass_partials_needed(int64_t n);

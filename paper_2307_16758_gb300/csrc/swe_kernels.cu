@@ -1,0 +1,698 @@
+// CUDA kernels of the explicit finite-volume shallow-water step (sm_103a).
+//
+// One time step (Sec. 5.1 of Delmas & Soulaimani, arXiv 2307.16758):
+//   prep  : per cell, the values each cell shows at the midpoints of its three
+//           edges -- MUSCL: least-squares gradients of (eta, u, v) limited
+//           with Barth-Jespersen; WAF: the cell's primitives and, per edge,
+//           the mean of its two other neighbours (the upwind data of Sec. 5.2.2).
+//   flux  : per cell, for its three edges: hydrostatic reconstruction, the
+//           HLLC (Sec. 5.2.1) or WAF (Sec. 5.2.2) flux in the canonical edge
+//           frame, boundary fluxes (Sec. 5.1), the explicit Euler update,
+//           depth clipping, point-implicit Manning friction, and the wave
+//           speed of the new state reduced (warp shuffle, then one atomicMax
+//           per block) for the next CFL time step.
+// The first-order HLLC path needs no prep: it gathers the neighbour state.
+//
+// Both sides of an interior edge evaluate the same canonical flux (left
+// state = the cell with the lower original id, normal pointing from left to
+// right) from the same inputs, so the mass flux is bitwise antisymmetric.
+#include <cuda_runtime.h>
+
+#include "swe_dev.h"
+
+namespace {
+
+template <typename T> __device__ __forceinline__ T dsqrt(T x) { return sqrt(x); }
+template <typename T> __device__ __forceinline__ T dmax(T a, T b) { return a > b ? a : b; }
+template <typename T> __device__ __forceinline__ T dmin(T a, T b) { return a < b ? a : b; }
+__device__ __forceinline__ float dcbrt(float x) { return cbrtf(x); }
+__device__ __forceinline__ double dcbrt(double x) { return cbrt(x); }
+__device__ __forceinline__ bool dfinite(float x) { return isfinite(x); }
+__device__ __forceinline__ bool dfinite(double x) { return isfinite(x); }
+
+// ---------------------------------------------------------------------------
+// Riemann problem in the rotated frame.  Inputs are the reconstructed depths
+// h*_L, h*_R (after the hydrostatic reconstruction) and the normal (u) and
+// tangential (v) velocities of both sides.  Outputs: the mass flux M, the
+// tangential momentum flux Tt and, for each side s, D_s = F_2 - G_2(U*_s),
+// the normal-momentum flux minus that side's physical flux.  In the star
+// region of HLL (Sec. 5.2.1),
+//   F - G_L = S_L (S_R dU - dG) / (S_R - S_L),  F - G_R = S_R (S_L dU - dG) / (S_R - S_L),
+// which is the printed star flux rearranged so that equal states give an
+// exact zero (well-balancing).
+// ---------------------------------------------------------------------------
+template <typename T> struct Flux { T M, Tt, DL2, DR2; };
+
+template <typename T> struct WafIn {
+    T dtdx;            // dt / |c_R - c_L|
+    T hupL, hupR;      // upwind mean depth of each side
+    T vupL, vupR;      // upwind mean tangential velocity of each side
+    T hcL, hcR;        // cell-centre depths
+};
+
+template <typename T>
+__device__ __forceinline__ T waf_ratio(T r_eps, T upw, T qL, T qR)
+{
+    T loc = qR - qL;
+    T sc = dmax(dmax(fabs(qL), fabs(qR)), T(1));
+    if (fabs(loc) <= r_eps * sc) return T(0);
+    return upw / loc;
+}
+
+// A(r, c) of Sec. 5.2.2 (SUPERBEE), or its phi = 1 / phi = 0 variants.
+template <typename T>
+__device__ __forceinline__ T waf_A(int lim, T r, T c)
+{
+    T ac = fabs(c);
+    if (lim == SWE_WAF_PHI1) return ac;
+    if (lim == SWE_WAF_PHI0) return T(1);
+    if (r <= T(0)) return T(1);
+    if (r <= T(0.5)) return T(1) - T(2) * (T(1) - ac) * r;
+    if (r <= T(1)) return ac;
+    if (r <= T(2)) return T(1) - (T(1) - ac) * r;
+    return T(2) * ac - T(1);
+}
+
+template <typename T, bool WAF>
+__device__ __forceinline__ Flux<T> riemann(T hsL, T uL, T vL, T hsR, T uR, T vR, T g, T h_eps,
+                                           const WafIn<T> &w, int lim, T r_eps)
+{
+    Flux<T> f;
+    const T half = T(0.5);
+    T GL1 = hsL * uL, GL2 = hsL * uL * uL + half * g * hsL * hsL;
+    T GR1 = hsR * uR, GR2 = hsR * uR * uR + half * g * hsR * hsR;
+    T dU1 = hsR - hsL, dU2 = hsR * uR - hsL * uL;
+    T dG1 = GR1 - GL1, dG2 = GR2 - GL2;
+    bool dryL = hsL <= h_eps, dryR = hsR <= h_eps;
+    if (dryL && dryR) {                    // both sides dry: zero numerical flux
+        f.M = T(0); f.Tt = T(0); f.DL2 = -GL2; f.DR2 = -GR2;
+        return f;
+    }
+    T aL = dsqrt(g * hsL), aR = dsqrt(g * hsR);
+    T SL, SR;
+    if (dryL) {                            // dry-bed wave speeds
+        SL = uR - T(2) * aR; SR = uR + aR;
+    } else if (dryR) {
+        SL = uL - aL; SR = uL + T(2) * aL;
+    } else {
+        T h0 = (hsL + hsR) / T(2) - (uR - uL) * (hsL + hsR) / (T(4) * (aR + aL));
+        T hs;
+        if (h0 <= dmin(hsL, hsR)) {        // two rarefactions
+            T br = dmax((aR + aL) / T(2) + (uL - uR) / T(4), T(0));
+            hs = br * br / g;
+        } else {                           // two shocks
+            T gL = dsqrt(g * (h0 + hsL) / (T(2) * h0 * hsL));
+            T gR = dsqrt(g * (h0 + hsR) / (T(2) * h0 * hsR));
+            hs = (hsL * gL + hsR * gR + uL - uR) / (gL + gR);
+        }
+        T pL = hs > hsL ? dsqrt(hs * (hs + hsL) / T(2)) / hsL : T(1);
+        T pR = hs > hsR ? dsqrt(hs * (hs + hsR) / T(2)) / hsR : T(1);
+        SL = uL - aL * pL;
+        SR = uR + aR * pR;
+    }
+    T num = SL * hsR * (uR - SR) - SR * hsL * (uL - SL);
+    T den = hsR * (uR - SR) - hsL * (uL - SL);
+    T Ss = den != T(0) ? num / den : T(0);
+    // HLL (three branches) as differences to G_L and G_R
+    T hL1, hL2, hR2;
+    bool rightgoing = SL >= T(0), leftgoing = !rightgoing && SR <= T(0);
+    if (rightgoing) {
+        hL1 = T(0); hL2 = T(0); hR2 = -dG2;
+    } else if (leftgoing) {
+        hL1 = dG1; hL2 = dG2; hR2 = T(0);
+    } else {
+        T wd = SR - SL;
+        hL1 = SL * (SR * dU1 - dG1) / wd;
+        hL2 = SL * (SR * dU2 - dG2) / wd;
+        hR2 = SR * (SL * dU2 - dG2) / wd;
+    }
+    if (!WAF) {
+        f.M = leftgoing ? GR1 : GL1 + hL1;
+        f.Tt = f.M * (Ss >= T(0) ? vL : vR);      // HLLC: upwind tangential velocity
+        f.DL2 = hL2; f.DR2 = hR2;
+    } else {
+        T cL = SL * w.dtdx, cR = SR * w.dtdx, cs = Ss * w.dtdx;
+        T rL = waf_ratio(r_eps, SL >= T(0) ? w.hcL - w.hupL : w.hupR - w.hcR, w.hcL, w.hcR);
+        T rR = waf_ratio(r_eps, SR >= T(0) ? w.hcL - w.hupL : w.hupR - w.hcR, w.hcL, w.hcR);
+        T rs = waf_ratio(r_eps, Ss >= T(0) ? vL - w.vupL : w.vupR - vR, vL, vR);
+        T sgL = cL >= T(0) ? T(1) : T(-1), sgR = cR >= T(0) ? T(1) : T(-1), sgs = cs >= T(0) ? T(1) : T(-1);
+        T AL = waf_A(lim, rL, cL), AR = waf_A(lim, rR, cR), As = waf_A(lim, rs, cs);
+        T wL = (T(1) + sgL * AL) / T(2);
+        T wLR = (sgR * AR - sgL * AL) / T(2);
+        T wR = (T(1) - sgR * AR) / T(2);
+        T wLs = (T(1) + sgs * As) / T(2), wRs = (T(1) - sgs * As) / T(2);
+        // weighted average of G_L, F_HLL and G_R, as differences to G_L and G_R
+        T DL1 = wLR * hL1 + wR * dG1;
+        f.DL2 = wLR * hL2 + wR * dG2;
+        f.DR2 = -wL * dG2 + wLR * hR2;
+        f.M = GL1 + DL1;
+        f.Tt = (wLs * vL + wRs * vR) * f.M;
+    }
+    return f;
+}
+
+// Offsets from the centroid to the three edge midpoints, from the scaled
+// outward normals: with e_k = (-ln_k.y, ln_k.x) the edge vectors,
+// m_0 - c = (e_2 - e_1)/6, m_1 - c = (e_0 - e_2)/6, m_2 - c = (e_1 - e_0)/6.
+template <typename T>
+__device__ __forceinline__ void midpoint_offsets(const Vec2<T> ln[3], T ox[3], T oy[3])
+{
+    const T s = T(1) / T(6);
+    ox[0] = (-ln[2].y + ln[1].y) * s; oy[0] = (ln[2].x - ln[1].x) * s;
+    ox[1] = (-ln[0].y + ln[2].y) * s; oy[1] = (ln[0].x - ln[2].x) * s;
+    ox[2] = (-ln[1].y + ln[0].y) * s; oy[2] = (ln[1].x - ln[0].x) * s;
+}
+
+template <typename T>
+__device__ __forceinline__ void primitives(T h, T hu, T hv, T h_eps, T &u, T &v)
+{
+    bool wet = h > h_eps;
+    u = wet ? hu / h : T(0);
+    v = wet ? hv / h : T(0);
+}
+
+// ---------------------------------------------------------------------------
+// prep kernels
+// ---------------------------------------------------------------------------
+
+// MUSCL face values: unweighted least squares over the face neighbours, then
+// Barth-Jespersen limiting at the three edge midpoints.  Zero gradient if the
+// cell or a neighbour is dry or the 2x2 system is singular.
+template <typename T>
+__global__ void k_prep_muscl(StepArgs<T> a, Vec4<T> *F)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.m.n) return;
+    const T h_eps = a.h_eps;
+    T hi = a.h[i], zi = a.m.z[i];
+    T ui, vi;
+    primitives(hi, a.hu[i], a.hv[i], h_eps, ui, vi);
+    T qi[3] = {hi + zi, ui, vi};
+    int nb[3];
+    Vec2<T> ln[3], dd[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        nb[k] = a.m.nbr[3 * i + k];
+        ln[k] = a.m.ln[3 * i + k];
+        dd[k] = a.m.dd[3 * i + k];
+    }
+    bool ok = hi > h_eps;
+    int cnt = 0;
+    T qn[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        if (nb[k] >= 0) {
+            int j = nb[k] >> 3;
+            T hj = a.h[j], uj, vj;
+            primitives(hj, a.hu[j], a.hv[j], h_eps, uj, vj);
+            ok = ok && hj > h_eps;
+            qn[k][0] = hj + a.m.z[j]; qn[k][1] = uj; qn[k][2] = vj;
+            cnt++;
+        } else {
+            qn[k][0] = qi[0]; qn[k][1] = qi[1]; qn[k][2] = qi[2];
+        }
+    }
+    T gx[3] = {T(0), T(0), T(0)}, gy[3] = {T(0), T(0), T(0)};
+    T ox[3], oy[3];
+    midpoint_offsets(ln, ox, oy);
+    if (ok && cnt >= 2) {
+        T Mxx = T(0), Mxy = T(0), Myy = T(0);
+        T bx[3] = {T(0), T(0), T(0)}, by[3] = {T(0), T(0), T(0)};
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            if (nb[k] < 0) continue;
+            T dx = dd[k].x, dy = dd[k].y;
+            Mxx += dx * dx; Mxy += dx * dy; Myy += dy * dy;
+#pragma unroll
+            for (int s = 0; s < 3; s++) {
+                T dq = qn[k][s] - qi[s];
+                bx[s] += dx * dq; by[s] += dy * dq;
+            }
+        }
+        T det = Mxx * Myy - Mxy * Mxy, tr = Mxx + Myy;
+        if (det > T(1e-12) * tr * tr) {
+#pragma unroll
+            for (int s = 0; s < 3; s++) {
+                T px = (Myy * bx[s] - Mxy * by[s]) / det;
+                T py = (Mxx * by[s] - Mxy * bx[s]) / det;
+                T qmin = qi[s], qmax = qi[s];
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    if (nb[k] < 0) continue;
+                    qmin = dmin(qmin, qn[k][s]);
+                    qmax = dmax(qmax, qn[k][s]);
+                }
+                T phi = T(1);
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    T d = px * ox[k] + py * oy[k];
+                    T ph = T(1);
+                    if (d > T(0)) ph = (qmax - qi[s]) / d;
+                    else if (d < T(0)) ph = (qmin - qi[s]) / d;
+                    phi = dmin(phi, ph);
+                }
+                gx[s] = phi * px; gy[s] = phi * py;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        Vec4<T> f;
+        f.x = qi[0] + (gx[0] * ox[k] + gy[0] * oy[k]);
+        f.y = qi[1] + (gx[1] * ox[k] + gy[1] * oy[k]);
+        f.z = qi[2] + (gx[2] * ox[k] + gy[2] * oy[k]);
+        f.w = zi;
+        F[3 * i + k] = f;
+    }
+}
+
+// WAF: centre primitives P[i] = (h, u, v, z) and, per edge k, the mean of
+// (h, u, v) over the neighbours across edges k+1 and k+2 (a missing neighbour
+// stands in with the cell itself).
+template <typename T>
+__global__ void k_prep_waf(StepArgs<T> a, Vec4<T> *P, Vec4<T> *U)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.m.n) return;
+    T hi = a.h[i], ui, vi;
+    primitives(hi, a.hu[i], a.hv[i], a.h_eps, ui, vi);
+    T qh[3], qu[3], qv[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        int nb = a.m.nbr[3 * i + k];
+        if (nb >= 0) {
+            int j = nb >> 3;
+            qh[k] = a.h[j];
+            primitives(qh[k], a.hu[j], a.hv[j], a.h_eps, qu[k], qv[k]);
+        } else {
+            qh[k] = hi; qu[k] = ui; qv[k] = vi;
+        }
+    }
+    Vec4<T> p;
+    p.x = hi; p.y = ui; p.z = vi; p.w = a.m.z[i];
+    P[i] = p;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+        Vec4<T> u;
+        u.x = (qh[k1] + qh[k2]) / T(2);
+        u.y = (qu[k1] + qu[k2]) / T(2);
+        u.z = (qv[k1] + qv[k2]) / T(2);
+        u.w = T(0);
+        U[3 * i + k] = u;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// block reductions
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T warp_max(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = dmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Max of s, sums of c1 and c2 over the block; thread 0 publishes them.
+template <typename T>
+__device__ __forceinline__ void block_publish(T s, double c1, double c2, DevScalars *sc, int slot_next,
+                                              bool want_max, double wsum)
+{
+    __shared__ double sh_s[32], sh_c1[32], sh_c2[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    double sd = (double)warp_max(s);
+    c1 = warp_sum(c1);
+    c2 = warp_sum(c2);
+    if (lane == 0) { sh_s[wid] = sd; sh_c1[wid] = c1; sh_c2[wid] = c2; }
+    __syncthreads();
+    if (wid == 0) {
+        sd = lane < nw ? sh_s[lane] : 0.0;
+        c1 = lane < nw ? sh_c1[lane] : 0.0;
+        c2 = lane < nw ? sh_c2[lane] : 0.0;
+        sd = warp_max(sd);
+        c1 = warp_sum(c1);
+        c2 = warp_sum(c2);
+        if (lane == 0) {
+            if (want_max && sd > 0.0) atomicMax(&sc->smax[slot_next], (unsigned long long)__double_as_longlong(sd));
+            if (c1 != 0.0) atomicAdd(&sc->clipped, wsum * c1);
+            if (c2 != 0.0) atomicAdd(&sc->bnd_in, wsum * c2);
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T step_dt(const StepArgs<T> &a, bool *dry)
+{
+    if (a.dtv) { *dry = false; return (T)a.dtv[0]; }
+    double sm = __longlong_as_double((long long)a.sc->smax[a.slot_cur]);
+    *dry = !(sm > 0.0);
+    if (*dry) return T(0);
+    return (T)a.cfl_rmin / (T)sm;
+}
+
+// ---------------------------------------------------------------------------
+// flux + update kernel
+// ---------------------------------------------------------------------------
+template <typename T, int SCHEME>
+__global__ void k_flux(StepArgs<T> a)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = i < a.m.n;
+    bool dry;
+    const T dt = step_dt(a, &dry);
+    const T g = a.g, h_eps = a.h_eps, half = T(0.5);
+    T smax = T(0);
+    double clip = 0.0, bsum = 0.0;
+    if (valid) {
+        const T hi = a.h[i], hui = a.hu[i], hvi = a.hv[i], zi = a.m.z[i];
+        int nb[3];
+        Vec2<T> ln[3];
+#pragma unroll
+        for (int k = 0; k < 3; k++) { nb[k] = a.m.nbr[3 * i + k]; ln[k] = a.m.ln[3 * i + k]; }
+        // own centre values
+        T ui, vi;
+        primitives(hi, hui, hvi, h_eps, ui, vi);
+        T R0 = T(0), R1 = T(0), R2 = T(0), bs = T(0);
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const T lx = ln[k].x, ly = ln[k].y;
+            const T L = dsqrt(lx * lx + ly * ly);
+            const T nx = lx / L, ny = ly / L;
+            // own face values (eta, u, v)
+            T ef, uf, vf;
+            if (SCHEME == SWE_SCHEME_MUSCL) {
+                Vec4<T> f = a.F[3 * i + k];
+                ef = f.x; uf = f.y; vf = f.z;
+            } else {
+                ef = hi + zi; uf = ui; vf = vi;
+            }
+            const T hf = dmax(ef - zi, T(0));
+            const T hyd = half * g * (hf - hi) * (hf + hi);
+            const int w = nb[k];
+            if (w >= 0) {
+                const int j = w >> 3, kj = (w >> 1) & 3;
+                const bool own = w & 1;
+                T ej, uj, vj, zj, hcj = T(0);
+                Vec4<T> Uj;
+                if (SCHEME == SWE_SCHEME_MUSCL) {
+                    Vec4<T> f = a.F[3 * j + kj];
+                    ej = f.x; uj = f.y; vj = f.z; zj = f.w;
+                } else if (SCHEME == SWE_SCHEME_WAF) {
+                    Vec4<T> p = a.F[j];
+                    hcj = p.x; uj = p.y; vj = p.z; zj = p.w;
+                    ej = hcj + zj;
+                    Uj = a.U[3 * j + kj];
+                } else {
+                    T hj = a.h[j];
+                    zj = a.m.z[j];
+                    primitives(hj, a.hu[j], a.hv[j], h_eps, uj, vj);
+                    ej = hj + zj;
+                }
+                // canonical orientation: side A is the owner of the edge
+                const T cnx = own ? nx : -nx, cny = own ? ny : -ny;
+                const T eA = own ? ef : ej, eB = own ? ej : ef;
+                const T uAx = own ? uf : uj, uAy = own ? vf : vj;
+                const T uBx = own ? uj : uf, uBy = own ? vj : vf;
+                const T zf = dmax(zi, zj);
+                const T hsA = dmax(eA - zf, T(0)), hsB = dmax(eB - zf, T(0));
+                const T unA = uAx * cnx + uAy * cny, vtA = -uAx * cny + uAy * cnx;
+                const T unB = uBx * cnx + uBy * cny, vtB = -uBx * cny + uBy * cnx;
+                Flux<T> fl;
+                if (SCHEME == SWE_SCHEME_WAF) {
+                    const Vec4<T> Ui = a.U[3 * i + k];
+                    const Vec2<T> d = a.m.dd[3 * i + k];
+                    WafIn<T> wi;
+                    wi.dtdx = dt / dsqrt(d.x * d.x + d.y * d.y);
+                    const Vec4<T> &UA = own ? Ui : Uj;
+                    const Vec4<T> &UB = own ? Uj : Ui;
+                    wi.hupL = UA.x; wi.hupR = UB.x;
+                    wi.vupL = -UA.y * cny + UA.z * cnx;
+                    wi.vupR = -UB.y * cny + UB.z * cnx;
+                    wi.hcL = own ? hi : hcj; wi.hcR = own ? hcj : hi;
+                    fl = riemann<T, true>(hsA, unA, vtA, hsB, unB, vtB, g, h_eps, wi, a.waf_limiter, a.r_eps);
+                } else {
+                    WafIn<T> wi{};
+                    fl = riemann<T, false>(hsA, unA, vtA, hsB, unB, vtB, g, h_eps, wi, 0, a.r_eps);
+                }
+                const T P = (own ? hsA * unA * unA + fl.DL2 : hsB * unB * unB + fl.DR2) + hyd;
+                const T sM = own ? fl.M : -fl.M;
+                R0 += L * sM;
+                R1 += L * (P * nx - fl.Tt * ny);
+                R2 += L * (P * ny + fl.Tt * nx);
+            } else {
+                // boundary edge, normal outward (Sec. 5.1)
+                const int tag = -1 - w, kind = tag & 3, grp = tag >> 2;
+                const T un = uf * nx + vf * ny, vt = -uf * ny + vf * nx;
+                T M, P, Tt;
+                if (kind == SWE_WALL) {
+                    M = T(0); P = hyd; Tt = T(0);
+                } else if (kind == SWE_OPEN) {
+                    M = hf * un; P = hf * un * un + hyd; Tt = M * vt;
+                } else if (kind == SWE_INFLOW) {
+                    const T q = a.qlen[grp];
+                    M = -q; P = (hf > h_eps ? q * q / hf : T(0)) + hyd; Tt = T(0);
+                } else {
+                    const T hg = dmax(a.level[grp] - zi, T(0));
+                    WafIn<T> wi{};
+                    Flux<T> fl = riemann<T, false>(hf, un, vt, hg, un, vt, g, h_eps, wi, 0, a.r_eps);
+                    M = fl.M; P = hf * un * un + fl.DL2 + hyd; Tt = fl.Tt;
+                }
+                R0 += L * M;
+                R1 += L * (P * nx - Tt * ny);
+                R2 += L * (P * ny + Tt * nx);
+                bs -= L * M;
+            }
+        }
+        // explicit Euler update (area from the scaled normals: |e_0 x e_1| / 2)
+        const T area = half * (ln[0].x * ln[1].y - ln[0].y * ln[1].x);
+        const T r = dt / area;
+        T hn = hi - r * R0, hun = hui - r * R1, hvn = hvi - r * R2;
+        if (hn < T(0)) { clip = -(double)hn * (double)area; hn = T(0); }
+        if (hn <= h_eps) {
+            hun = T(0); hvn = T(0);
+        } else if (a.m.nman) {
+            const T nm = a.m.nman[i];
+            if (nm > T(0)) {            // point-implicit Manning friction
+                const T sp = dsqrt(hun * hun + hvn * hvn) / hn;
+                const T fr = T(1) + dt * g * nm * nm * sp / (hn * dcbrt(hn));
+                hun /= fr; hvn /= fr;
+            }
+        }
+        a.ho[i] = hn; a.huo[i] = hun; a.hvo[i] = hvn;
+        if (!(dfinite(hn) && dfinite(hun) && dfinite(hvn))) atomicOr(&a.sc->status, ST_NONFINITE);
+        if (hn > h_eps) {
+            const T u = hun / hn, v = hvn / hn;
+            smax = dsqrt(g * hn) + dsqrt(u * u + v * v);
+        }
+        bsum = (double)bs * (double)dt;
+    }
+    const bool euler = a.mode == MODE_EULER;
+    block_publish<T>(smax, clip, bsum, a.sc, a.slot_next, euler, euler ? 1.0 : 0.5);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (dry) atomicOr(&a.sc->status, ST_DRY);
+        if (euler) {
+            a.sc->t += (double)dt;
+            a.sc->steps += 1;
+            a.sc->smax[a.slot_clear] = 0ULL;
+        }
+    }
+}
+
+// Wave speed of the current state into slot `slot` (CFL rule of Sec. 5.1).
+template <typename T>
+__global__ void k_smax(StepArgs<T> a, int slot)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    T s = T(0);
+    if (i < a.m.n) {
+        T h = a.h[i];
+        if (h > a.h_eps) {
+            T u = a.hu[i] / h, v = a.hv[i] / h;
+            s = dsqrt(a.g * h) + dsqrt(u * u + v * v);
+        }
+    }
+    block_publish<T>(s, 0.0, 0.0, a.sc, slot, true, 1.0);
+}
+
+// Heun: U^{n+1} = (U^n + U2) / 2 with U2 = E(E(U^n)); then the wave speed.
+template <typename T>
+__global__ void k_heun_avg(StepArgs<T> a, const T *h0, const T *hu0, const T *hv0)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    T s = T(0);
+    if (i < a.m.n) {
+        T h = T(0.5) * (h0[i] + a.h[i]), hu = T(0.5) * (hu0[i] + a.hu[i]), hv = T(0.5) * (hv0[i] + a.hv[i]);
+        a.ho[i] = h; a.huo[i] = hu; a.hvo[i] = hv;
+        if (h > a.h_eps) {
+            T u = hu / h, v = hv / h;
+            s = dsqrt(a.g * h) + dsqrt(u * u + v * v);
+        }
+    }
+    block_publish<T>(s, 0.0, 0.0, a.sc, a.slot_next, true, 1.0);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        bool dry;
+        T dt = step_dt(a, &dry);
+        a.sc->t += (double)dt;
+        a.sc->steps += 1;
+        a.sc->smax[a.slot_clear] = 0ULL;
+    }
+}
+
+// Mass: per-block FP64 partial sums in a fixed tree order, then one block
+// adds the partials in a fixed order (deterministic).
+constexpr int MASS_BLOCK = 256;
+constexpr int MASS_ITEMS = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(MASS_BLOCK) k_mass_partial(DevMesh<T> m, const T *h, double *partials)
+{
+    __shared__ double sh[MASS_BLOCK];
+    const int64_t base = (int64_t)blockIdx.x * MASS_BLOCK * MASS_ITEMS;
+    double s = 0.0;
+    for (int q = 0; q < MASS_ITEMS; q++) {
+        int64_t i = base + (int64_t)q * MASS_BLOCK + threadIdx.x;
+        if (i < m.n) s += m.area[i] * (double)h[i];
+    }
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = MASS_BLOCK / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
+}
+
+__global__ void __launch_bounds__(MASS_BLOCK) k_mass_final(const double *partials, int n, double *out)
+{
+    __shared__ double sh[MASS_BLOCK];
+    double s = 0.0;
+    for (int q = threadIdx.x; q < n; q += MASS_BLOCK) s += partials[q];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = MASS_BLOCK / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = sh[0];
+}
+
+// Original-order FP64 host layout <-> renumbered device state.
+template <typename T>
+__global__ void k_scatter_in(int64_t n, const int32_t *perm, const double *src, T *h, T *hu, T *hv)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t o = perm[i];
+    h[i] = (T)src[o]; hu[i] = (T)src[n + o]; hv[i] = (T)src[2 * n + o];
+}
+
+template <typename T>
+__global__ void k_gather_out(int64_t n, const int32_t *perm, const T *h, const T *hu, const T *hv, double *dst)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t o = perm[i];
+    dst[o] = (double)h[i]; dst[n + o] = (double)hu[i]; dst[2 * n + o] = (double)hv[i];
+}
+
+template <typename T>
+__global__ void k_convert(int64_t n, const double *src, T *dst)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = (T)src[i];
+}
+
+inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
+
+}  // namespace
+
+int mass_partials_needed(int64_t n) { return (int)((n + MASS_BLOCK * MASS_ITEMS - 1) / (MASS_BLOCK * MASS_ITEMS)); }
+
+template <typename T>
+cudaError_t launch_prep(int scheme, const StepArgs<T> &a, Vec4<T> *F, Vec4<T> *U, int block, cudaStream_t s)
+{
+    if (scheme == SWE_SCHEME_MUSCL) k_prep_muscl<T><<<grid_for(a.m.n, block), block, 0, s>>>(a, F);
+    else if (scheme == SWE_SCHEME_WAF) k_prep_waf<T><<<grid_for(a.m.n, block), block, 0, s>>>(a, F, U);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_flux(int scheme, const StepArgs<T> &a, int block, cudaStream_t s)
+{
+    unsigned gr = grid_for(a.m.n, block);
+    if (scheme == SWE_SCHEME_MUSCL) k_flux<T, SWE_SCHEME_MUSCL><<<gr, block, 0, s>>>(a);
+    else if (scheme == SWE_SCHEME_WAF) k_flux<T, SWE_SCHEME_WAF><<<gr, block, 0, s>>>(a);
+    else k_flux<T, SWE_SCHEME_HLLC><<<gr, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_smax(const StepArgs<T> &a, int slot, int block, cudaStream_t s)
+{
+    k_smax<T><<<grid_for(a.m.n, block), block, 0, s>>>(a, slot);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_heun_avg(const StepArgs<T> &a, const T *h0, const T *hu0, const T *hv0, int block,
+                            cudaStream_t s)
+{
+    k_heun_avg<T><<<grid_for(a.m.n, block), block, 0, s>>>(a, h0, hu0, hv0);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_mass(const DevMesh<T> &m, const T *h, double *partials, int n_partials, double *out,
+                        cudaStream_t s)
+{
+    k_mass_partial<T><<<n_partials, MASS_BLOCK, 0, s>>>(m, h, partials);
+    k_mass_final<<<1, MASS_BLOCK, 0, s>>>(partials, n_partials, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_scatter_in(int64_t n, const int32_t *perm, const double *src, T *h, T *hu, T *hv,
+                              cudaStream_t s)
+{
+    k_scatter_in<T><<<grid_for(n, 256), 256, 0, s>>>(n, perm, src, h, hu, hv);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_gather_out(int64_t n, const int32_t *perm, const T *h, const T *hu, const T *hv,
+                              double *dst, cudaStream_t s)
+{
+    k_gather_out<T><<<grid_for(n, 256), 256, 0, s>>>(n, perm, h, hu, hv, dst);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_convert(int64_t n, const double *src, T *dst, cudaStream_t s)
+{
+    k_convert<T><<<grid_for(n, 256), 256, 0, s>>>(n, src, dst);
+    return cudaGetLastError();
+}
+
+#define SWE_INSTANTIATE(T)                                                                                 \
+    template cudaError_t launch_prep<T>(int, const StepArgs<T> &, Vec4<T> *, Vec4<T> *, int, cudaStream_t); \
+    template cudaError_t launch_flux<T>(int, const StepArgs<T> &, int, cudaStream_t);                      \
+    template cudaError_t launch_smax<T>(const StepArgs<T> &, int, int, cudaStream_t);                      \
+    template cudaError_t launch_heun_avg<T>(const StepArgs<T> &, const T *, const T *, const T *, int,     \
+                                            cudaStream_t);                                                 \
+    template cudaError_t launch_mass<T>(const DevMesh<T> &, const T *, double *, int, double *,           \
+                                        cudaStream_t);                                                     \
+    template cudaError_t launch_scatter_in<T>(int64_t, const int32_t *, const double *, T *, T *, T *,     \
+                                              cudaStream_t);                                               \
+    template cudaError_t launch_gather_out<T>(int64_t, const int32_t *, const T *, const T *, const T *,   \
+                                              double *, cudaStream_t);                                     \
+    template cudaError_t launch_convert<T>(int64_t, const double *, T *, cudaStream_t);
+
+SWE_INSTANTIATE(float)
+SWE_INSTANTIATE(double)

@@ -1,0 +1,206 @@
+"""CUDA path against the FP64 oracle, element by element, through the C ABI.
+
+FP64: relative max error <= 1e-12 after one step and <= 1e-9 after 100 steps
+(the oracle and the kernels evaluate the same algorithm; they differ only in
+rounding order and fused multiply-adds).  FP32: relative L1 error of h and the
+mass drift are bounded (see each test).  Integer work (the mesh) is compared
+bit for bit in test_abi.py.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_common import rel_l1, rel_max, run_gpu, run_oracle, state_errors
+from paper_2307_16758_gb300 import build as B
+from paper_2307_16758_gb300 import swe
+from paper_2307_16758_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    B.build()
+    swe.load_library()
+
+
+def _pdb(nx=90, ny=44, seed=11):
+    return W.partial_dam_break(nx=nx, ny=ny, spacing=1.0, n_gauss=30, seed=seed)
+
+
+def _river(nx=100, ny=38, seed=21, q=1500.0):
+    return W.river(nx=nx, ny=ny, seed=seed, q_in=q)
+
+
+# ---- FP64 parity ------------------------------------------------------------
+
+@pytest.mark.parametrize("scheme", ["hllc", "muscl", "waf"])
+def test_fp64_one_step_dam_break_2000_cells(scheme):
+    w = W.dam_break_1d()                        # 2000 cells: 7 full blocks and a ragged tail
+    g = run_gpu(w, scheme, steps=1)
+    o = run_oracle(w, scheme, steps=1)
+    assert max(state_errors(g, o)) <= 1e-12
+    assert math.isclose(g["t"], o["t"], rel_tol=1e-15)
+
+
+def test_fp64_hllc_config1_200_steps_cfl():
+    """First-order HLLC, 2000 cells, CFL 0.9, 200 steps."""
+    w = W.dam_break_1d()
+    g100, o100 = run_gpu(w, "hllc", steps=100), run_oracle(w, "hllc", steps=100)
+    assert max(state_errors(g100, o100)) <= 1e-9
+    assert math.isclose(g100["t"], o100["t"], rel_tol=1e-12)
+    g, o = run_gpu(w, "hllc", steps=200), run_oracle(w, "hllc", steps=200)
+    assert max(state_errors(g, o)) <= 1e-9
+    assert g["steps"] == 200
+
+
+@pytest.mark.parametrize("scheme", ["hllc", "muscl", "waf"])
+def test_fp64_partial_dam_break(scheme):
+    """Jittered mesh, Gaussian bed, ~30 % dry, breach, Manning: 1 and 100 steps."""
+    w = _pdb()
+    g1, o1 = run_gpu(w, scheme, steps=1), run_oracle(w, scheme, steps=1)
+    assert max(state_errors(g1, o1)) <= 1e-12
+    o = run_oracle(w, scheme, steps=100)
+    g = run_gpu(w, scheme, dt=o["dts"])
+    errs = state_errors(g, o)
+    assert max(errs) <= 1e-9, errs
+    gc = run_gpu(w, scheme, steps=100)
+    assert math.isclose(gc["t"], o["t"], rel_tol=1e-9)
+
+
+@pytest.mark.parametrize("scheme", ["hllc", "muscl"])
+def test_fp64_river_inflow_level_friction(scheme):
+    w = _river()
+    o = run_oracle(w, scheme, steps=100)
+    g = run_gpu(w, scheme, dt=o["dts"])
+    assert max(state_errors(g, o)) <= 1e-9
+    assert math.isclose(g["bnd_in"], o["bnd_in"], rel_tol=1e-9)
+
+
+def test_fp64_heun():
+    w = _pdb(60, 30)
+    o = run_oracle(w, "muscl", steps=40, time_scheme="heun")
+    g = run_gpu(w, "muscl", dt=o["dts"], time_scheme="heun")
+    assert max(state_errors(g, o)) <= 1e-9
+
+
+@pytest.mark.parametrize("block", [64, 128, 512])
+def test_fp64_block_sizes(block):
+    w = _pdb(33, 17)
+    o = run_oracle(w, "muscl", steps=10)
+    g = run_gpu(w, "muscl", dt=o["dts"], block=block)
+    assert max(state_errors(g, o)) <= 1e-11
+
+
+# ---- invariants on the GPU ----------------------------------------------------
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("scheme", ["hllc", "muscl", "waf"])
+def test_lake_at_rest_bitwise(precision, scheme):
+    w = W.partial_dam_break(nx=80, ny=40, spacing=1.0, n_gauss=40, breach=False, seed=9)
+    w.bnd_tag = np.full(len(w.bnd_edges), W.tag(W.LEVEL), np.int32)
+    w.level = np.array([2.0])
+    g = run_gpu(w, scheme, precision, steps=1000)
+    assert np.array_equal(g["h"], w.h)
+    assert not g["hu"].any() and not g["hv"].any()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("fp32", 1e-6)])
+@pytest.mark.parametrize("scheme", ["hllc", "muscl", "waf"])
+def test_mass_conservation(precision, tol, scheme):
+    w = _pdb()
+    m0 = run_oracle(w, scheme, steps=0)["mass0"]
+    g = run_gpu(w, scheme, precision, steps=300)
+    assert abs(g["mass"] - m0 - g["clipped"]) <= tol * m0
+
+
+def test_mass_budget_with_inflow():
+    w = _river()
+    o = run_oracle(w, "muscl", steps=0)
+    g = run_gpu(w, "muscl", "fp64", steps=300)
+    assert abs(g["mass"] - o["mass0"] - g["clipped"] - g["bnd_in"]) <= 1e-12 * o["mass0"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_renumbering_is_bitwise_invisible(precision):
+    """Morton, RCM and the original order give the same bits (cf. Sec. 5.3.1)."""
+    w = _pdb(50, 24)
+    ref = run_gpu(w, "muscl", precision, steps=60, reorder="none")
+    for r in ("morton", "rcm"):
+        g = run_gpu(w, "muscl", precision, steps=60, reorder=r)
+        for k in ("h", "hu", "hv"):
+            assert np.array_equal(g[k], ref[k]), (r, k)
+        assert g["t"] == ref["t"]
+
+
+# ---- FP32 against the FP64 oracle ----------------------------------------------
+
+@pytest.mark.parametrize("scheme", ["muscl", "waf", "hllc"])
+def test_fp32_error_against_oracle(scheme):
+    """FP32 state and fluxes (FP64 mass and time): relative L1 of h after 1000
+    replayed steps <= 1e-4, mass drift <= 1e-6 (same h_eps on both sides)."""
+    w = _river(80, 30)
+    o = run_oracle(w, scheme, steps=1000, h_eps=1e-4, r_eps=1e-6)
+    g = run_gpu(w, scheme, "fp32", dt=o["dts"])
+    assert rel_l1(g["h"], o["h"]) <= 1e-4
+    drift = abs(g["mass"] - o["mass0"] - g["clipped"] - g["bnd_in"]) / o["mass0"]
+    assert drift <= 1e-6
+
+
+# ---- edge cases and error paths ------------------------------------------------
+
+def test_single_triangle_and_tiny_meshes():
+    nodes = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
+    n = 1
+    w = W.Workload("one", nodes, np.array([[0, 1, 2]], np.int32), np.zeros((0, 2), np.int32),
+                   np.zeros(0, np.int32), np.zeros((0, 2), np.int32), np.zeros(n), np.zeros(n),
+                   np.ones(n), np.zeros(n), np.zeros(n))
+    g = run_gpu(w, "muscl", steps=5)
+    assert np.array_equal(g["h"], [1.0]) and g["hu"][0] == 0 and g["hv"][0] == 0
+    for nx in (1, 2, 129):                       # 2, 4 and 258 cells (one block plus a tail)
+        w2 = W.dam_break_1d(nx, 1, float(nx), 1.0, 1.0, 0.5, x_dam=nx / 2.0 + 0.1)
+        o = run_oracle(w2, "muscl", steps=3)
+        g2 = run_gpu(w2, "muscl", dt=o["dts"])
+        assert max(state_errors(g2, o)) <= 1e-12
+
+
+def test_non_finite_input_is_reported():
+    w = W.dam_break_1d(20, 2, 20.0, 2.0)
+    w.h = w.h.copy()
+    w.h[3] = np.nan
+    p = swe.swe_params_default("hllc", "fp64")
+    m = swe.Mesh.from_workload(w)
+    s = swe.State.from_workload(m, p, w)
+    s.step_dt([0.01])
+    with pytest.raises(swe.SweError) as e:
+        s.sync()
+    assert e.value.code == -5
+
+
+def test_all_dry_domain_is_reported():
+    w = W.dam_break_1d(20, 2, 20.0, 2.0, 0.0, 0.0)
+    p = swe.swe_params_default("hllc", "fp64")
+    m = swe.Mesh.from_workload(w)
+    s = swe.State.from_workload(m, p, w)
+    s.step(1, 0.9)
+    with pytest.raises(swe.SweError) as e:
+        s.sync()
+    assert e.value.code == -4
+
+
+def test_set_state_round_trip_and_resume():
+    w = _pdb(40, 20)
+    p = swe.swe_params_default("muscl", "fp64")
+    m = swe.Mesh.from_workload(w)
+    a = swe.State.from_workload(m, p, w)
+    a.step(30, 0.9)
+    mid = a.get_state()
+    a.step(30, 0.9)
+    end_a = a.get_state()
+    b = swe.State.from_workload(m, p, w)
+    b.set_state(*mid)
+    b.step(30, 0.9)
+    end_b = b.get_state()
+    for x, y in zip(end_a, end_b):
+        assert np.array_equal(x, y)

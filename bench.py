@@ -1,0 +1,423 @@
+#!/usr/bin/env python
+"""Benchmark of the explicit shallow-water finite-volume step on one GB300.
+
+Workload: the synthetic 13,004,160-triangle river mesh (meandering channel in
+a 40 km x 15 km floodplain, ~50 % dry, inflow 8000 m^3/s, fixed downstream
+level, Manning friction, Morton order), MUSCL-HLLC, FP32 state and fluxes with
+FP64 mass and time.  One "step" is one explicit time step of the whole mesh,
+so the metric is cell-updates/s = cells x steps / time.
+
+Printed on one JSON line (rank 0): the device-timed value (inputs resident,
+CUDA events on the library's stream), the end-to-end value through the C ABI
+with host buffers, the roofline of the dominant kernel against the measured
+HBM peak, the FP64 GPU path and the FP32-vs-FP64 error at matched time, the
+FP64 oracle timed on the host cores (cpu_baseline), and the SM clocks sampled
+during the timed region.
+
+--impl reference times the FP64 CPU oracle instead (the reference arm).
+With torchrun (N > 1) every rank advances its own independent river (a
+replica with its own seed): no data-path collective; value = all cells x
+steps / max over ranks of the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s MUSCL-HLLC 13M tri, FP32 vs FP64 at stated error; % HBM peak"
+UNIT = "cell-updates/s"
+RIVER_GRID = (4160, 1563)
+SEED = 20230733
+
+# Algorithmic bytes per cell and launch: every array element the kernel must
+# touch counted once (neighbour gathers assumed to hit in cache).
+#   split MUSCL prep : state 3 + z + nbr(3 int) + scaled normals 6 + centroid offsets 6, writes 12 face values
+#   split MUSCL flux : state 3 + z + nbr + normals 6 + own face values 12 + Manning n, writes state 3
+#   fused MUSCL      : state 3 + z + nbr + normals 6 + offsets 6 + n, writes state 3 (the whole step)
+#   HLLC flux        : state 3 + z + nbr + normals 6 + n, writes state 3
+def algo_bytes(kind: str, scheme: str, precision: str) -> int:
+    f = 4 if precision == "fp32" else 8
+    nbr = 12
+    if scheme == "muscl" and kind == "prep":
+        return 3 * f + f + nbr + 6 * f + 6 * f + 12 * f
+    if scheme == "muscl" and kind == "flux":
+        return 3 * f + f + nbr + 6 * f + 12 * f + f + 3 * f
+    if kind == "fused":
+        return 3 * f + f + nbr + 6 * f + 6 * f + f + 3 * f
+    if scheme == "hllc" and kind == "flux":
+        return 3 * f + f + nbr + 6 * f + f + 3 * f
+    if scheme == "waf" and kind == "prep":
+        return 3 * f + nbr + 3 * f + f + 4 * f + 12 * f      # reads nbr state, writes P and U
+    if scheme == "waf" and kind == "flux":
+        return 3 * f + f + nbr + 6 * f + 6 * f + 4 * f + 12 * f + f + 3 * f
+    return 0
+
+
+def step_bytes_ideal(scheme: str, precision: str) -> int:
+    """Bytes per cell-update of the whole step if every array is read or written once."""
+    return algo_bytes("fused" if scheme != "hllc" else "flux", scheme, precision)
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2307_16758_gb300", "csrc", "*"))):
+        h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel_key: str, cells: int):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current kernels."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path)).get(kernel_key)
+    if not d or d.get("source_sha") != kernel_source_sha():
+        return None
+    return float(d["dram_bytes_per_cell"]) * cells
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def stop(self, t0, t1):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = [l for (t, l) in self.lines if t0 - 0.05 <= t <= t1 + 0.15] or [l for (_, l) in self.lines[-3:]]
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            f = [x.strip() for x in r.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def river_workload(rank: int, scale: float):
+    from paper_2307_16758_gb300 import workloads as W
+    nx, ny = RIVER_GRID
+    if scale != 1.0:
+        nx, ny = W.river_grid_for_cells(int(2 * nx * ny * scale))
+    return W.river(nx, ny, seed=SEED + 1000 * rank), (nx, ny)
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle as it stands
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2307_16758_gb300 import workloads as W
+    oracle.build()
+    cells_sample = 200_000
+    nx, ny = W.river_grid_for_cells(cells_sample)
+    w = W.river(nx, ny, seed=SEED)
+    om = oracle.Mesh(w.nodes, w.tris, w.bnd_edges, w.bnd_tag)
+    cores = os.cpu_count() or 1
+    o = oracle.opts("muscl", threads=cores)
+    state = (w.h, w.hu, w.hv)
+    t_steps = []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        h, hu, hv, dts, d = oracle.run(om, o, w.z, w.nman, *state, 1, q_in=w.q_in, level=w.level)
+        t1 = time.perf_counter()
+        state = (h, hu, hv)
+        if s >= args.warmup:
+            t_steps.append(t1 - t0)
+    el = sum(t_steps)
+    value = om.n * len(t_steps) / el
+    sample = (f"one FP64 MUSCL-HLLC Euler step per bench step on the river generator at {om.n} cells "
+              f"({nx}x{ny} grid, same recipe as the 13M workload), OpenMP over cells")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / len(t_steps),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "river-13M MUSCL-HLLC (oracle on a bounded sample)", "cells": om.n,
+                   "scheme": "muscl", "precision": "fp64"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def rel_l1(a, b):
+    return float(np.abs(a - b).sum() / max(np.abs(b).sum(), 1e-300))
+
+
+def rel_inf(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def run_gpu(args):
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    from paper_2307_16758_gb300 import swe
+
+    if rank == 0 or ws == 1:
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    swe.load_library()
+    stream = torch.cuda.current_stream()
+
+    w, grid = river_workload(rank, args.scale)
+    mesh = swe.Mesh.from_workload(w, "morton")
+    n = mesh.n
+    p32 = swe.swe_params_default("muscl", "fp32", kernel=args.kernel)
+    st = swe.State.from_workload(mesh, p32, w)
+    dev_bytes, kernel_used, block = st.info()
+    kname = {1: "split", 2: "fused"}.get(kernel_used, str(kernel_used))
+
+    # warm-up, then the timed region (production path, inputs resident in HBM)
+    st.step(args.warmup, args.cfl)
+    st.sync()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tw0 = time.time()
+    e0.record(stream)
+    st.step(args.steps, args.cfl)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    tw1 = time.time()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop(tw0, tw1)
+    ms = e0.elapsed_time(e1)
+    st.sync()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * n * args.steps / (ms / 1e3)
+
+    # per-kernel device time over a second timed region of the same length
+    st.profile_begin()
+    st.step(args.steps, args.cfl)
+    prof = st.profile_end()
+    launches = sum(c for _, c in prof.values())
+    dom = max(prof, key=lambda k: prof[k][0])
+    dom_ms = prof[dom][0] / prof[dom][1]
+    bytes_launch = algo_bytes(dom, "muscl", "fp32") * n
+    peak, peak_src = measured_peaks()
+    achieved = bytes_launch / (dom_ms / 1e3) / 1e9
+    traffic = ncu_traffic(f"{kname}:{dom}:muscl:fp32", n)
+    step_ms = ms / args.steps
+    step_ideal = step_bytes_ideal("muscl", "fp32") * n / (step_ms / 1e3) / 1e9
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).pin_memory().numpy()
+    hin = [pin(w.h), pin(w.hu), pin(w.hv)]
+    hout = [pin(np.zeros(n)) for _ in range(3)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st.set_state(*hin)
+    st.step(args.steps, args.cfl)
+    st.get_state(hout)
+    mass = st.mass()
+    t1 = time.perf_counter()
+    e2e = ws * n * args.steps / (t1 - t0)
+    h2d = 3 * 8 * n / args.steps
+    d2h = (3 * 8 * n + 8 * 3) / args.steps
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {
+            "workload": f"river {grid[0]}x{grid[1]} jittered grid, {n} triangles, MUSCL-HLLC FP32 bulk "
+                        "(FP64 mass/time), Euler, CFL 0.9, Morton order",
+            "cells": n, "scheme": "muscl", "precision": "fp32", "time_scheme": "euler", "kernel": kname,
+            "block": block, "device_bytes": dev_bytes,
+            "l2": f"inputs larger than L2: {dev_bytes / 1e9:.2f} GB resident per state, no flush needed",
+            "parallelism": "replicas" if ws > 1 else "single GPU", "seed": SEED,
+        },
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
+                     "algo_bytes_per_cell": algo_bytes(dom, "muscl", "fp32"),
+                     "kernel_ms": dom_ms, "per_kernel_ms": {k: v[0] / v[1] for k, v in prof.items()},
+                     "step_ideal_bytes_per_cell": step_bytes_ideal("muscl", "fp32"),
+                     "step_frac_of_ideal": step_ideal / peak},
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+
+    if rank == 0 and not args.quick:
+        out.update(fp64_comparison(args, mesh, w, swe, torch))
+        if ws == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(w, n)
+    if rank == 0:
+        print(json.dumps(out))
+    st.close()
+    mesh.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def fp64_comparison(args, mesh, w, swe, torch):
+    """FP64 GPU path: its throughput, and the FP32 error against it at matched time."""
+    n = mesh.n
+    m_steps = args.fp64_steps
+    p64 = swe.swe_params_default("muscl", "fp64", kernel=args.kernel)
+    s64 = swe.State.from_workload(mesh, p64, w)
+    s64.step(3, args.cfl)
+    s64.sync()
+    s64.close()
+    s64 = swe.State.from_workload(mesh, p64, w)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s64.step(m_steps, args.cfl)
+    e1.record(stream)
+    e1.synchronize()
+    ms64 = e0.elapsed_time(e1)
+    dts = s64.dt_history(m_steps)
+    h64, hu64, hv64 = s64.get_state()
+    mass64 = s64.mass()
+    p32 = swe.swe_params_default("muscl", "fp32", kernel=args.kernel)
+    p32.h_eps = p64.h_eps         # same algorithm, precision differs only
+    p32.r_eps = p64.r_eps
+    s32 = swe.State.from_workload(mesh, p32, w)
+    m0 = s32.mass()[0]
+    s32.step_dt(dts)
+    h32, hu32, hv32 = s32.get_state()
+    mass32 = s32.mass()
+    qs = max(np.abs(hu64).max(), np.abs(hv64).max())
+    err = {
+        "steps": m_steps, "t_end": float(np.sum(dts)),
+        "l1_h": rel_l1(h32, h64), "linf_h": rel_inf(h32, h64),
+        "l1_hu": rel_l1(hu32, hu64), "linf_hu": float(np.abs(hu32 - hu64).max() / qs),
+        "l1_hv": rel_l1(hv32, hv64), "linf_hv": float(np.abs(hv32 - hv64).max() / qs),
+        "mass_drift_fp32": abs(mass32[0] - m0 - mass32[1] - mass32[2]) / m0,
+        "mass_drift_fp64": abs(mass64[0] - m0 - mass64[1] - mass64[2]) / m0,
+        "h_eps": p64.h_eps,
+    }
+    s32.close()
+    s64.close()
+    v64 = n * m_steps / (ms64 / 1e3)
+    return {"fp64": {"value": v64, "unit": UNIT, "ms_per_step": ms64 / m_steps, "steps": m_steps},
+            "error_fp32_vs_fp64": err}
+
+
+def cpu_baseline(w, n):
+    """The FP64 oracle as it stands, on the host cores, 2 steps of the full mesh (bounded sample)."""
+    import oracle
+    oracle.build()
+    om = oracle.Mesh(w.nodes, w.tris, w.bnd_edges, w.bnd_tag)
+    cores = os.cpu_count() or 1
+    o = oracle.opts("muscl", threads=cores)
+    steps = 2
+    t0 = time.perf_counter()
+    oracle.run(om, o, w.z, w.nman, w.h, w.hu, w.hv, steps, q_in=w.q_in, level=w.level)
+    el = time.perf_counter() - t0
+    return {"value": n * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} FP64 MUSCL-HLLC Euler steps of the full {n}-cell river mesh "
+                      f"(mesh build excluded), OpenMP over cells"}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cfl", type=float, default=0.9)
+    ap.add_argument("--kernel", default="auto", choices=["auto", "split", "fused"])
+    ap.add_argument("--fp64-steps", type=int, default=100)
+    ap.add_argument("--scale", type=float, default=1.0, help="fraction of the 13M-cell mesh (testing only)")
+    ap.add_argument("--quick", action="store_true", help="skip the FP64 comparison and the CPU baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -162,6 +162,23 @@ int swe_time(swe_state *s, double *t, int64_t *steps);
 /* Device bytes held by the state and the kernel configuration in use. */
 int swe_state_info(const swe_state *s, int64_t *device_bytes, int *kernel, int *block);
 
+/* ---- Tracing ----------------------------------------------------------- */
+
+/* Kernel kinds reported by swe_profile_end. */
+enum { SWE_K_PREP = 0, SWE_K_FLUX = 1, SWE_K_HEUN_AVG = 2, SWE_K_SMAX = 3, SWE_K_FUSED = 4,
+       SWE_K_ENSEMBLE = 5, SWE_K_COUNT = 8 };
+#define SWE_DT_HISTORY 4096
+
+/* While profiling, every kernel launched by swe_step / swe_step_dt is
+ * bracketed by CUDA events on the state's stream (and CUDA graphs are not
+ * used).  swe_profile_end waits for the stream and returns, per kernel kind,
+ * the summed device time in ms and the number of launches (arrays of
+ * SWE_K_COUNT; either may be NULL). */
+int swe_profile_begin(swe_state *s);
+int swe_profile_end(swe_state *s, double *kernel_ms, int64_t *launches);
+/* The last n time steps taken (oldest first), n <= min(steps taken, SWE_DT_HISTORY). */
+int swe_dt_history(swe_state *s, double *dt, int n);
+
 /* ---- Ensemble ---------------------------------------------------------- */
 
 /* Group independent states (same precision, scheme and time scheme) so that

@@ -80,6 +80,11 @@ template <typename T> struct StateT {
     int n_part = 0;
     double *dtbuf = nullptr;
     int dtbuf_len = 0;
+    double *dt_hist = nullptr;
+    // tracing: CUDA events around every launch while profiling
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> ev_used;
     int64_t k = 0;            // steps launched (selects the smax slots)
     bool smax_valid = false;
     T qlen[SWE_MAX_GROUPS] = {}, level[SWE_MAX_GROUPS] = {};
@@ -93,7 +98,29 @@ template <typename T> struct StateT {
     }
     ~StateT()
     {
+        for (auto &e : ev_used) { cudaEventDestroy(std::get<1>(e)); cudaEventDestroy(std::get<2>(e)); }
+        for (auto e : ev_pool) cudaEventDestroy(e);
         for (auto &b : mem.blocks) dev_free(b.first, stream);
+    }
+
+    cudaEvent_t take_event()
+    {
+        if (!ev_pool.empty()) { cudaEvent_t e = ev_pool.back(); ev_pool.pop_back(); return e; }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+
+    // Launch f (returning cudaError_t), bracketed by events when profiling.
+    template <typename F> cudaError_t traced(int kind, F &&f)
+    {
+        if (!prof) return f();
+        cudaEvent_t a = take_event(), b = take_event();
+        cudaEventRecord(a, stream);
+        cudaError_t e = f();
+        cudaEventRecord(b, stream);
+        ev_used.emplace_back(kind, a, b);
+        return e;
     }
 
     DevMesh<T> dmesh() const
@@ -111,6 +138,7 @@ template <typename T> struct StateT {
         a.ho = h[out]; a.huo = hu[out]; a.hvo = hv[out];
         a.F = F; a.U = U; a.sc = sc;
         a.dtv = nullptr;
+        a.dt_hist = dt_hist;
         a.slot_cur = (int)(k % 3); a.slot_next = (int)((k + 1) % 3); a.slot_clear = (int)((k + 2) % 3);
         a.mode = MODE_EULER;
         a.g = (T)p.g; a.h_eps = (T)p.h_eps; a.r_eps = (T)p.r_eps;
@@ -125,7 +153,7 @@ template <typename T> struct StateT {
     {
         CK(cudaMemsetAsync(sc->smax, 0, sizeof(sc->smax), stream));
         StepArgs<T> a = args(cur, cur);
-        CK(launch_smax<T>(a, (int)(k % 3), block(), stream));
+        CK(traced(SWE_K_SMAX, [&] { return launch_smax<T>(a, (int)(k % 3), block(), stream); }));
         smax_valid = true;
         return SWE_OK;
     }
@@ -138,21 +166,22 @@ template <typename T> struct StateT {
         a.cfl_rmin = cfl * r_min;
         a.dtv = dt_dev;
         const int bl = block();
+        const bool has_prep = p.scheme != SWE_SCHEME_HLLC;
         if (p.time_scheme == SWE_EULER) {
-            CK(launch_prep<T>(p.scheme, a, F, U, bl, stream));
-            CK(launch_flux<T>(p.scheme, a, bl, stream));
+            if (has_prep) CK(traced(SWE_K_PREP, [&] { return launch_prep<T>(p.scheme, a, F, U, bl, stream); }));
+            CK(traced(SWE_K_FLUX, [&] { return launch_flux<T>(p.scheme, a, bl, stream); }));
         } else {
             StepArgs<T> s1 = args(cur, 2);
             s1.cfl_rmin = a.cfl_rmin; s1.dtv = dt_dev; s1.mode = MODE_STAGE;
-            CK(launch_prep<T>(p.scheme, s1, F, U, bl, stream));
-            CK(launch_flux<T>(p.scheme, s1, bl, stream));
+            if (has_prep) CK(traced(SWE_K_PREP, [&] { return launch_prep<T>(p.scheme, s1, F, U, bl, stream); }));
+            CK(traced(SWE_K_FLUX, [&] { return launch_flux<T>(p.scheme, s1, bl, stream); }));
             StepArgs<T> s2 = args(2, nxt);
             s2.cfl_rmin = a.cfl_rmin; s2.dtv = dt_dev; s2.mode = MODE_STAGE;
-            CK(launch_prep<T>(p.scheme, s2, F, U, bl, stream));
-            CK(launch_flux<T>(p.scheme, s2, bl, stream));
+            if (has_prep) CK(traced(SWE_K_PREP, [&] { return launch_prep<T>(p.scheme, s2, F, U, bl, stream); }));
+            CK(traced(SWE_K_FLUX, [&] { return launch_flux<T>(p.scheme, s2, bl, stream); }));
             StepArgs<T> av = args(nxt, nxt);
             av.cfl_rmin = a.cfl_rmin; av.dtv = dt_dev;
-            CK(launch_heun_avg<T>(av, h[cur], hu[cur], hv[cur], bl, stream));
+            CK(traced(SWE_K_HEUN_AVG, [&] { return launch_heun_avg<T>(av, h[cur], hu[cur], hv[cur], bl, stream); }));
         }
         cur = nxt;
         k++;
@@ -231,6 +260,7 @@ int state_init(StateT<T> &s, const swe_mesh *m, const double *h, const double *h
     s.mass_part = s.template alloc<double>(s.n_part);
     s.mass_out = s.template alloc<double>(1);
     s.staging = s.template alloc<double>(3 * n);
+    s.dt_hist = s.template alloc<double>(SWE_DT_HISTORY);
     for (auto &b : s.mem.blocks)
         if (!b.first) { swe_set_error("device allocation failed"); return SWE_ERR_NOMEM; }
     if (!s.nbr || !s.staging) { swe_set_error("device allocation failed"); return SWE_ERR_NOMEM; }
@@ -503,6 +533,55 @@ int swe_state_info(const swe_state *s, int64_t *device_bytes, int *kernel, int *
         if (device_bytes) *device_bytes = S.mem.bytes;
         if (kernel) *kernel = SWE_KERNEL_SPLIT;
         if (block) *block = S.block();
+        return SWE_OK;
+    })());
+}
+
+int swe_profile_begin(swe_state *s)
+{
+    if (!s) { swe_set_error("swe_profile_begin: NULL state"); return SWE_ERR_ARG; }
+    return DISPATCH(s, (S.prof = true, SWE_OK));
+}
+
+int swe_profile_end(swe_state *s, double *kernel_ms, int64_t *launches)
+{
+    if (!s) { swe_set_error("swe_profile_end: NULL state"); return SWE_ERR_ARG; }
+    return DISPATCH(s, ([&]() -> int {
+        CK(cudaStreamSynchronize(S.stream));
+        double ms[SWE_K_COUNT] = {};
+        int64_t cnt[SWE_K_COUNT] = {};
+        for (auto &e : S.ev_used) {
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, std::get<1>(e), std::get<2>(e)));
+            ms[std::get<0>(e)] += t;
+            cnt[std::get<0>(e)]++;
+            S.ev_pool.push_back(std::get<1>(e));
+            S.ev_pool.push_back(std::get<2>(e));
+        }
+        S.ev_used.clear();
+        S.prof = false;
+        for (int q = 0; q < SWE_K_COUNT; q++) {
+            if (kernel_ms) kernel_ms[q] = ms[q];
+            if (launches) launches[q] = cnt[q];
+        }
+        return SWE_OK;
+    })());
+}
+
+int swe_dt_history(swe_state *s, double *dt, int n)
+{
+    if (!s || n < 0 || n > SWE_DT_HISTORY || (n > 0 && !dt)) { swe_set_error("swe_dt_history: bad argument"); return SWE_ERR_ARG; }
+    return DISPATCH(s, ([&]() -> int {
+        DevScalars d;
+        int rc = S.read_scalars(d);
+        if (rc) return rc;
+        if (n > d.steps) { swe_set_error("swe_dt_history: fewer steps taken"); return SWE_ERR_ARG; }
+        std::vector<double> ring(SWE_DT_HISTORY);
+        CK(cudaMemcpy(ring.data(), S.dt_hist, sizeof(double) * SWE_DT_HISTORY, cudaMemcpyDeviceToHost));
+        for (int q = 0; q < n; q++) {
+            long long idx = d.steps - n + q;
+            dt[q] = ring[(size_t)(idx % SWE_DT_HISTORY)];
+        }
         return SWE_OK;
     })());
 }

@@ -51,6 +51,7 @@ template <typename T> struct StepArgs {
     const Vec4<T> *U;           // WAF: upwind means [3n] (h, u, v, -)
     DevScalars *sc;
     const double *dtv;          // replayed time step (NULL: CFL rule)
+    double *dt_hist;            // ring of the last SWE_DT_HISTORY time steps
     int slot_cur, slot_next, slot_clear;
     int mode;                   // MODE_EULER or MODE_STAGE (first Heun stage or second without averaging)
     double cfl_rmin;            // cfl * r_min

@@ -498,6 +498,7 @@ __global__ void k_flux(StepArgs<T> a)
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         if (dry) atomicOr(&a.sc->status, ST_DRY);
         if (euler) {
+            a.dt_hist[a.sc->steps % SWE_DT_HISTORY] = (double)dt;
             a.sc->t += (double)dt;
             a.sc->steps += 1;
             a.sc->smax[a.slot_clear] = 0ULL;
@@ -539,6 +540,7 @@ __global__ void k_heun_avg(StepArgs<T> a, const T *h0, const T *hu0, const T *hv
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         bool dry;
         T dt = step_dt(a, &dry);
+        a.dt_hist[a.sc->steps % SWE_DT_HISTORY] = (double)dt;
         a.sc->t += (double)dt;
         a.sc->steps += 1;
         a.sc->smax[a.slot_clear] = 0ULL;

@@ -35,8 +35,9 @@ EXPORTED = [
     "swe_mesh_info", "swe_mesh_export", "swe_state_init", "swe_state_destroy", "swe_set_stream",
     "swe_set_state", "swe_step", "swe_step_dt", "swe_sync", "swe_get_state", "swe_mass", "swe_time",
     "swe_state_info", "swe_ensemble_create", "swe_ensemble_destroy", "swe_ensemble_step",
-    "swe_ensemble_sync",
+    "swe_ensemble_sync", "swe_profile_begin", "swe_profile_end", "swe_dt_history",
 ]
+KERNEL_KINDS = ["prep", "flux", "heun_avg", "smax", "fused", "ensemble", "k6", "k7"]
 
 
 class SweError(RuntimeError):
@@ -94,6 +95,9 @@ def load_library(path: str = LIB_PATH, use_torch_allocator: bool = True):
     lib.swe_ensemble_destroy.argtypes = [vp]
     lib.swe_ensemble_step.argtypes = [vp, i32, dp]
     lib.swe_ensemble_sync.argtypes = [vp]
+    lib.swe_profile_begin.argtypes = [vp]
+    lib.swe_profile_end.argtypes = [vp, vp, vp]
+    lib.swe_dt_history.argtypes = [vp, vp, i32]
     if use_torch_allocator:
         import torch
 
@@ -249,6 +253,24 @@ def swe_state_info(s):
     return b.value, k.value, bl.value
 
 
+def swe_profile_begin(s):
+    _check(load_library().swe_profile_begin(s))
+
+
+def swe_profile_end(s):
+    """Per kernel kind: (summed device ms, launches)."""
+    ms = np.zeros(8)
+    cnt = np.zeros(8, np.int64)
+    _check(load_library().swe_profile_end(s, _p(ms), _p(cnt)))
+    return {KERNEL_KINDS[q]: (float(ms[q]), int(cnt[q])) for q in range(8) if cnt[q]}
+
+
+def swe_dt_history(s, n):
+    out = np.empty(n)
+    _check(load_library().swe_dt_history(s, _p(out), int(n)))
+    return out
+
+
 def swe_ensemble_create(states):
     arr = (C.c_void_p * len(states))(*[s.value if isinstance(s, C.c_void_p) else s for s in states])
     out = C.c_void_p()
@@ -330,6 +352,15 @@ class State:
 
     def info(self):
         return swe_state_info(self.handle)
+
+    def dt_history(self, n):
+        return swe_dt_history(self.handle, n)
+
+    def profile_begin(self):
+        swe_profile_begin(self.handle)
+
+    def profile_end(self):
+        return swe_profile_end(self.handle)
 
     def close(self):
         if self.handle:

@@ -72,7 +72,8 @@ def structured(nx: int, ny: int, lx: float, ly: float, jitter: float = 0.0, seed
     """Rectangle [0,lx]x[0,ly] of nx*ny squares, each split by its "/" diagonal.
 
     Interior nodes move by U(-jitter, jitter) spacings per axis (boundary
-    nodes stay).  Returns nodes, tris and the boundary edges with their side
+    nodes stay); nodes of triangles left with less than 20 % of their nominal
+    area have their displacement halved until no such triangle remains.  Returns nodes, tris and the boundary edges with their side
     (0 bottom, 1 right, 2 top, 3 left)."""
     dx, dy = lx / nx, ly / ny
     ii, jj = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1))
@@ -86,9 +87,8 @@ def structured(nx: int, ny: int, lx: float, ly: float, jitter: float = 0.0, seed
         mx = interior.copy()
         if fixed_x_col is not None:
             mx &= (ii.ravel() != fixed_x_col)
-        x = x + np.where(mx, jx, 0.0)
-        y = y + np.where(interior, jy, 0.0)
-    nodes = np.stack([x, y], axis=1)
+        jx = np.where(mx, jx, 0.0)
+        jy = np.where(interior, jy, 0.0)
     i, j = np.meshgrid(np.arange(nx), np.arange(ny))
     i, j = i.ravel(), j.ravel()
     p00 = j * (nx + 1) + i
@@ -96,6 +96,21 @@ def structured(nx: int, ny: int, lx: float, ly: float, jitter: float = 0.0, seed
     tris = np.empty((2 * nx * ny, 3), np.int32)
     tris[0::2] = np.stack([p00, p10, p11], axis=1)
     tris[1::2] = np.stack([p00, p11, p01], axis=1)
+    if jitter > 0:
+        # a jitter above 1/6 of the spacing can fold or flatten a triangle:
+        # halve the jitter of the nodes of any triangle under 20 % of its
+        # nominal area until none is left (deterministic)
+        for _ in range(40):
+            px, py = (x + jx)[tris], (y + jy)[tris]
+            cross = (px[:, 1] - px[:, 0]) * (py[:, 2] - py[:, 0]) - (py[:, 1] - py[:, 0]) * (px[:, 2] - px[:, 0])
+            bad = cross < 0.2 * dx * dy
+            if not bad.any():
+                break
+            nodes_bad = np.unique(tris[bad])
+            jx[nodes_bad] *= 0.5
+            jy[nodes_bad] *= 0.5
+        x, y = x + jx, y + jy
+    nodes = np.stack([x, y], axis=1)
     # boundary edges, side by side
     b = np.arange(nx)
     bottom = np.stack([b, b + 1], axis=1)

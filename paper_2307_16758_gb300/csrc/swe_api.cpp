@@ -14,6 +14,7 @@
 
 #include "swe_dev.h"
 #include "swe_mesh.h"
+#include "swe_tiles.h"
 
 int swe_mesh_build_host(const double *xy, int64_t n_nodes, const int32_t *tri, int64_t n,
                         const int32_t *bnd, const int32_t *bnd_tag, int64_t n_bnd,
@@ -85,6 +86,9 @@ template <typename T> struct StateT {
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> ev_used;
+    // fused tile kernel
+    bool fused = false;
+    FusedArgs fa{};
     int64_t k = 0;            // steps launched (selects the smax slots)
     bool smax_valid = false;
     T qlen[SWE_MAX_GROUPS] = {}, level[SWE_MAX_GROUPS] = {};
@@ -147,7 +151,17 @@ template <typename T> struct StateT {
         return a;
     }
 
-    int block() const { return p.block > 0 ? p.block : 256; }
+    int block() const { return fused ? fa.tile : (p.block > 0 ? p.block : 256); }
+
+    cudaError_t launch_step_kernels(const StepArgs<T> &a, int bl)
+    {
+        if (fused) return traced(SWE_K_FUSED, [&] { return launch_fused<T>(p.scheme, a, fa, stream); });
+        if (p.scheme != SWE_SCHEME_HLLC) {
+            cudaError_t e = traced(SWE_K_PREP, [&] { return launch_prep<T>(p.scheme, a, F, U, bl, stream); });
+            if (e != cudaSuccess) return e;
+        }
+        return traced(SWE_K_FLUX, [&] { return launch_flux<T>(p.scheme, a, bl, stream); });
+    }
 
     int init_smax()
     {
@@ -166,19 +180,15 @@ template <typename T> struct StateT {
         a.cfl_rmin = cfl * r_min;
         a.dtv = dt_dev;
         const int bl = block();
-        const bool has_prep = p.scheme != SWE_SCHEME_HLLC;
         if (p.time_scheme == SWE_EULER) {
-            if (has_prep) CK(traced(SWE_K_PREP, [&] { return launch_prep<T>(p.scheme, a, F, U, bl, stream); }));
-            CK(traced(SWE_K_FLUX, [&] { return launch_flux<T>(p.scheme, a, bl, stream); }));
+            CK(launch_step_kernels(a, bl));
         } else {
             StepArgs<T> s1 = args(cur, 2);
             s1.cfl_rmin = a.cfl_rmin; s1.dtv = dt_dev; s1.mode = MODE_STAGE;
-            if (has_prep) CK(traced(SWE_K_PREP, [&] { return launch_prep<T>(p.scheme, s1, F, U, bl, stream); }));
-            CK(traced(SWE_K_FLUX, [&] { return launch_flux<T>(p.scheme, s1, bl, stream); }));
+            CK(launch_step_kernels(s1, bl));
             StepArgs<T> s2 = args(2, nxt);
             s2.cfl_rmin = a.cfl_rmin; s2.dtv = dt_dev; s2.mode = MODE_STAGE;
-            if (has_prep) CK(traced(SWE_K_PREP, [&] { return launch_prep<T>(p.scheme, s2, F, U, bl, stream); }));
-            CK(traced(SWE_K_FLUX, [&] { return launch_flux<T>(p.scheme, s2, bl, stream); }));
+            CK(launch_step_kernels(s2, bl));
             StepArgs<T> av = args(nxt, nxt);
             av.cfl_rmin = a.cfl_rmin; av.dtv = dt_dev;
             CK(traced(SWE_K_HEUN_AVG, [&] { return launch_heun_avg<T>(av, h[cur], hu[cur], hv[cur], bl, stream); }));
@@ -253,8 +263,26 @@ int state_init(StateT<T> &s, const swe_mesh *m, const double *h, const double *h
     for (int b = 0; b < nbuf; b++) {
         s.h[b] = s.template alloc<T>(n); s.hu[b] = s.template alloc<T>(n); s.hv[b] = s.template alloc<T>(n);
     }
-    if (s.p.scheme == SWE_SCHEME_MUSCL) s.F = s.template alloc<Vec4<T>>(3 * n);
-    if (s.p.scheme == SWE_SCHEME_WAF) { s.F = s.template alloc<Vec4<T>>(n); s.U = s.template alloc<Vec4<T>>(3 * n); }
+    s.fused = s.p.scheme != SWE_SCHEME_HLLC &&
+              (s.p.kernel == SWE_KERNEL_FUSED || s.p.kernel == SWE_KERNEL_AUTO);
+    Tiling tl;
+    if (s.fused) {
+        const int tile = s.p.block > 0 ? s.p.block : 256;
+        if (swe_build_tiling(*m, tile, tl) != 0) { swe_set_error("swe_state_init: tile too large"); return SWE_ERR_ARG; }
+        s.fa.tile = tile;
+        s.fa.slots = tile + tl.max_halo;
+        if (fused_smem_bytes<T>(s.p.scheme, s.fa.slots) > 227 * 1024) {
+            swe_set_error("swe_state_init: tile needs more shared memory than a block has");
+            return SWE_ERR_ARG;
+        }
+        int32_t *hp = s.template alloc<int32_t>(tl.halo_ptr.size());
+        int32_t *hi = s.template alloc<int32_t>(std::max<size_t>(tl.halo_ids.size(), 1));
+        uint16_t *nl = s.template alloc<uint16_t>(3 * n);
+        s.fa.halo_ptr = hp; s.fa.halo_ids = hi; s.fa.nbr_local = nl;
+    } else {
+        if (s.p.scheme == SWE_SCHEME_MUSCL) s.F = s.template alloc<Vec4<T>>(3 * n);
+        if (s.p.scheme == SWE_SCHEME_WAF) { s.F = s.template alloc<Vec4<T>>(n); s.U = s.template alloc<Vec4<T>>(3 * n); }
+    }
     s.sc = s.template alloc<DevScalars>(1);
     s.n_part = mass_partials_needed(n);
     s.mass_part = s.template alloc<double>(s.n_part);
@@ -273,6 +301,15 @@ int state_init(StateT<T> &s, const swe_mesh *m, const double *h, const double *h
     if (s.nman) CK(cudaMemcpyAsync(s.nman, nt.data(), sizeof(T) * n, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(s.area, m->area.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(s.sc, 0, sizeof(DevScalars), st));
+    if (s.fused) {
+        CK(cudaMemcpyAsync((void *)s.fa.halo_ptr, tl.halo_ptr.data(), sizeof(int32_t) * tl.halo_ptr.size(),
+                           cudaMemcpyHostToDevice, st));
+        if (!tl.halo_ids.empty())
+            CK(cudaMemcpyAsync((void *)s.fa.halo_ids, tl.halo_ids.data(), sizeof(int32_t) * tl.halo_ids.size(),
+                               cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync((void *)s.fa.nbr_local, tl.nbr_local.data(), sizeof(uint16_t) * 3 * n,
+                           cudaMemcpyHostToDevice, st));
+    }
     // initial state through the same path as swe_set_state
     CK(cudaMemcpyAsync(s.staging, h, sizeof(double) * n, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(s.staging + n, hu, sizeof(double) * n, cudaMemcpyHostToDevice, st));
@@ -531,7 +568,7 @@ int swe_state_info(const swe_state *s, int64_t *device_bytes, int *kernel, int *
     auto *ms = const_cast<swe_state *>(s);
     return DISPATCH(ms, ([&]() -> int {
         if (device_bytes) *device_bytes = S.mem.bytes;
-        if (kernel) *kernel = SWE_KERNEL_SPLIT;
+        if (kernel) *kernel = S.fused ? SWE_KERNEL_FUSED : SWE_KERNEL_SPLIT;
         if (block) *block = S.block();
         return SWE_OK;
     })());

@@ -61,7 +61,20 @@ template <typename T> struct StepArgs {
     T level[SWE_MAX_GROUPS];    // fixed free-surface levels [m]
 };
 
-// Launchers (defined in swe_kernels.cu).  All launches go to `stream`.
+// Fused tile kernel: the cells of tile b are [b*tile, (b+1)*tile); the tile's
+// halo (neighbours outside it) is halo_ids[halo_ptr[b] .. halo_ptr[b+1]).
+// nbr_local[3n] gives, per cell edge, (slot << 3) | (neighbour's local edge << 1)
+// | owner with slot < tile for tile cells and tile + q for halo cell q, or
+// 0x8000 | tag on a boundary.
+struct FusedArgs {
+    const int32_t *halo_ptr;
+    const int32_t *halo_ids;
+    const uint16_t *nbr_local;
+    int tile;       // cells per tile = threads per block
+    int slots;      // tile + largest halo
+};
+
+// Launchers (defined in swe_kernels.cu and swe_fused.cu).  All launches go to `stream`.
 template <typename T>
 cudaError_t launch_prep(int scheme, const StepArgs<T> &a, Vec4<T> *F, Vec4<T> *U, int block, cudaStream_t s);
 template <typename T>
@@ -82,5 +95,9 @@ cudaError_t launch_gather_out(int64_t n, const int32_t *perm, const T *h, const 
                               double *dst, cudaStream_t s);
 template <typename T>
 cudaError_t launch_convert(int64_t n, const double *src, T *dst, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_fused(int scheme, const StepArgs<T> &a, const FusedArgs &f, cudaStream_t s);
+template <typename T> size_t fused_smem_bytes(int scheme, int slots);
 
 int mass_partials_needed(int64_t n);

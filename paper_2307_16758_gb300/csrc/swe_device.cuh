@@ -9,7 +9,15 @@
 
 namespace swe_dev {
 
-template <typename T> __device__ __forceinline__ T dsqrt(T x) { return sqrt(x); }
+// Square root and division.  FP64 keeps IEEE-rounded sqrt and division (the
+// FP64 path is compared with the oracle to 1e-12).  The FP32 path uses the
+// hardware approximations (MUFU.RSQ / MUFU.RCP based, about 2 ulp), which is
+// far inside its error budget and keeps every exact-zero and symmetry
+// property, since equal inputs still give equal outputs.
+__device__ __forceinline__ double dsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float dsqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+__device__ __forceinline__ double ddiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float ddiv(float a, float b) { return __fdividef(a, b); }
 template <typename T> __device__ __forceinline__ T dmax(T a, T b) { return a > b ? a : b; }
 template <typename T> __device__ __forceinline__ T dmin(T a, T b) { return a < b ? a : b; }
 __device__ __forceinline__ float dcbrt(float x) { return cbrtf(x); }
@@ -43,7 +51,7 @@ __device__ __forceinline__ T waf_ratio(T r_eps, T upw, T qL, T qR)
     T loc = qR - qL;
     T sc = dmax(dmax(fabs(qL), fabs(qR)), T(1));
     if (fabs(loc) <= r_eps * sc) return T(0);
-    return upw / loc;
+    return ddiv(upw, loc);
 }
 
 // A(r, c) of Sec. 5.2.2 (SUPERBEE), or its phi = 1 / phi = 0 variants.
@@ -82,24 +90,24 @@ __device__ __forceinline__ Flux<T> riemann(T hsL, T uL, T vL, T hsR, T uR, T vR,
     } else if (dryR) {
         SL = uL - aL; SR = uL + T(2) * aL;
     } else {
-        T h0 = (hsL + hsR) / T(2) - (uR - uL) * (hsL + hsR) / (T(4) * (aR + aL));
+        T h0 = (hsL + hsR) / T(2) - ddiv((uR - uL) * (hsL + hsR), T(4) * (aR + aL));
         T hs;
         if (h0 <= dmin(hsL, hsR)) {        // two rarefactions
             T br = dmax((aR + aL) / T(2) + (uL - uR) / T(4), T(0));
-            hs = br * br / g;
+            hs = ddiv(br * br, g);
         } else {                           // two shocks
-            T gL = dsqrt(g * (h0 + hsL) / (T(2) * h0 * hsL));
-            T gR = dsqrt(g * (h0 + hsR) / (T(2) * h0 * hsR));
-            hs = (hsL * gL + hsR * gR + uL - uR) / (gL + gR);
+            T gL = dsqrt(ddiv(g * (h0 + hsL), T(2) * h0 * hsL));
+            T gR = dsqrt(ddiv(g * (h0 + hsR), T(2) * h0 * hsR));
+            hs = ddiv(hsL * gL + hsR * gR + uL - uR, gL + gR);
         }
-        T pL = hs > hsL ? dsqrt(hs * (hs + hsL) / T(2)) / hsL : T(1);
-        T pR = hs > hsR ? dsqrt(hs * (hs + hsR) / T(2)) / hsR : T(1);
+        T pL = hs > hsL ? ddiv(dsqrt(hs * (hs + hsL) / T(2)), hsL) : T(1);
+        T pR = hs > hsR ? ddiv(dsqrt(hs * (hs + hsR) / T(2)), hsR) : T(1);
         SL = uL - aL * pL;
         SR = uR + aR * pR;
     }
     T num = SL * hsR * (uR - SR) - SR * hsL * (uL - SL);
     T den = hsR * (uR - SR) - hsL * (uL - SL);
-    T Ss = den != T(0) ? num / den : T(0);
+    T Ss = den != T(0) ? ddiv(num, den) : T(0);
     // HLL (three branches) as differences to G_L and G_R
     T hL1, hL2, hR2;
     bool rightgoing = SL >= T(0), leftgoing = !rightgoing && SR <= T(0);
@@ -109,9 +117,9 @@ __device__ __forceinline__ Flux<T> riemann(T hsL, T uL, T vL, T hsR, T uR, T vR,
         hL1 = dG1; hL2 = dG2; hR2 = T(0);
     } else {
         T wd = SR - SL;
-        hL1 = SL * (SR * dU1 - dG1) / wd;
-        hL2 = SL * (SR * dU2 - dG2) / wd;
-        hR2 = SR * (SL * dU2 - dG2) / wd;
+        hL1 = ddiv(SL * (SR * dU1 - dG1), wd);
+        hL2 = ddiv(SL * (SR * dU2 - dG2), wd);
+        hR2 = ddiv(SR * (SL * dU2 - dG2), wd);
     }
     if (!WAF) {
         f.M = leftgoing ? GR1 : GL1 + hL1;
@@ -154,8 +162,8 @@ template <typename T>
 __device__ __forceinline__ void primitives(T h, T hu, T hv, T h_eps, T &u, T &v)
 {
     bool wet = h > h_eps;
-    u = wet ? hu / h : T(0);
-    v = wet ? hv / h : T(0);
+    u = wet ? ddiv(hu, h) : T(0);
+    v = wet ? ddiv(hv, h) : T(0);
 }
 
 // ---------------------------------------------------------------------------
@@ -168,36 +176,41 @@ __device__ __forceinline__ T warp_max(T v)
     for (int o = 16; o > 0; o >>= 1) v = dmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
-__device__ __forceinline__ double warp_sum(double v)
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
-// Max of s, sums of c1 and c2 over the block; thread 0 publishes them.
+// Max of s and sums of c1, c2 over the block (in the compute type; a warp
+// whose values are all zero skips its sum); thread 0 publishes them: the
+// max into the CFL slot (atomicMax on the bits of the non-negative double),
+// the sums into the FP64 diagnostics, scaled by wsum.
 template <typename T>
-__device__ __forceinline__ void block_publish(T s, double c1, double c2, DevScalars *sc, int slot_next,
+__device__ __forceinline__ void block_publish(T s, T c1, T c2, DevScalars *sc, int slot_next,
                                               bool want_max, double wsum)
 {
-    __shared__ double sh_s[32], sh_c1[32], sh_c2[32];
+    __shared__ T sh_s[32], sh_c1[32], sh_c2[32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    double sd = (double)warp_max(s);
-    c1 = warp_sum(c1);
-    c2 = warp_sum(c2);
-    if (lane == 0) { sh_s[wid] = sd; sh_c1[wid] = c1; sh_c2[wid] = c2; }
+    s = warp_max(s);
+    if (__any_sync(0xffffffffu, c1 != T(0))) c1 = warp_sum(c1);
+    if (__any_sync(0xffffffffu, c2 != T(0))) c2 = warp_sum(c2);
+    if (lane == 0) { sh_s[wid] = s; sh_c1[wid] = c1; sh_c2[wid] = c2; }
     __syncthreads();
     if (wid == 0) {
-        sd = lane < nw ? sh_s[lane] : 0.0;
-        c1 = lane < nw ? sh_c1[lane] : 0.0;
-        c2 = lane < nw ? sh_c2[lane] : 0.0;
-        sd = warp_max(sd);
-        c1 = warp_sum(c1);
-        c2 = warp_sum(c2);
+        s = lane < nw ? sh_s[lane] : T(0);
+        c1 = lane < nw ? sh_c1[lane] : T(0);
+        c2 = lane < nw ? sh_c2[lane] : T(0);
+        s = warp_max(s);
+        if (__any_sync(0xffffffffu, c1 != T(0))) c1 = warp_sum(c1);
+        if (__any_sync(0xffffffffu, c2 != T(0))) c2 = warp_sum(c2);
         if (lane == 0) {
-            if (want_max && sd > 0.0) atomicMax(&sc->smax[slot_next], (unsigned long long)__double_as_longlong(sd));
-            if (c1 != 0.0) atomicAdd(&sc->clipped, wsum * c1);
-            if (c2 != 0.0) atomicAdd(&sc->bnd_in, wsum * c2);
+            if (want_max && s > T(0))
+                atomicMax(&sc->smax[slot_next], (unsigned long long)__double_as_longlong((double)s));
+            if (c1 != T(0)) atomicAdd(&sc->clipped, wsum * (double)c1);
+            if (c2 != T(0)) atomicAdd(&sc->bnd_in, wsum * (double)c2);
         }
     }
 }
@@ -209,8 +222,255 @@ __device__ __forceinline__ T step_dt(const StepArgs<T> &a, bool *dry)
     double sm = __longlong_as_double((long long)a.sc->smax[a.slot_cur]);
     *dry = !(sm > 0.0);
     if (*dry) return T(0);
-    return (T)a.cfl_rmin / (T)sm;
+    return ddiv((T)a.cfl_rmin, (T)sm);
 }
 
+// The time step, computed by one thread and shared with the block.
+template <typename T>
+__device__ __forceinline__ T block_dt(const StepArgs<T> &a, bool *dry)
+{
+    __shared__ T sh_dt;
+    __shared__ int sh_dry;
+    if (threadIdx.x == 0) {
+        bool d;
+        sh_dt = step_dt(a, &d);
+        sh_dry = d;
+    }
+    __syncthreads();
+    *dry = sh_dry != 0;
+    return sh_dt;
+}
+
+// MUSCL face values of one cell (least squares + Barth-Jespersen, zero
+// gradient next to a dry cell or for a singular 2x2 system).  qi = own
+// (eta, u, v); qn[k] = neighbour k's (eta, u, v) where has[k]; ok = the cell
+// and all its neighbours are wet; cnt = number of neighbours.  F[k] =
+// (eta, u, v, z) at the midpoint of edge k.
+template <typename T>
+__device__ __forceinline__ void muscl_faces(const T qi[3], T zi, bool ok, int cnt, const T qn[3][3],
+                                            const bool has[3], const Vec2<T> ln[3], const Vec2<T> dd[3],
+                                            Vec4<T> F[3])
+{
+    T gx[3] = {T(0), T(0), T(0)}, gy[3] = {T(0), T(0), T(0)};
+    T ox[3], oy[3];
+    midpoint_offsets(ln, ox, oy);
+    if (ok && cnt >= 2) {
+        T Mxx = T(0), Mxy = T(0), Myy = T(0);
+        T bx[3] = {T(0), T(0), T(0)}, by[3] = {T(0), T(0), T(0)};
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            if (!has[k]) continue;
+            T dx = dd[k].x, dy = dd[k].y;
+            Mxx += dx * dx; Mxy += dx * dy; Myy += dy * dy;
+#pragma unroll
+            for (int s = 0; s < 3; s++) {
+                T dq = qn[k][s] - qi[s];
+                bx[s] += dx * dq; by[s] += dy * dq;
+            }
+        }
+        T det = Mxx * Myy - Mxy * Mxy, tr = Mxx + Myy;
+        if (det > T(1e-12) * tr * tr) {
+#pragma unroll
+            for (int s = 0; s < 3; s++) {
+                T px = ddiv(Myy * bx[s] - Mxy * by[s], det);
+                T py = ddiv(Mxx * by[s] - Mxy * bx[s], det);
+                T qmin = qi[s], qmax = qi[s];
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    if (!has[k]) continue;
+                    qmin = dmin(qmin, qn[k][s]);
+                    qmax = dmax(qmax, qn[k][s]);
+                }
+                T phi = T(1);
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    T d = px * ox[k] + py * oy[k];
+                    T ph = T(1);
+                    if (d > T(0)) ph = ddiv(qmax - qi[s], d);
+                    else if (d < T(0)) ph = ddiv(qmin - qi[s], d);
+                    phi = dmin(phi, ph);
+                }
+                gx[s] = phi * px; gy[s] = phi * py;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        F[k].x = qi[0] + (gx[0] * ox[k] + gy[0] * oy[k]);
+        F[k].y = qi[1] + (gx[1] * ox[k] + gy[1] * oy[k]);
+        F[k].z = qi[2] + (gx[2] * ox[k] + gy[2] * oy[k]);
+        F[k].w = zi;
+    }
+}
+
+// A decoded neighbour word: interior edge (index into the caller's arrays,
+// the neighbour's local edge, owner flag) or boundary tag.
+struct Nb {
+    bool interior, own;
+    int idx, kj, tag;
+};
+
+__device__ __forceinline__ Nb decode_global(int w)
+{
+    Nb b;
+    b.interior = w >= 0;
+    b.idx = w >> 3; b.kj = (w >> 1) & 3; b.own = w & 1;
+    b.tag = -1 - w;
+    return b;
+}
+
+__device__ __forceinline__ Nb decode_local(unsigned w)
+{
+    Nb b;
+    b.interior = !(w & 0x8000u);
+    b.idx = (int)(w >> 3); b.kj = (int)((w >> 1) & 3u); b.own = w & 1u;
+    b.tag = (int)(w & 0x7fffu);
+    return b;
+}
+
+template <typename T> struct CellOut { T h, hu, hv, smax, clip, bsum; };
+
+// Edge fluxes, explicit Euler update, clipping, Manning friction and the new
+// wave speed of one cell (Sec. 5.1-5.2), shared by the split and fused
+// kernels.  Data of the cell and of its neighbours come through `src`:
+//   MUSCL: own_face(k), nbr_face(nb) -> (eta, u, v, z) at the edge midpoint
+//   WAF  : own_centre(), nbr_centre(nb) -> (h, u, v, z); own_up(k), nbr_up(nb) -> upwind means
+//   HLLC : nbr_state(nb) -> (h, hu, hv, z)
+template <typename T, int SCHEME, typename Src>
+__device__ __forceinline__ CellOut<T> cell_update(const StepArgs<T> &a, T dt, T hi, T hui, T hvi, T zi, T nm,
+                                                  const Nb nb[3], const Vec2<T> ln[3], const Vec2<T> dd[3],
+                                                  const Src &src)
+{
+    const T g = a.g, h_eps = a.h_eps, half = T(0.5);
+    CellOut<T> o;
+    T ui, vi;
+    primitives(hi, hui, hvi, h_eps, ui, vi);
+    T R0 = T(0), R1 = T(0), R2 = T(0), bs = T(0);
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const T lx = ln[k].x, ly = ln[k].y;
+        const T L = dsqrt(lx * lx + ly * ly);
+        const T nx = ddiv(lx, L), ny = ddiv(ly, L);
+        T ef, uf, vf;
+        if (SCHEME == SWE_SCHEME_MUSCL) {
+            Vec4<T> f = src.own_face(k);
+            ef = f.x; uf = f.y; vf = f.z;
+        } else {
+            ef = hi + zi; uf = ui; vf = vi;
+        }
+        const T hf = dmax(ef - zi, T(0));
+        const T hyd = half * g * (hf - hi) * (hf + hi);
+        if (nb[k].interior) {
+            const bool own = nb[k].own;
+            T ej, uj, vj, zj, hcj = T(0);
+            Vec4<T> Uj;
+            if (SCHEME == SWE_SCHEME_MUSCL) {
+                Vec4<T> f = src.nbr_face(nb[k]);
+                ej = f.x; uj = f.y; vj = f.z; zj = f.w;
+            } else if (SCHEME == SWE_SCHEME_WAF) {
+                Vec4<T> p = src.nbr_centre(nb[k]);
+                hcj = p.x; uj = p.y; vj = p.z; zj = p.w;
+                ej = hcj + zj;
+                Uj = src.nbr_up(nb[k]);
+            } else {
+                Vec4<T> q = src.nbr_state(nb[k]);
+                zj = q.w;
+                primitives(q.x, q.y, q.z, h_eps, uj, vj);
+                ej = q.x + zj;
+            }
+            // canonical orientation: side A is the owner of the edge
+            const T cnx = own ? nx : -nx, cny = own ? ny : -ny;
+            const T eA = own ? ef : ej, eB = own ? ej : ef;
+            const T uAx = own ? uf : uj, uAy = own ? vf : vj;
+            const T uBx = own ? uj : uf, uBy = own ? vj : vf;
+            const T zf = dmax(zi, zj);
+            const T hsA = dmax(eA - zf, T(0)), hsB = dmax(eB - zf, T(0));
+            const T unA = uAx * cnx + uAy * cny, vtA = -uAx * cny + uAy * cnx;
+            const T unB = uBx * cnx + uBy * cny, vtB = -uBx * cny + uBy * cnx;
+            Flux<T> fl;
+            if (SCHEME == SWE_SCHEME_WAF) {
+                const Vec4<T> Ui = src.own_up(k);
+                WafIn<T> wi;
+                wi.dtdx = ddiv(dt, dsqrt(dd[k].x * dd[k].x + dd[k].y * dd[k].y));
+                const Vec4<T> &UA = own ? Ui : Uj;
+                const Vec4<T> &UB = own ? Uj : Ui;
+                wi.hupL = UA.x; wi.hupR = UB.x;
+                wi.vupL = -UA.y * cny + UA.z * cnx;
+                wi.vupR = -UB.y * cny + UB.z * cnx;
+                wi.hcL = own ? hi : hcj; wi.hcR = own ? hcj : hi;
+                fl = riemann<T, true>(hsA, unA, vtA, hsB, unB, vtB, g, h_eps, wi, a.waf_limiter, a.r_eps);
+            } else {
+                WafIn<T> wi{};
+                fl = riemann<T, false>(hsA, unA, vtA, hsB, unB, vtB, g, h_eps, wi, 0, a.r_eps);
+            }
+            const T P = (own ? hsA * unA * unA + fl.DL2 : hsB * unB * unB + fl.DR2) + hyd;
+            const T sM = own ? fl.M : -fl.M;
+            R0 += L * sM;
+            R1 += L * (P * nx - fl.Tt * ny);
+            R2 += L * (P * ny + fl.Tt * nx);
+        } else {
+            // boundary edge, normal outward (Sec. 5.1)
+            const int tag = nb[k].tag, kind = tag & 3, grp = tag >> 2;
+            const T un = uf * nx + vf * ny, vt = -uf * ny + vf * nx;
+            T M, P, Tt;
+            if (kind == SWE_WALL) {
+                M = T(0); P = hyd; Tt = T(0);
+            } else if (kind == SWE_OPEN) {
+                M = hf * un; P = hf * un * un + hyd; Tt = M * vt;
+            } else if (kind == SWE_INFLOW) {
+                const T q = a.qlen[grp];
+                M = -q; P = (hf > h_eps ? ddiv(q * q, hf) : T(0)) + hyd; Tt = T(0);
+            } else {
+                const T hg = dmax(a.level[grp] - zi, T(0));
+                WafIn<T> wi{};
+                Flux<T> fl = riemann<T, false>(hf, un, vt, hg, un, vt, g, h_eps, wi, 0, a.r_eps);
+                M = fl.M; P = hf * un * un + fl.DL2 + hyd; Tt = fl.Tt;
+            }
+            R0 += L * M;
+            R1 += L * (P * nx - Tt * ny);
+            R2 += L * (P * ny + Tt * nx);
+            bs -= L * M;
+        }
+    }
+    // explicit Euler update (area from the scaled normals: |e_0 x e_1| / 2)
+    const T area = half * (ln[0].x * ln[1].y - ln[0].y * ln[1].x);
+    const T r = ddiv(dt, area);
+    T hn = hi - r * R0, hun = hui - r * R1, hvn = hvi - r * R2;
+    o.clip = T(0);
+    if (hn < T(0)) { o.clip = -hn * area; hn = T(0); }
+    if (hn <= h_eps) {
+        hun = T(0); hvn = T(0);
+    } else if (nm > T(0)) {            // point-implicit Manning friction
+        const T sp = ddiv(dsqrt(hun * hun + hvn * hvn), hn);
+        const T fr = T(1) + ddiv(dt * g * nm * nm * sp, hn * dcbrt(hn));
+        hun = ddiv(hun, fr); hvn = ddiv(hvn, fr);
+    }
+    o.h = hn; o.hu = hun; o.hv = hvn;
+    o.smax = T(0);
+    if (hn > h_eps) {
+        const T u = ddiv(hun, hn), v = ddiv(hvn, hn);
+        o.smax = dsqrt(g * hn) + dsqrt(u * u + v * v);
+    }
+    o.bsum = bs * dt;
+    return o;
+}
+
+// Step epilogue: publish the block's wave speed and diagnostics; block 0
+// advances time and the step count and clears the stale CFL slot.
+template <typename T>
+__device__ __forceinline__ void step_epilogue(const StepArgs<T> &a, T dt, bool dry, T smax, T clip, T bsum)
+{
+    const bool euler = a.mode == MODE_EULER;
+    block_publish<T>(smax, clip, bsum, a.sc, a.slot_next, euler, euler ? 1.0 : 0.5);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (dry) atomicOr(&a.sc->status, ST_DRY);
+        if (euler) {
+            a.dt_hist[a.sc->steps % SWE_DT_HISTORY] = (double)dt;
+            a.sc->t += (double)dt;
+            a.sc->steps += 1;
+            a.sc->smax[a.slot_clear] = 0ULL;
+        }
+    }
+}
 
 }  // namespace swe_dev

@@ -41,21 +41,19 @@ __global__ void k_prep_muscl(StepArgs<T> a, Vec4<T> *F)
     T ui, vi;
     primitives(hi, a.hu[i], a.hv[i], h_eps, ui, vi);
     T qi[3] = {hi + zi, ui, vi};
-    int nb[3];
     Vec2<T> ln[3], dd[3];
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-        nb[k] = a.m.nbr[3 * i + k];
-        ln[k] = a.m.ln[3 * i + k];
-        dd[k] = a.m.dd[3 * i + k];
-    }
+    T qn[3][3];
+    bool has[3];
     bool ok = hi > h_eps;
     int cnt = 0;
-    T qn[3][3];
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-        if (nb[k] >= 0) {
-            int j = nb[k] >> 3;
+        const int w = a.m.nbr[3 * i + k];
+        ln[k] = a.m.ln[3 * i + k];
+        dd[k] = a.m.dd[3 * i + k];
+        has[k] = w >= 0;
+        if (has[k]) {
+            const int j = w >> 3;
             T hj = a.h[j], uj, vj;
             primitives(hj, a.hu[j], a.hv[j], h_eps, uj, vj);
             ok = ok && hj > h_eps;
@@ -65,58 +63,10 @@ __global__ void k_prep_muscl(StepArgs<T> a, Vec4<T> *F)
             qn[k][0] = qi[0]; qn[k][1] = qi[1]; qn[k][2] = qi[2];
         }
     }
-    T gx[3] = {T(0), T(0), T(0)}, gy[3] = {T(0), T(0), T(0)};
-    T ox[3], oy[3];
-    midpoint_offsets(ln, ox, oy);
-    if (ok && cnt >= 2) {
-        T Mxx = T(0), Mxy = T(0), Myy = T(0);
-        T bx[3] = {T(0), T(0), T(0)}, by[3] = {T(0), T(0), T(0)};
+    Vec4<T> f[3];
+    muscl_faces(qi, zi, ok, cnt, qn, has, ln, dd, f);
 #pragma unroll
-        for (int k = 0; k < 3; k++) {
-            if (nb[k] < 0) continue;
-            T dx = dd[k].x, dy = dd[k].y;
-            Mxx += dx * dx; Mxy += dx * dy; Myy += dy * dy;
-#pragma unroll
-            for (int s = 0; s < 3; s++) {
-                T dq = qn[k][s] - qi[s];
-                bx[s] += dx * dq; by[s] += dy * dq;
-            }
-        }
-        T det = Mxx * Myy - Mxy * Mxy, tr = Mxx + Myy;
-        if (det > T(1e-12) * tr * tr) {
-#pragma unroll
-            for (int s = 0; s < 3; s++) {
-                T px = (Myy * bx[s] - Mxy * by[s]) / det;
-                T py = (Mxx * by[s] - Mxy * bx[s]) / det;
-                T qmin = qi[s], qmax = qi[s];
-#pragma unroll
-                for (int k = 0; k < 3; k++) {
-                    if (nb[k] < 0) continue;
-                    qmin = dmin(qmin, qn[k][s]);
-                    qmax = dmax(qmax, qn[k][s]);
-                }
-                T phi = T(1);
-#pragma unroll
-                for (int k = 0; k < 3; k++) {
-                    T d = px * ox[k] + py * oy[k];
-                    T ph = T(1);
-                    if (d > T(0)) ph = (qmax - qi[s]) / d;
-                    else if (d < T(0)) ph = (qmin - qi[s]) / d;
-                    phi = dmin(phi, ph);
-                }
-                gx[s] = phi * px; gy[s] = phi * py;
-            }
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-        Vec4<T> f;
-        f.x = qi[0] + (gx[0] * ox[k] + gy[0] * oy[k]);
-        f.y = qi[1] + (gx[1] * ox[k] + gy[1] * oy[k]);
-        f.z = qi[2] + (gx[2] * ox[k] + gy[2] * oy[k]);
-        f.w = zi;
-        F[3 * i + k] = f;
-    }
+    for (int k = 0; k < 3; k++) F[3 * i + k] = f[k];
 }
 
 // WAF: centre primitives P[i] = (h, u, v, z) and, per edge k, the mean of
@@ -157,152 +107,48 @@ __global__ void k_prep_waf(StepArgs<T> a, Vec4<T> *P, Vec4<T> *U)
 }
 
 // ---------------------------------------------------------------------------
-// flux + update kernel
+// flux + update kernel (split path): neighbours through global memory
 // ---------------------------------------------------------------------------
+template <typename T> struct GlobalSrc {
+    const StepArgs<T> &a;
+    int64_t i;
+    __device__ Vec4<T> own_face(int k) const { return a.F[3 * i + k]; }
+    __device__ Vec4<T> nbr_face(const Nb &b) const { return a.F[3 * (int64_t)b.idx + b.kj]; }
+    __device__ Vec4<T> nbr_centre(const Nb &b) const { return a.F[b.idx]; }
+    __device__ Vec4<T> own_up(int k) const { return a.U[3 * i + k]; }
+    __device__ Vec4<T> nbr_up(const Nb &b) const { return a.U[3 * (int64_t)b.idx + b.kj]; }
+    __device__ Vec4<T> nbr_state(const Nb &b) const
+    {
+        Vec4<T> q;
+        q.x = a.h[b.idx]; q.y = a.hu[b.idx]; q.z = a.hv[b.idx]; q.w = a.m.z[b.idx];
+        return q;
+    }
+};
+
 template <typename T, int SCHEME>
 __global__ void k_flux(StepArgs<T> a)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = i < a.m.n;
     bool dry;
-    const T dt = step_dt(a, &dry);
-    const T g = a.g, h_eps = a.h_eps, half = T(0.5);
-    T smax = T(0);
-    double clip = 0.0, bsum = 0.0;
-    if (valid) {
-        const T hi = a.h[i], hui = a.hu[i], hvi = a.hv[i], zi = a.m.z[i];
-        int nb[3];
-        Vec2<T> ln[3];
-#pragma unroll
-        for (int k = 0; k < 3; k++) { nb[k] = a.m.nbr[3 * i + k]; ln[k] = a.m.ln[3 * i + k]; }
-        // own centre values
-        T ui, vi;
-        primitives(hi, hui, hvi, h_eps, ui, vi);
-        T R0 = T(0), R1 = T(0), R2 = T(0), bs = T(0);
+    const T dt = block_dt(a, &dry);
+    CellOut<T> o;
+    o.smax = T(0); o.clip = T(0); o.bsum = T(0);
+    if (i < a.m.n) {
+        Nb nb[3];
+        Vec2<T> ln[3], dd[3];
 #pragma unroll
         for (int k = 0; k < 3; k++) {
-            const T lx = ln[k].x, ly = ln[k].y;
-            const T L = dsqrt(lx * lx + ly * ly);
-            const T nx = lx / L, ny = ly / L;
-            // own face values (eta, u, v)
-            T ef, uf, vf;
-            if (SCHEME == SWE_SCHEME_MUSCL) {
-                Vec4<T> f = a.F[3 * i + k];
-                ef = f.x; uf = f.y; vf = f.z;
-            } else {
-                ef = hi + zi; uf = ui; vf = vi;
-            }
-            const T hf = dmax(ef - zi, T(0));
-            const T hyd = half * g * (hf - hi) * (hf + hi);
-            const int w = nb[k];
-            if (w >= 0) {
-                const int j = w >> 3, kj = (w >> 1) & 3;
-                const bool own = w & 1;
-                T ej, uj, vj, zj, hcj = T(0);
-                Vec4<T> Uj;
-                if (SCHEME == SWE_SCHEME_MUSCL) {
-                    Vec4<T> f = a.F[3 * j + kj];
-                    ej = f.x; uj = f.y; vj = f.z; zj = f.w;
-                } else if (SCHEME == SWE_SCHEME_WAF) {
-                    Vec4<T> p = a.F[j];
-                    hcj = p.x; uj = p.y; vj = p.z; zj = p.w;
-                    ej = hcj + zj;
-                    Uj = a.U[3 * j + kj];
-                } else {
-                    T hj = a.h[j];
-                    zj = a.m.z[j];
-                    primitives(hj, a.hu[j], a.hv[j], h_eps, uj, vj);
-                    ej = hj + zj;
-                }
-                // canonical orientation: side A is the owner of the edge
-                const T cnx = own ? nx : -nx, cny = own ? ny : -ny;
-                const T eA = own ? ef : ej, eB = own ? ej : ef;
-                const T uAx = own ? uf : uj, uAy = own ? vf : vj;
-                const T uBx = own ? uj : uf, uBy = own ? vj : vf;
-                const T zf = dmax(zi, zj);
-                const T hsA = dmax(eA - zf, T(0)), hsB = dmax(eB - zf, T(0));
-                const T unA = uAx * cnx + uAy * cny, vtA = -uAx * cny + uAy * cnx;
-                const T unB = uBx * cnx + uBy * cny, vtB = -uBx * cny + uBy * cnx;
-                Flux<T> fl;
-                if (SCHEME == SWE_SCHEME_WAF) {
-                    const Vec4<T> Ui = a.U[3 * i + k];
-                    const Vec2<T> d = a.m.dd[3 * i + k];
-                    WafIn<T> wi;
-                    wi.dtdx = dt / dsqrt(d.x * d.x + d.y * d.y);
-                    const Vec4<T> &UA = own ? Ui : Uj;
-                    const Vec4<T> &UB = own ? Uj : Ui;
-                    wi.hupL = UA.x; wi.hupR = UB.x;
-                    wi.vupL = -UA.y * cny + UA.z * cnx;
-                    wi.vupR = -UB.y * cny + UB.z * cnx;
-                    wi.hcL = own ? hi : hcj; wi.hcR = own ? hcj : hi;
-                    fl = riemann<T, true>(hsA, unA, vtA, hsB, unB, vtB, g, h_eps, wi, a.waf_limiter, a.r_eps);
-                } else {
-                    WafIn<T> wi{};
-                    fl = riemann<T, false>(hsA, unA, vtA, hsB, unB, vtB, g, h_eps, wi, 0, a.r_eps);
-                }
-                const T P = (own ? hsA * unA * unA + fl.DL2 : hsB * unB * unB + fl.DR2) + hyd;
-                const T sM = own ? fl.M : -fl.M;
-                R0 += L * sM;
-                R1 += L * (P * nx - fl.Tt * ny);
-                R2 += L * (P * ny + fl.Tt * nx);
-            } else {
-                // boundary edge, normal outward (Sec. 5.1)
-                const int tag = -1 - w, kind = tag & 3, grp = tag >> 2;
-                const T un = uf * nx + vf * ny, vt = -uf * ny + vf * nx;
-                T M, P, Tt;
-                if (kind == SWE_WALL) {
-                    M = T(0); P = hyd; Tt = T(0);
-                } else if (kind == SWE_OPEN) {
-                    M = hf * un; P = hf * un * un + hyd; Tt = M * vt;
-                } else if (kind == SWE_INFLOW) {
-                    const T q = a.qlen[grp];
-                    M = -q; P = (hf > h_eps ? q * q / hf : T(0)) + hyd; Tt = T(0);
-                } else {
-                    const T hg = dmax(a.level[grp] - zi, T(0));
-                    WafIn<T> wi{};
-                    Flux<T> fl = riemann<T, false>(hf, un, vt, hg, un, vt, g, h_eps, wi, 0, a.r_eps);
-                    M = fl.M; P = hf * un * un + fl.DL2 + hyd; Tt = fl.Tt;
-                }
-                R0 += L * M;
-                R1 += L * (P * nx - Tt * ny);
-                R2 += L * (P * ny + Tt * nx);
-                bs -= L * M;
-            }
+            nb[k] = decode_global(a.m.nbr[3 * i + k]);
+            ln[k] = a.m.ln[3 * i + k];
+            if (SCHEME == SWE_SCHEME_WAF) dd[k] = a.m.dd[3 * i + k];
         }
-        // explicit Euler update (area from the scaled normals: |e_0 x e_1| / 2)
-        const T area = half * (ln[0].x * ln[1].y - ln[0].y * ln[1].x);
-        const T r = dt / area;
-        T hn = hi - r * R0, hun = hui - r * R1, hvn = hvi - r * R2;
-        if (hn < T(0)) { clip = -(double)hn * (double)area; hn = T(0); }
-        if (hn <= h_eps) {
-            hun = T(0); hvn = T(0);
-        } else if (a.m.nman) {
-            const T nm = a.m.nman[i];
-            if (nm > T(0)) {            // point-implicit Manning friction
-                const T sp = dsqrt(hun * hun + hvn * hvn) / hn;
-                const T fr = T(1) + dt * g * nm * nm * sp / (hn * dcbrt(hn));
-                hun /= fr; hvn /= fr;
-            }
-        }
-        a.ho[i] = hn; a.huo[i] = hun; a.hvo[i] = hvn;
-        if (!(dfinite(hn) && dfinite(hun) && dfinite(hvn))) atomicOr(&a.sc->status, ST_NONFINITE);
-        if (hn > h_eps) {
-            const T u = hun / hn, v = hvn / hn;
-            smax = dsqrt(g * hn) + dsqrt(u * u + v * v);
-        }
-        bsum = (double)bs * (double)dt;
+        const T nm = a.m.nman ? a.m.nman[i] : T(0);
+        GlobalSrc<T> src{a, i};
+        o = cell_update<T, SCHEME>(a, dt, a.h[i], a.hu[i], a.hv[i], a.m.z[i], nm, nb, ln, dd, src);
+        a.ho[i] = o.h; a.huo[i] = o.hu; a.hvo[i] = o.hv;
+        if (!(dfinite(o.h) && dfinite(o.hu) && dfinite(o.hv))) atomicOr(&a.sc->status, ST_NONFINITE);
     }
-    const bool euler = a.mode == MODE_EULER;
-    block_publish<T>(smax, clip, bsum, a.sc, a.slot_next, euler, euler ? 1.0 : 0.5);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        if (dry) atomicOr(&a.sc->status, ST_DRY);
-        if (euler) {
-            a.dt_hist[a.sc->steps % SWE_DT_HISTORY] = (double)dt;
-            a.sc->t += (double)dt;
-            a.sc->steps += 1;
-            a.sc->smax[a.slot_clear] = 0ULL;
-        }
-    }
+    step_epilogue<T>(a, dt, dry, o.smax, o.clip, o.bsum);
 }
 
 // Wave speed of the current state into slot `slot` (CFL rule of Sec. 5.1).
@@ -318,7 +164,7 @@ __global__ void k_smax(StepArgs<T> a, int slot)
             s = dsqrt(a.g * h) + dsqrt(u * u + v * v);
         }
     }
-    block_publish<T>(s, 0.0, 0.0, a.sc, slot, true, 1.0);
+    block_publish<T>(s, T(0), T(0), a.sc, slot, true, 1.0);
 }
 
 // Heun: U^{n+1} = (U^n + U2) / 2 with U2 = E(E(U^n)); then the wave speed.
@@ -335,7 +181,7 @@ __global__ void k_heun_avg(StepArgs<T> a, const T *h0, const T *hu0, const T *hv
             s = dsqrt(a.g * h) + dsqrt(u * u + v * v);
         }
     }
-    block_publish<T>(s, 0.0, 0.0, a.sc, a.slot_next, true, 1.0);
+    block_publish<T>(s, T(0), T(0), a.sc, a.slot_next, true, 1.0);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         bool dry;
         T dt = step_dt(a, &dry);

@@ -55,53 +55,74 @@ def test_fp64_hllc_config1_200_steps_cfl():
     assert g["steps"] == 200
 
 
+KERNELS = ["split", "fused"]
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("scheme", ["hllc", "muscl", "waf"])
-def test_fp64_partial_dam_break(scheme):
+def test_fp64_partial_dam_break(scheme, kernel):
     """Jittered mesh, Gaussian bed, ~30 % dry, breach, Manning: 1 and 100 steps."""
     w = _pdb()
-    g1, o1 = run_gpu(w, scheme, steps=1), run_oracle(w, scheme, steps=1)
+    g1, o1 = run_gpu(w, scheme, steps=1, kernel=kernel), run_oracle(w, scheme, steps=1)
     assert max(state_errors(g1, o1)) <= 1e-12
     o = run_oracle(w, scheme, steps=100)
-    g = run_gpu(w, scheme, dt=o["dts"])
+    g = run_gpu(w, scheme, dt=o["dts"], kernel=kernel)
     errs = state_errors(g, o)
     assert max(errs) <= 1e-9, errs
-    gc = run_gpu(w, scheme, steps=100)
+    gc = run_gpu(w, scheme, steps=100, kernel=kernel)
     assert math.isclose(gc["t"], o["t"], rel_tol=1e-9)
 
 
-@pytest.mark.parametrize("scheme", ["hllc", "muscl"])
-def test_fp64_river_inflow_level_friction(scheme):
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("scheme", ["hllc", "muscl", "waf"])
+def test_fp64_river_inflow_level_friction(scheme, kernel):
     w = _river()
     o = run_oracle(w, scheme, steps=100)
-    g = run_gpu(w, scheme, dt=o["dts"])
+    g = run_gpu(w, scheme, dt=o["dts"], kernel=kernel)
     assert max(state_errors(g, o)) <= 1e-9
     assert math.isclose(g["bnd_in"], o["bnd_in"], rel_tol=1e-9)
 
 
-def test_fp64_heun():
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_fp64_heun(kernel):
     w = _pdb(60, 30)
     o = run_oracle(w, "muscl", steps=40, time_scheme="heun")
-    g = run_gpu(w, "muscl", dt=o["dts"], time_scheme="heun")
+    g = run_gpu(w, "muscl", dt=o["dts"], time_scheme="heun", kernel=kernel)
     assert max(state_errors(g, o)) <= 1e-9
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("block", [64, 128, 512])
-def test_fp64_block_sizes(block):
+def test_fp64_block_sizes(block, kernel):
+    """Block (and, for the fused kernel, tile) sizes; 33x17 squares = 1122 cells, ragged tail."""
     w = _pdb(33, 17)
     o = run_oracle(w, "muscl", steps=10)
-    g = run_gpu(w, "muscl", dt=o["dts"], block=block)
+    g = run_gpu(w, "muscl", dt=o["dts"], block=block, kernel=kernel)
     assert max(state_errors(g, o)) <= 1e-11
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("scheme", ["muscl", "waf"])
+def test_split_and_fused_kernels_agree_bitwise(precision, scheme):
+    """The fused tile kernel runs the same per-cell code as the split kernels."""
+    w = _river(90, 34)
+    a = run_gpu(w, scheme, precision, steps=50, kernel="split")
+    for block in (128, 256):
+        b = run_gpu(w, scheme, precision, steps=50, kernel="fused", block=block)
+        for k in ("h", "hu", "hv"):
+            assert np.array_equal(a[k], b[k]), (block, k)
 
 
 # ---- invariants on the GPU ----------------------------------------------------
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("scheme", ["hllc", "muscl", "waf"])
-def test_lake_at_rest_bitwise(precision, scheme):
+def test_lake_at_rest_bitwise(precision, scheme, kernel):
     w = W.partial_dam_break(nx=80, ny=40, spacing=1.0, n_gauss=40, breach=False, seed=9)
     w.bnd_tag = np.full(len(w.bnd_edges), W.tag(W.LEVEL), np.int32)
     w.level = np.array([2.0])
-    g = run_gpu(w, scheme, precision, steps=1000)
+    g = run_gpu(w, scheme, precision, steps=1000, kernel=kernel)
     assert np.array_equal(g["h"], w.h)
     assert not g["hu"].any() and not g["hv"].any()
 
@@ -122,13 +143,14 @@ def test_mass_budget_with_inflow():
     assert abs(g["mass"] - o["mass0"] - g["clipped"] - g["bnd_in"]) <= 1e-12 * o["mass0"]
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_renumbering_is_bitwise_invisible(precision):
+def test_renumbering_is_bitwise_invisible(precision, kernel):
     """Morton, RCM and the original order give the same bits (cf. Sec. 5.3.1)."""
     w = _pdb(50, 24)
-    ref = run_gpu(w, "muscl", precision, steps=60, reorder="none")
+    ref = run_gpu(w, "muscl", precision, steps=60, reorder="none", kernel=kernel)
     for r in ("morton", "rcm"):
-        g = run_gpu(w, "muscl", precision, steps=60, reorder=r)
+        g = run_gpu(w, "muscl", precision, steps=60, reorder=r, kernel=kernel)
         for k in ("h", "hu", "hv"):
             assert np.array_equal(g[k], ref[k]), (r, k)
         assert g["t"] == ref["t"]
@@ -136,13 +158,14 @@ def test_renumbering_is_bitwise_invisible(precision):
 
 # ---- FP32 against the FP64 oracle ----------------------------------------------
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("scheme", ["muscl", "waf", "hllc"])
-def test_fp32_error_against_oracle(scheme):
+def test_fp32_error_against_oracle(scheme, kernel):
     """FP32 state and fluxes (FP64 mass and time): relative L1 of h after 1000
     replayed steps <= 1e-4, mass drift <= 1e-6 (same h_eps on both sides)."""
     w = _river(80, 30)
     o = run_oracle(w, scheme, steps=1000, h_eps=1e-4, r_eps=1e-6)
-    g = run_gpu(w, scheme, "fp32", dt=o["dts"])
+    g = run_gpu(w, scheme, "fp32", dt=o["dts"], kernel=kernel)
     assert rel_l1(g["h"], o["h"]) <= 1e-4
     drift = abs(g["mass"] - o["mass0"] - g["clipped"] - g["bnd_in"]) / o["mass0"]
     assert drift <= 1e-6

@@ -263,8 +263,19 @@ int state_init(StateT<T> &s, const swe_mesh *m, const double *h, const double *h
     for (int b = 0; b < nbuf; b++) {
         s.h[b] = s.template alloc<T>(n); s.hu[b] = s.template alloc<T>(n); s.hv[b] = s.template alloc<T>(n);
     }
-    s.fused = s.p.scheme != SWE_SCHEME_HLLC &&
-              (s.p.kernel == SWE_KERNEL_FUSED || s.p.kernel == SWE_KERNEL_AUTO);
+    // automatic choice: the split kernels (measured faster on GB300 for both
+    // precisions); the fused tile kernel on request
+    s.fused = s.p.scheme != SWE_SCHEME_HLLC && s.p.kernel == SWE_KERNEL_FUSED;
+    {
+        const int want = s.p.block > 0 ? s.p.block : 256;
+        const int lim = s.fused ? fused_max_threads<T>(s.p.scheme) : split_max_threads<T>(s.p.scheme);
+        if (lim <= 0) { swe_set_error("swe_state_init: cannot query the kernels (no usable GPU?)"); return SWE_ERR_CUDA; }
+        if (want > lim) {
+            swe_set_error("swe_state_init: block of " + std::to_string(want) + " threads exceeds the kernel's limit of " +
+                          std::to_string(lim));
+            return SWE_ERR_ARG;
+        }
+    }
     Tiling tl;
     if (s.fused) {
         const int tile = s.p.block > 0 ? s.p.block : 256;

@@ -99,5 +99,7 @@ cudaError_t launch_convert(int64_t n, const double *src, T *dst, cudaStream_t s)
 template <typename T>
 cudaError_t launch_fused(int scheme, const StepArgs<T> &a, const FusedArgs &f, cudaStream_t s);
 template <typename T> size_t fused_smem_bytes(int scheme, int slots);
+template <typename T> int fused_max_threads(int scheme);     // launch limit of the fused kernel (registers)
+template <typename T> int split_max_threads(int scheme);     // launch limit of the split kernels
 
 int mass_partials_needed(int64_t n);

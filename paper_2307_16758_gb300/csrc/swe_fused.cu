@@ -199,6 +199,14 @@ __global__ void k_fused(StepArgs<T> a, FusedArgs f)
 
 }  // namespace
 
+template <typename T> int fused_max_threads(int scheme)
+{
+    cudaFuncAttributes fa{};
+    cudaError_t e = scheme == SWE_SCHEME_WAF ? cudaFuncGetAttributes(&fa, k_fused<T, SWE_SCHEME_WAF>)
+                                             : cudaFuncGetAttributes(&fa, k_fused<T, SWE_SCHEME_MUSCL>);
+    return e == cudaSuccess ? fa.maxThreadsPerBlock : 0;
+}
+
 template <typename T> size_t fused_smem_bytes(int scheme, int slots)
 {
     (void)scheme;
@@ -225,4 +233,6 @@ cudaError_t launch_fused(int scheme, const StepArgs<T> &a, const FusedArgs &f, c
 template cudaError_t launch_fused<float>(int, const StepArgs<float> &, const FusedArgs &, cudaStream_t);
 template cudaError_t launch_fused<double>(int, const StepArgs<double> &, const FusedArgs &, cudaStream_t);
 template size_t fused_smem_bytes<float>(int, int);
+template int fused_max_threads<float>(int);
+template int fused_max_threads<double>(int);
 template size_t fused_smem_bytes<double>(int, int);

@@ -260,6 +260,18 @@ inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 
 
 }  // namespace
 
+template <typename T> int split_max_threads(int scheme)
+{
+    cudaFuncAttributes fa{};
+    cudaError_t e;
+    if (scheme == SWE_SCHEME_MUSCL) e = cudaFuncGetAttributes(&fa, k_flux<T, SWE_SCHEME_MUSCL>);
+    else if (scheme == SWE_SCHEME_WAF) e = cudaFuncGetAttributes(&fa, k_flux<T, SWE_SCHEME_WAF>);
+    else e = cudaFuncGetAttributes(&fa, k_flux<T, SWE_SCHEME_HLLC>);
+    return e == cudaSuccess ? fa.maxThreadsPerBlock : 0;
+}
+template int split_max_threads<float>(int);
+template int split_max_threads<double>(int);
+
 int mass_partials_needed(int64_t n) { return (int)((n + MASS_BLOCK * MASS_ITEMS - 1) / (MASS_BLOCK * MASS_ITEMS)); }
 
 template <typename T>

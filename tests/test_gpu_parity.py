@@ -91,14 +91,22 @@ def test_fp64_heun(kernel):
     assert max(state_errors(g, o)) <= 1e-9
 
 
-@pytest.mark.parametrize("kernel", KERNELS)
-@pytest.mark.parametrize("block", [64, 128, 512])
+@pytest.mark.parametrize("kernel,block", [("split", 64), ("split", 128), ("split", 512),
+                                          ("fused", 64), ("fused", 128), ("fused", 256)])
 def test_fp64_block_sizes(block, kernel):
     """Block (and, for the fused kernel, tile) sizes; 33x17 squares = 1122 cells, ragged tail."""
     w = _pdb(33, 17)
     o = run_oracle(w, "muscl", steps=10)
     g = run_gpu(w, "muscl", dt=o["dts"], block=block, kernel=kernel)
     assert max(state_errors(g, o)) <= 1e-11
+
+
+def test_block_above_the_kernel_limit_is_rejected():
+    """FP64 tiles of 1024 threads need more registers than a block has: a host error."""
+    w = _pdb(20, 10)
+    with pytest.raises(swe.SweError) as e:
+        run_gpu(w, "muscl", "fp64", steps=1, kernel="fused", block=1024)
+    assert e.value.code == -1
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])

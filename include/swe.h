@@ -3,11 +3,11 @@
  *
  * The library advances the 2D shallow-water equations (h, hu, hv) on an
  * unstructured triangle mesh with bathymetry by explicit finite-volume steps
- * (Delmas & Soulaimani, arXiv 2307.16758, Sec. 5.1: the semi-discrete form
+ * (Delmas & Soulaimani, arXiv 2307.16758, Sec. 6.1: the semi-discrete form
  * |Omega_i| dU_i/dt = -sum_j L_ij T^-1 G~(T U_i, T U_j) + sources, explicit
  * Euler in time, CFL time step with the inscribed radius).  Fluxes are HLLC
- * (Sec. 5.2.1), HLLC on MUSCL states (least-squares gradients with a
- * Barth-Jespersen limiter) or WAF (Sec. 5.2.2), with a well-balanced
+ * (Sec. 6.2.1), HLLC on MUSCL states (least-squares gradients with a
+ * Barth-Jespersen limiter) or WAF (Sec. 6.2.2), with a well-balanced
  * hydrostatic reconstruction, wet/dry handling and Manning friction.  Every
  * step runs in CUDA kernels for sm_103a; the host side only builds the mesh,
  * copies inputs and outputs, and launches.
@@ -66,8 +66,8 @@ typedef struct swe_ensemble swe_ensemble;
 typedef struct {
     int scheme;       /* SWE_SCHEME_*; HLLC first order, MUSCL-HLLC or WAF-HLLC */
     int precision;    /* SWE_FP64, or SWE_FP32 (FP32 state and fluxes; mass and time in FP64) */
-    int time_scheme;  /* SWE_EULER (Sec. 5.1) or SWE_HEUN (two Euler stages averaged) */
-    int waf_limiter;  /* SWE_WAF_* (Sec. 5.2.2; SUPERBEE is the paper's choice) */
+    int time_scheme;  /* SWE_EULER (Sec. 6.1) or SWE_HEUN (two Euler stages averaged) */
+    int waf_limiter;  /* SWE_WAF_* (Sec. 6.2.2; SUPERBEE is the paper's choice) */
     double g;         /* gravity [m/s^2] */
     double h_eps;     /* depth below which a cell counts as dry [m] */
     double r_eps;     /* WAF: relative size of a local change treated as zero */
@@ -98,7 +98,7 @@ int swe_set_allocator(swe_alloc_fn alloc, swe_free_fn free_fn, void *ctx);
 
 /* ---- Mesh (host only) -------------------------------------------------- */
 
-/* Build a mesh (Sec. 5.1 notation: cells Omega_i, sides L_ij, normals n_ij).
+/* Build a mesh (Sec. 6.1 notation: cells Omega_i, sides L_ij, normals n_ij).
  *  node_xy[n_nodes][2] FP64 coordinates; tri[n_tri][3] node ids (any
  *  orientation; the library orients counter-clockwise);
  *  bnd_edges[n_bnd][2] node pairs on the boundary with bnd_tag[n_bnd]
@@ -113,7 +113,7 @@ int swe_mesh_create(const double *node_xy, int64_t n_nodes,
                     const int32_t *cut_edges, int64_t n_cut,
                     int reorder, swe_mesh **out);
 int swe_mesh_destroy(swe_mesh *m);
-/* Number of cells and the smallest inscribed radius (CFL rule, Sec. 5.1). */
+/* Number of cells and the smallest inscribed radius (CFL rule, Sec. 6.1). */
 int swe_mesh_info(const swe_mesh *m, int64_t *n_cells, double *r_min);
 
 /* Export the builder's arrays in the library's (new) cell order; any pointer
@@ -144,7 +144,7 @@ int swe_set_stream(swe_state *s, void *stream);
 int swe_set_state(swe_state *s, const double *h, const double *hu, const double *hv);
 
 /* Advance n_steps explicit steps with the CFL rule dt = cfl * r_min / max_wet(sqrt(g h)+|u|)
- * (Sec. 5.1).  Asynchronous: returns once the work is enqueued. */
+ * (Sec. 6.1).  Asynchronous: returns once the work is enqueued. */
 int swe_step(swe_state *s, int n_steps, double cfl);
 /* Advance with a given time-step sequence dt[n_steps] (host array). */
 int swe_step_dt(swe_state *s, const double *dt, int n_steps);

@@ -1,27 +1,27 @@
 /*
  * swe_oracle.c -- plain FP64 CPU oracle for the explicit finite-volume
- * shallow-water step of Delmas & Soulaimani (arXiv 2307.16758), Section 5.
+ * shallow-water step of Delmas & Soulaimani (arXiv 2307.16758), Section 6.
  *
  * TEST INFRASTRUCTURE ONLY.  It is loaded by the tests, by the smoke check
  * and by the benchmark's CPU-baseline leg; the product library never links,
  * includes or calls it, and it shares no code with the CUDA path.
  *
  * It is written to be read against the paper, not to be fast: one loop per
- * step of the algorithm, in the order of Section 5.1-5.2, FP64 throughout.
+ * step of the algorithm, in the order of Sec. 6.1-6.2, FP64 throughout.
  * Parity status of each function (what pins it) is listed in the tests and in
  * the design notes; every function here is pinned (nothing is "parity
  * unpinned").
  *
  * Readings of passages the paper leaves open (the numbering is the one used
  * in the design notes):
- *  R1  p_k of the HLL speed estimate (Sec. 5.2.1) is dimensionally garbled;
+ *  R1  p_k of the HLL speed estimate (Sec. 6.2.1) is dimensionally garbled;
  *      it is read as p_k = sqrt(h*(h*+h_k)/2)/h_k for h* > h_k, else 1.
  *  R1b two-rarefaction h*: the bracket is clipped at 0 before squaring
  *      (a vacuum forms when it is negative).
- *  R2  HLLC third component (Sec. 5.2.1): the upwind tangential velocity is
+ *  R2  HLLC third component (Sec. 6.2.1): the upwind tangential velocity is
  *      v_L when S* >= 0 and v_R otherwise (the printed cases are swapped;
- *      the WAF passive weights of Sec. 5.2.2 agree with this reading).
- *  R3  WAF limited weights (Sec. 5.2.2): Toro's TVD form,
+ *      the WAF passive weights of Sec. 6.2.2 agree with this reading).
+ *  R3  WAF limited weights (Sec. 6.2.2): Toro's TVD form,
  *      w_L=(1+sgn(c_L)A_L)/2, w_LR=(sgn(c_R)A_R-sgn(c_L)A_L)/2,
  *      w_R=(1-sgn(c_R)A_R)/2, w_L*=(1+sgn(c*)A*)/2, w_R*=(1-sgn(c*)A*)/2,
  *      sgn(0)=+1.  The weights sum to 1; phi=1 gives the unlimited weights.
@@ -36,16 +36,16 @@
  *      flux-difference form (F - G(U*_s)) and the cell-centre pressure
  *      g/2 h_i^2 n (which sums to zero round a closed triangle) is removed, so
  *      that a lake at rest is preserved bit for bit.
- *  R7  Inflow (Sec. 5.1): mass flux -q enters the cell; normal momentum flux
+ *  R7  Inflow (Sec. 6.1): mass flux -q enters the cell; normal momentum flux
  *      q^2/h + g h^2/2 (the q^2/h term dropped when h <= h_eps); q = Q / total
  *      length of the inflow edges of the group.
  *  R8  Fixed-level boundary (not in the paper): ghost depth
  *      max(0, eta_out - z_i), ghost velocity = inner velocity, HLLC.
- *  R9  Manning friction (named in Sec. 5.1, no formula): point-implicit
+ *  R9  Manning friction (named in Sec. 6.1, no formula): point-implicit
  *      (hu,hv) <- (hu,hv) / (1 + dt g n^2 |u| h^(-4/3)) after the flux update.
- *  R10 Explicit Euler (Sec. 5.1) is the time scheme; Heun is offered only for
+ *  R10 Explicit Euler (Sec. 6.1) is the time scheme; Heun is offered only for
  *      the convergence-order study.
- *  R11 CFL (Sec. 5.1): dt = CFL * min_i r_i / max_wet(sqrt(g h)+|u|).
+ *  R11 CFL (Sec. 6.1): dt = CFL * min_i r_i / max_wet(sqrt(g h)+|u|).
  *  R12 Each interior edge is evaluated in one canonical orientation (L = the
  *      cell with the lower original id), so both cells see the same flux.
  *  R13 MUSCL: unweighted least-squares gradients of (eta,u,v) over the face
@@ -228,7 +228,7 @@ int om_mesh_build(const double *xy, int64_t n_nodes, const int32_t *tri_in, int6
     free(bk);
     if (matched != n_bnd) goto bad;   /* a listed boundary edge is not on the boundary */
 
-    /* Geometry (Sec. 5.1: |Omega_i|, L_ij, n_ij; inscribed radius R_L of the CFL rule). */
+    /* Geometry (Sec. 6.1: |Omega_i|, L_ij, n_ij; inscribed radius R_L of the CFL rule). */
     for (int64_t i = 0; i < n; i++) {
         const int32_t *t = &m->tri[3 * i];
         double x0 = xy[2 * t[0]], y0 = xy[2 * t[0] + 1];
@@ -362,10 +362,10 @@ int om_rcm_order(const om_mesh *m, int32_t *perm)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Riemann problem in the rotated frame (Sec. 5.2.1 and 5.2.2)               */
+/* Riemann problem in the rotated frame (Sec. 6.2.1 and 5.2.2)               */
 /* ------------------------------------------------------------------------ */
 
-/* Wave-speed estimates S_L, S_R of Sec. 5.2.1 with readings R1, R1b, R5. */
+/* Wave-speed estimates S_L, S_R of Sec. 6.2.1 with readings R1, R1b, R5. */
 static void hll_speeds(double g, double h_eps, double hL, double uL, double hR, double uR,
                        double *SL, double *SR)
 {
@@ -398,7 +398,7 @@ static void hll_speeds(double g, double h_eps, double hL, double uL, double hR, 
     *SR = uR + aR * pR;
 }
 
-/* SUPERBEE-type WAF limiter A(r,c) of Sec. 5.2.2 (phi selects the variants). */
+/* SUPERBEE-type WAF limiter A(r,c) of Sec. 6.2.2 (phi selects the variants). */
 static double waf_A(int lim, double r, double c)
 {
     double ac = fabs(c);
@@ -422,7 +422,7 @@ static double waf_ratio(double r_eps, double upw, double qL, double qR)
 
 /* The edge flux; see om_edge_flux in the header for in/waf/out.
  * For each side s the numerical flux is written as G(U*_s) + D_s with
- * D_s = F - G(U*_s):  HLL (three branches of Sec. 5.2.1) gives, in the star
+ * D_s = F - G(U*_s):  HLL (three branches of Sec. 6.2.1) gives, in the star
  * region, D_L = S_L (S_R dU - dG)/(S_R - S_L) and D_R = S_R (S_L dU - dG)/(S_R - S_L),
  * which is the printed star flux minus G_L or G_R rearranged (R6). */
 static void edge_flux(const om_opts *o, int scheme, const double *in, const double *waf, double *out)
@@ -443,11 +443,11 @@ static void edge_flux(const om_opts *o, int scheme, const double *in, const doub
     } else {
         double SL, SR;
         hll_speeds(g, h_eps, hsL, uL, hsR, uR, &SL, &SR);
-        /* S* of Sec. 5.2.1 */
+        /* S* of Sec. 6.2.1 */
         double num = SL * hsR * (uR - SR) - SR * hsL * (uL - SL);
         double den = hsR * (uR - SR) - hsL * (uL - SL);
         double Ss = den != 0.0 ? num / den : 0.0;
-        /* HLL, Sec. 5.2.1, as differences to G_L and G_R */
+        /* HLL, Sec. 6.2.1, as differences to G_L and G_R */
         double hL1, hL2, hR1, hR2;
         if (SL >= 0.0) {
             hL1 = 0.0; hL2 = 0.0; hR1 = -dG1; hR2 = -dG2;
@@ -465,7 +465,7 @@ static void edge_flux(const om_opts *o, int scheme, const double *in, const doub
             if (SR <= 0.0 && !(SL >= 0.0)) M = GR1;
             T = M * (Ss >= 0.0 ? vL : vR);
         } else {
-            /* WAF of Sec. 5.2.2 with the TVD weights of reading R3 */
+            /* WAF of Sec. 6.2.2 with the TVD weights of reading R3 */
             double dtdx = waf[0];
             double hupL = waf[1], hupR = waf[2], vupL = waf[3], vupR = waf[4];
             double hcl = waf[5], hcr = waf[6];
@@ -581,7 +581,7 @@ int om_gradients(const om_mesh *m, const om_opts *o, const double *z,
 }
 
 /* ------------------------------------------------------------------------ */
-/* One explicit Euler step (Sec. 5.1, eq. of the semi-discrete form)         */
+/* One explicit Euler step (Sec. 6.1, eq. of the semi-discrete form)         */
 /* ------------------------------------------------------------------------ */
 
 typedef struct {
@@ -678,7 +678,7 @@ static void euler_stage(const om_mesh *m, const om_opts *o, work_t *w,
                 R[2] += L * (P * ny + T * nx);
                 continue;
             }
-            /* boundary edge: cell i is the left state, normal outward (Sec. 5.1) */
+            /* boundary edge: cell i is the left state, normal outward (Sec. 6.1) */
             int tag = m->btag[3 * i + k], type = tag & 3, grp = tag >> 2;
             double un = fi[1] * nx + fi[2] * ny, vt = -fi[1] * ny + fi[2] * nx;
             double hyd = 0.5 * g * (hfi - h[i]) * (hfi + h[i]);
@@ -783,7 +783,7 @@ int om_run(const om_mesh *m, const om_opts *o,
         if (dt_given) {
             dt = dt_given[s];
         } else {
-            /* CFL rule of Sec. 5.1 with d = inscribed radius (R11) */
+            /* CFL rule of Sec. 6.1 with d = inscribed radius (R11) */
             double smax = 0.0;
             for (int64_t i = 0; i < n; i++) {
                 if (h[i] <= o->h_eps) continue;

@@ -1,7 +1,7 @@
 /*
  * swe_oracle.h -- plain FP64 CPU oracle for the explicit finite-volume step of
  * the 2D shallow-water equations on triangles (Delmas & Soulaimani,
- * arXiv 2307.16758, Section 5).
+ * arXiv 2307.16758, Section 6).
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, includes
  * or calls this code; only the tests, the smoke check and the benchmark's

@@ -1,5 +1,5 @@
 // Device functions shared by the split kernels (swe_kernels.cu) and the fused
-// tile kernel (swe_fused.cu): the Riemann solver of Sec. 5.2, the MUSCL face
+// tile kernel (swe_fused.cu): the Riemann solver of Sec. 6.2, the MUSCL face
 // values, WAF helpers and the block reductions.  Both kernels inline the same
 // code, so a cell gets the same bits whichever kernel computes it.
 #pragma once
@@ -31,7 +31,7 @@ __device__ __forceinline__ bool dfinite(double x) { return isfinite(x); }
 // tangential (v) velocities of both sides.  Outputs: the mass flux M, the
 // tangential momentum flux Tt and, for each side s, D_s = F_2 - G_2(U*_s),
 // the normal-momentum flux minus that side's physical flux.  In the star
-// region of HLL (Sec. 5.2.1),
+// region of HLL (Sec. 6.2.1),
 //   F - G_L = S_L (S_R dU - dG) / (S_R - S_L),  F - G_R = S_R (S_L dU - dG) / (S_R - S_L),
 // which is the printed star flux rearranged so that equal states give an
 // exact zero (well-balancing).
@@ -54,7 +54,7 @@ __device__ __forceinline__ T waf_ratio(T r_eps, T upw, T qL, T qR)
     return ddiv(upw, loc);
 }
 
-// A(r, c) of Sec. 5.2.2 (SUPERBEE), or its phi = 1 / phi = 0 variants.
+// A(r, c) of Sec. 6.2.2 (SUPERBEE), or its phi = 1 / phi = 0 variants.
 template <typename T>
 __device__ __forceinline__ T waf_A(int lim, T r, T c)
 {
@@ -331,7 +331,7 @@ __device__ __forceinline__ Nb decode_local(unsigned w)
 template <typename T> struct CellOut { T h, hu, hv, smax, clip, bsum; };
 
 // Edge fluxes, explicit Euler update, clipping, Manning friction and the new
-// wave speed of one cell (Sec. 5.1-5.2), shared by the split and fused
+// wave speed of one cell (Sec. 6.1-5.2), shared by the split and fused
 // kernels.  Data of the cell and of its neighbours come through `src`:
 //   MUSCL: own_face(k), nbr_face(nb) -> (eta, u, v, z) at the edge midpoint
 //   WAF  : own_centre(), nbr_centre(nb) -> (h, u, v, z); own_up(k), nbr_up(nb) -> upwind means
@@ -409,7 +409,7 @@ __device__ __forceinline__ CellOut<T> cell_update(const StepArgs<T> &a, T dt, T 
             R1 += L * (P * nx - fl.Tt * ny);
             R2 += L * (P * ny + fl.Tt * nx);
         } else {
-            // boundary edge, normal outward (Sec. 5.1)
+            // boundary edge, normal outward (Sec. 6.1)
             const int tag = nb[k].tag, kind = tag & 3, grp = tag >> 2;
             const T un = uf * nx + vf * ny, vt = -uf * ny + vf * nx;
             T M, P, Tt;

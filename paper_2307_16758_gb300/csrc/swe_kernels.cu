@@ -1,13 +1,13 @@
 // CUDA kernels of the explicit finite-volume shallow-water step (sm_103a).
 //
-// One time step (Sec. 5.1 of Delmas & Soulaimani, arXiv 2307.16758):
+// One time step (Sec. 6.1 of Delmas & Soulaimani, arXiv 2307.16758):
 //   prep  : per cell, the values each cell shows at the midpoints of its three
 //           edges -- MUSCL: least-squares gradients of (eta, u, v) limited
 //           with Barth-Jespersen; WAF: the cell's primitives and, per edge,
-//           the mean of its two other neighbours (the upwind data of Sec. 5.2.2).
+//           the mean of its two other neighbours (the upwind data of Sec. 6.2.2).
 //   flux  : per cell, for its three edges: hydrostatic reconstruction, the
-//           HLLC (Sec. 5.2.1) or WAF (Sec. 5.2.2) flux in the canonical edge
-//           frame, boundary fluxes (Sec. 5.1), the explicit Euler update,
+//           HLLC (Sec. 6.2.1) or WAF (Sec. 6.2.2) flux in the canonical edge
+//           frame, boundary fluxes (Sec. 6.1), the explicit Euler update,
 //           depth clipping, point-implicit Manning friction, and the wave
 //           speed of the new state reduced (warp shuffle, then one atomicMax
 //           per block) for the next CFL time step.
@@ -151,7 +151,7 @@ __global__ void k_flux(StepArgs<T> a)
     step_epilogue<T>(a, dt, dry, o.smax, o.clip, o.bsum);
 }
 
-// Wave speed of the current state into slot `slot` (CFL rule of Sec. 5.1).
+// Wave speed of the current state into slot `slot` (CFL rule of Sec. 6.1).
 template <typename T>
 __global__ void k_smax(StepArgs<T> a, int slot)
 {

@@ -1,12 +1,12 @@
 // Host mesh builder: orientation, edge adjacency, boundary tags, geometry and
 // a locality renumbering (Morton or reverse Cuthill-McKee).
 //
-// The adjacency follows the idea of the paper's pre-processing (Sec. 4: cells
+// The adjacency follows the idea of the paper's pre-processing (Sec. 3.1: cells
 // are connected through their shared edges, found from a map of edges); here
 // the edges are sorted by their node pair instead of hashed, which keeps the
 // result deterministic.  The renumbering plays the role of the paper's
-// renumbering for locality (Sec. 4.3) on a single GPU.  Geometry follows the
-// notation of Sec. 5.1 (|Omega_i|, L_ij, n_ij) and the inscribed radius R_L
+// renumbering for locality (Sec. 3.3) on a single GPU.  Geometry follows the
+// notation of Sec. 6.1 (|Omega_i|, L_ij, n_ij) and the inscribed radius R_L
 // of the CFL rule.  Compiled without floating-point contraction so that every
 // geometric quantity is reproducible bit for bit.
 #include <algorithm>

@@ -4,10 +4,10 @@ This module only builds inputs (node coordinates, triangles, boundary tags,
 bed elevation, Manning coefficients, initial depth and discharge); it holds
 none of the solver's arithmetic.  The same arrays feed the CUDA path and the
 FP64 oracle.  The paper's meshes and bathymetry (the Mille-Iles river and the
-Montreal archipelago, Sec. 5.5) are not available, so these generators stand
+Montreal archipelago, Sec. 6.5) are not available, so these generators stand
 in for them at the sizes of the benchmark workloads:
 
-* ``dam_break_1d``  -- the idealised wet-bed dam break of Sec. 5.3, as a strip
+* ``dam_break_1d``  -- the idealised wet-bed dam break of Sec. 6.3, as a strip
   of squares split by their "/" diagonal (the 100 m x 10 m case is 2000 cells).
 * ``partial_dam_break`` -- a jittered 1 m structured triangulation, a bed made
   of seeded Gaussians on a 0.1 % slope, a lake at rest at eta = 2 m with about
@@ -130,7 +130,7 @@ def _empty_edges():
 def dam_break_1d(nx: int = 100, ny: int = 10, lx: float = 100.0, ly: float = 10.0,
                  h_left: float = 1.0, h_right: float = 0.5, v_left: float = 0.0, v_right: float = 0.0,
                  x_dam: float | None = None, open_ends: bool = False) -> Workload:
-    """Idealised wet-bed dam break (Sec. 5.3), walls all round by default.
+    """Idealised wet-bed dam break (Sec. 6.3), walls all round by default.
 
     Optional tangential velocities v_left / v_right add a passive shear layer."""
     nodes, tris, bnd, side = structured(nx, ny, lx, ly)
@@ -212,7 +212,7 @@ def _fractal_noise(shape, rng, std):
 def river(nx: int = 4160, ny: int = 1563, lx: float = 40000.0, ly: float = 15000.0,
           seed: int = 20230733, q_in: float = 8000.0, n_channel: float = 0.025,
           n_floodplain: float = 0.05, level_quantile: float = 0.5, jitter: float = 0.25) -> Workload:
-    """Meandering river in a floodplain (stand-in for the Mille-Iles mesh of Sec. 5.5).
+    """Meandering river in a floodplain (stand-in for the Mille-Iles mesh of Sec. 6.5).
 
     Centreline y = ly/2 + A sin(2 pi x / lambda) with A = 0.262 lambda
     (sinuosity 1.5) and lambda = 5.5 km +-20 %; width 200-800 m and depth

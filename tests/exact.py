@@ -1,7 +1,7 @@
 """Closed-form solutions used to pin the oracle (no solver code here).
 
 The dam-break problems are Riemann problems of the 1D shallow-water
-equations with zero initial velocity (Sec. 5.3 of the paper refers to Toro's
+equations with zero initial velocity (Sec. 6.3 of the paper refers to Toro's
 book for the analytical solution).  The left rarefaction and the right shock
 (wet bed, Stoker) or the single rarefaction reaching a dry front (Ritter)
 follow from the Riemann invariants and the Rankine-Hugoniot relations.

@@ -154,7 +154,7 @@ def test_mass_budget_with_inflow():
 @pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_renumbering_is_bitwise_invisible(precision, kernel):
-    """Morton, RCM and the original order give the same bits (cf. Sec. 5.3.1)."""
+    """Morton, RCM and the original order give the same bits (cf. Sec. 6.3.1)."""
     w = _pdb(50, 24)
     ref = run_gpu(w, "muscl", precision, steps=60, reorder="none", kernel=kernel)
     for r in ("morton", "rcm"):

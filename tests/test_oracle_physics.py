@@ -37,7 +37,7 @@ def _l1(m, q, qex):
 
 
 # --------------------------------------------------------------------------
-# Sec. 5.3: the paper's worked example, against the closed form
+# Sec. 6.3: the paper's worked example, against the closed form
 # --------------------------------------------------------------------------
 
 @pytest.mark.parametrize("scheme", ["hllc", "muscl", "waf"])
@@ -61,7 +61,7 @@ def test_paper_dam_break_converges_to_closed_form(scheme):
 
 
 def test_second_order_beats_first_order():
-    """Sec. 5.3: WAF and MUSCL are closer to the closed form than HLLC."""
+    """Sec. 6.3: WAF and MUSCL are closer to the closed form than HLLC."""
     w = W.dam_break_1d(95, 13, 10.0, 1.0, 1.0, 0.5, x_dam=5.0)
     m = _mesh(w)
     dt = np.full(1000, 1.0 / 1000)
@@ -159,7 +159,7 @@ def test_mass_conserved_with_walls(scheme):
 
 
 def test_inflow_adds_exactly_q_times_t():
-    """Inflow boundary (Sec. 5.1): the only mass source is Q per unit time."""
+    """Inflow boundary (Sec. 6.1): the only mass source is Q per unit time."""
     w = W.river(nx=80, ny=30, seed=4, q_in=500.0)
     w.bnd_tag = np.where((w.bnd_tag & 3) == W.LEVEL, W.tag(W.WALL), w.bnd_tag).astype(np.int32)
     m = _mesh(w)
@@ -220,7 +220,7 @@ def test_rotation_by_90_degrees(scheme):
 
 
 def test_cell_renumbering_does_not_change_the_solution():
-    """The same mesh under another cell numbering gives the same solution (cf. Sec. 5.3.1)."""
+    """The same mesh under another cell numbering gives the same solution (cf. Sec. 6.3.1)."""
     w = W.partial_dam_break(nx=24, ny=12, spacing=1.0, n_gauss=8, seed=5)
     m = _mesh(w)
     p = np.random.default_rng(1).permutation(w.n_cells)
@@ -359,7 +359,7 @@ def test_flux_dry_bed_and_both_dry():
 
 
 def test_waf_phi0_is_hllc_and_weights_are_upwind():
-    """WAF with phi = 0 (A = 1) reduces to the first-order HLLC flux (Sec. 5.2.2)."""
+    """WAF with phi = 0 (A = 1) reduces to the first-order HLLC flux (Sec. 6.2.2)."""
     rng = np.random.default_rng(2)
     for _ in range(300):
         st = _state(rng.uniform(0.05, 3), rng.uniform(-3, 3), rng.uniform(-1, 1),
@@ -443,7 +443,7 @@ def test_gradient_is_zero_next_to_a_dry_cell():
 
 
 def test_first_time_step_closed_form():
-    """CFL rule of Sec. 5.1 with d = inscribed radius: on unit right triangles
+    """CFL rule of Sec. 6.1 with d = inscribed radius: on unit right triangles
     r = (2 - sqrt 2)/2, and at rest the fastest speed is sqrt(g h_max)."""
     w = W.dam_break_1d()
     m = _mesh(w)

@@ -179,6 +179,39 @@ int swe_profile_end(swe_state *s, double *kernel_ms, int64_t *launches);
 /* The last n time steps taken (oldest first), n <= min(steps taken, SWE_DT_HISTORY). */
 int swe_dt_history(swe_state *s, double *dt, int n);
 
+/* ---- One step without device allocation ---------------------------------- */
+
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory -- a plug-in inside an application that
+ * owns the GPU's memory pools, or a real-time loop where an allocation could
+ * block -- and therefore cannot create a swe_state.
+ *
+ * One MUSCL-HLLC explicit Euler step in FP32 (the same kernels as swe_step
+ * with SWE_KERNEL_SPLIT) on caller-owned device buffers, with a given dt.
+ * Inputs, in the library's cell order (see swe_mesh_export):
+ *  nbr[3n]  packed neighbour words: (nbr << 3) | (nbr_edge << 1) | owner for
+ *           an interior edge, owner = 1 when perm[i] < perm[nbr]; -1 - btag on
+ *           a boundary edge;
+ *  ln[3n][2] scaled outward normals (lnx, lny), dd[3n][2] centroid offsets
+ *           (dx, dy), z[n] bed, manning_n[n] (may be NULL), h, hu, hv[n];
+ *  p: scheme SWE_SCHEME_MUSCL and precision SWE_FP32 (g, h_eps, r_eps, block
+ *     are used); inflow_qlen[n_inflow] inflow discharge per unit length
+ *     (m^2/s) per group; level[n_level] fixed levels; stream a cudaStream_t.
+ * Outputs h_out, hu_out, hv_out[n] (must not alias the inputs).
+ * The face values (48 bytes per cell) go to a scratch array compiled into
+ * the library (about 12.6 MB per GPU, held until the process exits), so
+ * n_cells must not exceed SWE_NOALLOC_MAX_CELLS (else SWE_ERR_ARG).  The
+ * first call on a GPU looks the array up (cudaGetSymbolAddress) with that GPU
+ * current: make it before any stream capture.  All calls on a GPU share the
+ * array, so calls that overlap on the GPU race.  Asynchronous on `stream`;
+ * no status is read back. */
+#define SWE_NOALLOC_MAX_CELLS 262144
+int swe_muscl_step_noalloc(int64_t n_cells, const int32_t *nbr, const float *ln, const float *dd,
+                           const float *z, const float *manning_n, const float *h, const float *hu,
+                           const float *hv, float *h_out, float *hu_out, float *hv_out, double dt,
+                           const swe_params *p, const float *inflow_qlen, int n_inflow,
+                           const float *level, int n_level, void *stream);
+
 /* ---- Ensemble ---------------------------------------------------------- */
 
 /* Group independent states (same precision, scheme and time scheme) so that

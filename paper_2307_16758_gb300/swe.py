@@ -36,7 +36,9 @@ EXPORTED = [
     "swe_set_state", "swe_step", "swe_step_dt", "swe_sync", "swe_get_state", "swe_mass", "swe_time",
     "swe_state_info", "swe_ensemble_create", "swe_ensemble_destroy", "swe_ensemble_step",
     "swe_ensemble_sync", "swe_profile_begin", "swe_profile_end", "swe_dt_history",
+    "swe_muscl_step_noalloc",
 ]
+NOALLOC_MAX_CELLS = 262144
 KERNEL_KINDS = ["prep", "flux", "heun_avg", "smax", "fused", "ensemble", "k6", "k7"]
 
 
@@ -98,6 +100,7 @@ def load_library(path: str = LIB_PATH, use_torch_allocator: bool = True):
     lib.swe_profile_begin.argtypes = [vp]
     lib.swe_profile_end.argtypes = [vp, vp, vp]
     lib.swe_dt_history.argtypes = [vp, vp, i32]
+    lib.swe_muscl_step_noalloc.argtypes = [i64] + [vp] * 11 + [dp, C.POINTER(Params), vp, i32, vp, i32, vp]
     if use_torch_allocator:
         import torch
 
@@ -269,6 +272,17 @@ def swe_dt_history(s, n):
     out = np.empty(n)
     _check(load_library().swe_dt_history(s, _p(out), int(n)))
     return out
+
+
+def swe_muscl_step_noalloc(n_cells, nbr, ln, dd, z, manning_n, h, hu, hv, h_out, hu_out, hv_out, dt,
+                           params: Params, inflow_qlen=(), level=(), stream=None):
+    """Device pointers (ints) in, device pointers out; no allocation inside."""
+    qa = np.ascontiguousarray(inflow_qlen, dtype=np.float32).reshape(-1)
+    la = np.ascontiguousarray(level, dtype=np.float32).reshape(-1)
+    _check(load_library().swe_muscl_step_noalloc(
+        int(n_cells), nbr, ln, dd, z, manning_n, h, hu, hv, h_out, hu_out, hv_out, float(dt), C.byref(params),
+        _p(qa) if len(qa) else None, len(qa), _p(la) if len(la) else None, len(la),
+        stream if stream is not None else _current_stream()))
 
 
 def swe_ensemble_create(states):

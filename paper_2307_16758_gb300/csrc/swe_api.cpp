@@ -151,7 +151,7 @@ template <typename T> struct StateT {
         return a;
     }
 
-    int block() const { return fused ? fa.tile : (p.block > 0 ? p.block : 256); }
+    int block() const { return fused ? fa.block : (p.block > 0 ? p.block : 256); }
 
     cudaError_t launch_step_kernels(const StepArgs<T> &a, int bl)
     {
@@ -278,18 +278,20 @@ int state_init(StateT<T> &s, const swe_mesh *m, const double *h, const double *h
     }
     Tiling tl;
     if (s.fused) {
-        const int tile = s.p.block > 0 ? s.p.block : 256;
-        if (swe_build_tiling(*m, tile, tl) != 0) { swe_set_error("swe_state_init: tile too large"); return SWE_ERR_ARG; }
-        s.fa.tile = tile;
-        s.fa.slots = tile + tl.max_halo;
-        if (fused_smem_bytes<T>(s.p.scheme, s.fa.slots) > 227 * 1024) {
+        const int block = s.p.block > 0 ? s.p.block : 256;
+        if (swe_build_tiling(*m, block, tl) != 0) { swe_set_error("swe_state_init: unsupported tile block"); return SWE_ERR_ARG; }
+        if (fused_smem_bytes<T>(s.p.scheme, block) > 227 * 1024) {
             swe_set_error("swe_state_init: tile needs more shared memory than a block has");
             return SWE_ERR_ARG;
         }
-        int32_t *hp = s.template alloc<int32_t>(tl.halo_ptr.size());
-        int32_t *hi = s.template alloc<int32_t>(std::max<size_t>(tl.halo_ids.size(), 1));
-        uint16_t *nl = s.template alloc<uint16_t>(3 * n);
-        s.fa.halo_ptr = hp; s.fa.halo_ids = hi; s.fa.nbr_local = nl;
+        s.fa.block = block;
+        s.fa.n_tiles = tl.n_tiles;
+        s.fa.tile_start = s.template alloc<int32_t>(tl.tile_start.size());
+        s.fa.halo_ptr = s.template alloc<int32_t>(tl.halo_ptr.size());
+        s.fa.halo_ids = s.template alloc<int32_t>(std::max<size_t>(tl.halo_ids.size(), 1));
+        s.fa.edge_ptr = s.template alloc<int32_t>(tl.edge_ptr.size());
+        s.fa.edges = s.template alloc<uint32_t>(std::max<size_t>(tl.edges.size(), 1));
+        s.fa.nbr_local = s.template alloc<uint16_t>(3 * n);
     } else {
         if (s.p.scheme == SWE_SCHEME_MUSCL) s.F = s.template alloc<Vec4<T>>(3 * n);
         if (s.p.scheme == SWE_SCHEME_WAF) { s.F = s.template alloc<Vec4<T>>(n); s.U = s.template alloc<Vec4<T>>(3 * n); }
@@ -313,13 +315,15 @@ int state_init(StateT<T> &s, const swe_mesh *m, const double *h, const double *h
     CK(cudaMemcpyAsync(s.area, m->area.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(s.sc, 0, sizeof(DevScalars), st));
     if (s.fused) {
-        CK(cudaMemcpyAsync((void *)s.fa.halo_ptr, tl.halo_ptr.data(), sizeof(int32_t) * tl.halo_ptr.size(),
-                           cudaMemcpyHostToDevice, st));
-        if (!tl.halo_ids.empty())
-            CK(cudaMemcpyAsync((void *)s.fa.halo_ids, tl.halo_ids.data(), sizeof(int32_t) * tl.halo_ids.size(),
-                               cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync((void *)s.fa.nbr_local, tl.nbr_local.data(), sizeof(uint16_t) * 3 * n,
-                           cudaMemcpyHostToDevice, st));
+        auto up = [&](const void *dst, const void *src, size_t bytes) {
+            return bytes ? cudaMemcpyAsync((void *)dst, src, bytes, cudaMemcpyHostToDevice, st) : cudaSuccess;
+        };
+        CK(up(s.fa.tile_start, tl.tile_start.data(), sizeof(int32_t) * tl.tile_start.size()));
+        CK(up(s.fa.halo_ptr, tl.halo_ptr.data(), sizeof(int32_t) * tl.halo_ptr.size()));
+        CK(up(s.fa.halo_ids, tl.halo_ids.data(), sizeof(int32_t) * tl.halo_ids.size()));
+        CK(up(s.fa.edge_ptr, tl.edge_ptr.data(), sizeof(int32_t) * tl.edge_ptr.size()));
+        CK(up(s.fa.edges, tl.edges.data(), sizeof(uint32_t) * tl.edges.size()));
+        CK(up(s.fa.nbr_local, tl.nbr_local.data(), sizeof(uint16_t) * 3 * n));
     }
     // initial state through the same path as swe_set_state
     CK(cudaMemcpyAsync(s.staging, h, sizeof(double) * n, cudaMemcpyHostToDevice, st));

@@ -61,17 +61,22 @@ template <typename T> struct StepArgs {
     T level[SWE_MAX_GROUPS];    // fixed free-surface levels [m]
 };
 
-// Fused tile kernel: the cells of tile b are [b*tile, (b+1)*tile); the tile's
-// halo (neighbours outside it) is halo_ids[halo_ptr[b] .. halo_ptr[b+1]).
-// nbr_local[3n] gives, per cell edge, (slot << 3) | (neighbour's local edge << 1)
-// | owner with slot < tile for tile cells and tile + q for halo cell q, or
-// 0x8000 | tag on a boundary.
+// Fused tile kernel (see swe_tiles.cpp): tile b holds the cells
+// [tile_start[b], tile_start[b+1]) in slots 0..nc-1 and its halo
+// halo_ids[halo_ptr[b] .. halo_ptr[b+1]) in the following slots.
+// nbr_local[3n]: (slot << 3) | (neighbour's local edge << 1) | owner, or
+// 0x8000 | tag on a boundary.  edges[edge_ptr[b] .. edge_ptr[b+1]): one word
+// per interior edge with a tile cell on side i: slot_i | k_i << 9 |
+// slot_j << 11 | k_j << 20 | owner_i << 22 | j_in_tile << 23.
 struct FusedArgs {
+    const int32_t *tile_start;
     const int32_t *halo_ptr;
     const int32_t *halo_ids;
+    const int32_t *edge_ptr;
+    const uint32_t *edges;
     const uint16_t *nbr_local;
-    int tile;       // cells per tile = threads per block
-    int slots;      // tile + largest halo
+    int n_tiles;
+    int block;      // threads per block (largest tile + halo)
 };
 
 // Launchers (defined in swe_kernels.cu and swe_fused.cu).  All launches go to `stream`.
@@ -98,7 +103,7 @@ cudaError_t launch_convert(int64_t n, const double *src, T *dst, cudaStream_t s)
 
 template <typename T>
 cudaError_t launch_fused(int scheme, const StepArgs<T> &a, const FusedArgs &f, cudaStream_t s);
-template <typename T> size_t fused_smem_bytes(int scheme, int slots);
+template <typename T> size_t fused_smem_bytes(int scheme, int block);
 template <typename T> int fused_max_threads(int scheme);     // launch limit of the fused kernel (registers)
 template <typename T> int split_max_threads(int scheme);     // launch limit of the split kernels
 

@@ -20,8 +20,9 @@ __device__ __forceinline__ double ddiv(double a, double b) { return a / b; }
 __device__ __forceinline__ float ddiv(float a, float b) { return __fdividef(a, b); }
 template <typename T> __device__ __forceinline__ T dmax(T a, T b) { return a > b ? a : b; }
 template <typename T> __device__ __forceinline__ T dmin(T a, T b) { return a < b ? a : b; }
-__device__ __forceinline__ float dcbrt(float x) { return cbrtf(x); }
-__device__ __forceinline__ double dcbrt(double x) { return cbrt(x); }
+// h^(4/3) of the Manning term: FP64 h * cbrt(h); FP32 the fast exp2/log2 form.
+__device__ __forceinline__ float dpow43(float x) { return __powf(x, 4.0f / 3.0f); }
+__device__ __forceinline__ double dpow43(double x) { return x * cbrt(x); }
 __device__ __forceinline__ bool dfinite(float x) { return isfinite(x); }
 __device__ __forceinline__ bool dfinite(double x) { return isfinite(x); }
 
@@ -330,109 +331,138 @@ __device__ __forceinline__ Nb decode_local(unsigned w)
 
 template <typename T> struct CellOut { T h, hu, hv, smax, clip, bsum; };
 
-// Edge fluxes, explicit Euler update, clipping, Manning friction and the new
-// wave speed of one cell (Sec. 6.1-5.2), shared by the split and fused
-// kernels.  Data of the cell and of its neighbours come through `src`:
-//   MUSCL: own_face(k), nbr_face(nb) -> (eta, u, v, z) at the edge midpoint
-//   WAF  : own_centre(), nbr_centre(nb) -> (h, u, v, z); own_up(k), nbr_up(nb) -> upwind means
-//   HLLC : nbr_state(nb) -> (h, hu, hv, z)
-template <typename T, int SCHEME, typename Src>
-__device__ __forceinline__ CellOut<T> cell_update(const StepArgs<T> &a, T dt, T hi, T hui, T hvi, T zi, T nm,
-                                                  const Nb nb[3], const Vec2<T> ln[3], const Vec2<T> dd[3],
-                                                  const Src &src)
+// Products and sums that the compiler must not fuse, so that an edge's
+// contribution and a cell's sum of contributions have the same bits whether
+// the edge is evaluated by the cell (split kernels) or once per edge (fused).
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+
+// Edge length and unit normal from the scaled normal (FP32: one rsqrt).
+__device__ __forceinline__ void unit_normal(float lx, float ly, float &L, float &nx, float &ny)
+{
+    const float l2 = lx * lx + ly * ly;
+    const float ri = rsqrtf(l2);
+    L = l2 * ri; nx = lx * ri; ny = ly * ri;
+}
+__device__ __forceinline__ void unit_normal(double lx, double ly, double &L, double &nx, double &ny)
+{
+    L = sqrt(lx * lx + ly * ly);
+    nx = lx / L; ny = ly / L;
+}
+
+// Contribution of one edge to its cell's flux sum: L * (M, P n - Tt t) with t = (-n_y, n_x).
+template <typename T> struct Contrib { T c0, c1, c2; };
+
+template <typename T>
+__device__ __forceinline__ Contrib<T> contribution(T L, T sM, T P, T Tt, T nx, T ny)
+{
+    Contrib<T> c;
+    c.c0 = mul_rn(L, sM);
+    c.c1 = mul_rn(L, P * nx - Tt * ny);
+    c.c2 = mul_rn(L, P * ny + Tt * nx);
+    return c;
+}
+
+// One side of an edge: the free surface and velocities at the edge midpoint,
+// the cell's bed and its cell-centre depth.
+template <typename T> struct Side { T ef, uf, vf, z, hc; };
+
+// Interior edge seen from side i (scaled outward normal (lx, ly) of i):
+// hydrostatic reconstruction, canonical-orientation Riemann flux, and the
+// contribution to i -- and, if cj is given, to j (normal -n).
+template <typename T, int SCHEME>
+__device__ __forceinline__ void interior_edge(const StepArgs<T> &a, T dt, const Side<T> &si, const Side<T> &sj,
+                                              bool own_i, T lx, T ly, T dlen, const Vec4<T> &Ui,
+                                              const Vec4<T> &Uj, Contrib<T> &ci, Contrib<T> *cj)
+{
+    const T g = a.g, h_eps = a.h_eps, half = T(0.5);
+    T L, nx, ny;
+    unit_normal(lx, ly, L, nx, ny);
+    // canonical orientation: side A is the owner of the edge
+    const T cnx = own_i ? nx : -nx, cny = own_i ? ny : -ny;
+    const Side<T> &A = own_i ? si : sj;
+    const Side<T> &B = own_i ? sj : si;
+    const T zf = dmax(si.z, sj.z);
+    const T hsA = dmax(A.ef - zf, T(0)), hsB = dmax(B.ef - zf, T(0));
+    const T unA = A.uf * cnx + A.vf * cny, vtA = -A.uf * cny + A.vf * cnx;
+    const T unB = B.uf * cnx + B.vf * cny, vtB = -B.uf * cny + B.vf * cnx;
+    Flux<T> fl;
+    if (SCHEME == SWE_SCHEME_WAF) {
+        WafIn<T> wi;
+        wi.dtdx = ddiv(dt, dlen);
+        const Vec4<T> &UA = own_i ? Ui : Uj;
+        const Vec4<T> &UB = own_i ? Uj : Ui;
+        wi.hupL = UA.x; wi.hupR = UB.x;
+        wi.vupL = -UA.y * cny + UA.z * cnx;
+        wi.vupR = -UB.y * cny + UB.z * cnx;
+        wi.hcL = A.hc; wi.hcR = B.hc;
+        fl = riemann<T, true>(hsA, unA, vtA, hsB, unB, vtB, g, h_eps, wi, a.waf_limiter, a.r_eps);
+    } else {
+        WafIn<T> wi{};
+        fl = riemann<T, false>(hsA, unA, vtA, hsB, unB, vtB, g, h_eps, wi, 0, a.r_eps);
+    }
+    const T PA = hsA * unA * unA + fl.DL2, PB = hsB * unB * unB + fl.DR2;
+    const T hfi = dmax(si.ef - si.z, T(0));
+    const T Pi = (own_i ? PA : PB) + half * g * (hfi - si.hc) * (hfi + si.hc);
+    const T sMi = own_i ? fl.M : -fl.M;
+    ci = contribution(L, sMi, Pi, fl.Tt, nx, ny);
+    if (cj) {
+        const T hfj = dmax(sj.ef - sj.z, T(0));
+        const T Pj = (own_i ? PB : PA) + half * g * (hfj - sj.hc) * (hfj + sj.hc);
+        const T sMj = own_i ? -fl.M : fl.M;
+        *cj = contribution(L, sMj, Pj, fl.Tt, -nx, -ny);
+    }
+}
+
+// Boundary edge of cell i (outward normal, Sec. 6.1): wall, open, inflow,
+// fixed level.  bs receives the mass that leaves, -L*M.
+template <typename T>
+__device__ __forceinline__ Contrib<T> boundary_edge(const StepArgs<T> &a, const Side<T> &si, int tag, T lx, T ly,
+                                                    T &bs)
+{
+    const T g = a.g, h_eps = a.h_eps, half = T(0.5);
+    T L, nx, ny;
+    unit_normal(lx, ly, L, nx, ny);
+    const T hf = dmax(si.ef - si.z, T(0));
+    const T hyd = half * g * (hf - si.hc) * (hf + si.hc);
+    const int kind = tag & 3, grp = tag >> 2;
+    const T un = si.uf * nx + si.vf * ny, vt = -si.uf * ny + si.vf * nx;
+    T M, P, Tt;
+    if (kind == SWE_WALL) {
+        M = T(0); P = hyd; Tt = T(0);
+    } else if (kind == SWE_OPEN) {
+        M = hf * un; P = hf * un * un + hyd; Tt = M * vt;
+    } else if (kind == SWE_INFLOW) {
+        const T q = a.qlen[grp];
+        M = -q; P = (hf > h_eps ? ddiv(q * q, hf) : T(0)) + hyd; Tt = T(0);
+    } else {
+        const T hg = dmax(a.level[grp] - si.z, T(0));
+        WafIn<T> wi{};
+        Flux<T> fl = riemann<T, false>(hf, un, vt, hg, un, vt, g, h_eps, wi, 0, a.r_eps);
+        M = fl.M; P = hf * un * un + fl.DL2 + hyd; Tt = fl.Tt;
+    }
+    bs -= L * M;
+    return contribution(L, M, P, Tt, nx, ny);
+}
+
+// Add contribution k (k = 0, 1, 2 in this order) to the cell's sum.
+template <typename T>
+__device__ __forceinline__ void accumulate(int k, const Contrib<T> &c, T &R0, T &R1, T &R2)
+{
+    if (k == 0) { R0 = c.c0; R1 = c.c1; R2 = c.c2; }
+    else { R0 = add_rn(R0, c.c0); R1 = add_rn(R1, c.c1); R2 = add_rn(R2, c.c2); }
+}
+
+// Explicit Euler update, clipping, point-implicit Manning friction and the
+// wave speed of the new state.  Area from the scaled normals: |e_0 x e_1|/2.
+template <typename T>
+__device__ __forceinline__ CellOut<T> cell_finish(const StepArgs<T> &a, T dt, T hi, T hui, T hvi, T R0, T R1, T R2,
+                                                  const Vec2<T> ln[3], T nm, T bs)
 {
     const T g = a.g, h_eps = a.h_eps, half = T(0.5);
     CellOut<T> o;
-    T ui, vi;
-    primitives(hi, hui, hvi, h_eps, ui, vi);
-    T R0 = T(0), R1 = T(0), R2 = T(0), bs = T(0);
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-        const T lx = ln[k].x, ly = ln[k].y;
-        const T L = dsqrt(lx * lx + ly * ly);
-        const T nx = ddiv(lx, L), ny = ddiv(ly, L);
-        T ef, uf, vf;
-        if (SCHEME == SWE_SCHEME_MUSCL) {
-            Vec4<T> f = src.own_face(k);
-            ef = f.x; uf = f.y; vf = f.z;
-        } else {
-            ef = hi + zi; uf = ui; vf = vi;
-        }
-        const T hf = dmax(ef - zi, T(0));
-        const T hyd = half * g * (hf - hi) * (hf + hi);
-        if (nb[k].interior) {
-            const bool own = nb[k].own;
-            T ej, uj, vj, zj, hcj = T(0);
-            Vec4<T> Uj;
-            if (SCHEME == SWE_SCHEME_MUSCL) {
-                Vec4<T> f = src.nbr_face(nb[k]);
-                ej = f.x; uj = f.y; vj = f.z; zj = f.w;
-            } else if (SCHEME == SWE_SCHEME_WAF) {
-                Vec4<T> p = src.nbr_centre(nb[k]);
-                hcj = p.x; uj = p.y; vj = p.z; zj = p.w;
-                ej = hcj + zj;
-                Uj = src.nbr_up(nb[k]);
-            } else {
-                Vec4<T> q = src.nbr_state(nb[k]);
-                zj = q.w;
-                primitives(q.x, q.y, q.z, h_eps, uj, vj);
-                ej = q.x + zj;
-            }
-            // canonical orientation: side A is the owner of the edge
-            const T cnx = own ? nx : -nx, cny = own ? ny : -ny;
-            const T eA = own ? ef : ej, eB = own ? ej : ef;
-            const T uAx = own ? uf : uj, uAy = own ? vf : vj;
-            const T uBx = own ? uj : uf, uBy = own ? vj : vf;
-            const T zf = dmax(zi, zj);
-            const T hsA = dmax(eA - zf, T(0)), hsB = dmax(eB - zf, T(0));
-            const T unA = uAx * cnx + uAy * cny, vtA = -uAx * cny + uAy * cnx;
-            const T unB = uBx * cnx + uBy * cny, vtB = -uBx * cny + uBy * cnx;
-            Flux<T> fl;
-            if (SCHEME == SWE_SCHEME_WAF) {
-                const Vec4<T> Ui = src.own_up(k);
-                WafIn<T> wi;
-                wi.dtdx = ddiv(dt, dsqrt(dd[k].x * dd[k].x + dd[k].y * dd[k].y));
-                const Vec4<T> &UA = own ? Ui : Uj;
-                const Vec4<T> &UB = own ? Uj : Ui;
-                wi.hupL = UA.x; wi.hupR = UB.x;
-                wi.vupL = -UA.y * cny + UA.z * cnx;
-                wi.vupR = -UB.y * cny + UB.z * cnx;
-                wi.hcL = own ? hi : hcj; wi.hcR = own ? hcj : hi;
-                fl = riemann<T, true>(hsA, unA, vtA, hsB, unB, vtB, g, h_eps, wi, a.waf_limiter, a.r_eps);
-            } else {
-                WafIn<T> wi{};
-                fl = riemann<T, false>(hsA, unA, vtA, hsB, unB, vtB, g, h_eps, wi, 0, a.r_eps);
-            }
-            const T P = (own ? hsA * unA * unA + fl.DL2 : hsB * unB * unB + fl.DR2) + hyd;
-            const T sM = own ? fl.M : -fl.M;
-            R0 += L * sM;
-            R1 += L * (P * nx - fl.Tt * ny);
-            R2 += L * (P * ny + fl.Tt * nx);
-        } else {
-            // boundary edge, normal outward (Sec. 6.1)
-            const int tag = nb[k].tag, kind = tag & 3, grp = tag >> 2;
-            const T un = uf * nx + vf * ny, vt = -uf * ny + vf * nx;
-            T M, P, Tt;
-            if (kind == SWE_WALL) {
-                M = T(0); P = hyd; Tt = T(0);
-            } else if (kind == SWE_OPEN) {
-                M = hf * un; P = hf * un * un + hyd; Tt = M * vt;
-            } else if (kind == SWE_INFLOW) {
-                const T q = a.qlen[grp];
-                M = -q; P = (hf > h_eps ? ddiv(q * q, hf) : T(0)) + hyd; Tt = T(0);
-            } else {
-                const T hg = dmax(a.level[grp] - zi, T(0));
-                WafIn<T> wi{};
-                Flux<T> fl = riemann<T, false>(hf, un, vt, hg, un, vt, g, h_eps, wi, 0, a.r_eps);
-                M = fl.M; P = hf * un * un + fl.DL2 + hyd; Tt = fl.Tt;
-            }
-            R0 += L * M;
-            R1 += L * (P * nx - Tt * ny);
-            R2 += L * (P * ny + Tt * nx);
-            bs -= L * M;
-        }
-    }
-    // explicit Euler update (area from the scaled normals: |e_0 x e_1| / 2)
     const T area = half * (ln[0].x * ln[1].y - ln[0].y * ln[1].x);
     const T r = ddiv(dt, area);
     T hn = hi - r * R0, hun = hui - r * R1, hvn = hvi - r * R2;
@@ -440,9 +470,9 @@ __device__ __forceinline__ CellOut<T> cell_update(const StepArgs<T> &a, T dt, T 
     if (hn < T(0)) { o.clip = -hn * area; hn = T(0); }
     if (hn <= h_eps) {
         hun = T(0); hvn = T(0);
-    } else if (nm > T(0)) {            // point-implicit Manning friction
+    } else if (nm > T(0)) {
         const T sp = ddiv(dsqrt(hun * hun + hvn * hvn), hn);
-        const T fr = T(1) + ddiv(dt * g * nm * nm * sp, hn * dcbrt(hn));
+        const T fr = T(1) + ddiv(dt * g * nm * nm * sp, dpow43(hn));
         hun = ddiv(hun, fr); hvn = ddiv(hvn, fr);
     }
     o.h = hn; o.hu = hun; o.hv = hvn;
@@ -453,6 +483,58 @@ __device__ __forceinline__ CellOut<T> cell_update(const StepArgs<T> &a, T dt, T 
     }
     o.bsum = bs * dt;
     return o;
+}
+
+// Edge fluxes and update of one cell, all three edges evaluated by the cell
+// (split kernels).  Data of the cell and of its neighbours come through `src`:
+//   MUSCL: own_face(k), nbr_face(nb) -> (eta, u, v, z) at the edge midpoint
+//   WAF  : nbr_centre(nb) -> (h, u, v, z); own_up(k), nbr_up(nb) -> upwind means
+//   HLLC : nbr_state(nb) -> (h, hu, hv, z)
+template <typename T, int SCHEME, typename Src>
+__device__ __forceinline__ CellOut<T> cell_update(const StepArgs<T> &a, T dt, T hi, T hui, T hvi, T zi, T nm,
+                                                  const Nb nb[3], const Vec2<T> ln[3], const Vec2<T> dd[3],
+                                                  const Src &src)
+{
+    const T h_eps = a.h_eps;
+    T ui, vi;
+    primitives(hi, hui, hvi, h_eps, ui, vi);
+    T R0 = T(0), R1 = T(0), R2 = T(0), bs = T(0);
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        Side<T> si;
+        si.z = zi; si.hc = hi;
+        if (SCHEME == SWE_SCHEME_MUSCL) {
+            const Vec4<T> f = src.own_face(k);
+            si.ef = f.x; si.uf = f.y; si.vf = f.z;
+        } else {
+            si.ef = hi + zi; si.uf = ui; si.vf = vi;
+        }
+        Contrib<T> c;
+        if (nb[k].interior) {
+            Side<T> sj;
+            Vec4<T> Ui{}, Uj{};
+            T dlen = T(0);
+            if (SCHEME == SWE_SCHEME_MUSCL) {
+                const Vec4<T> f = src.nbr_face(nb[k]);
+                sj.ef = f.x; sj.uf = f.y; sj.vf = f.z; sj.z = f.w; sj.hc = T(0);
+            } else if (SCHEME == SWE_SCHEME_WAF) {
+                const Vec4<T> p = src.nbr_centre(nb[k]);
+                sj.hc = p.x; sj.uf = p.y; sj.vf = p.z; sj.z = p.w; sj.ef = p.x + p.w;
+                Ui = src.own_up(k);
+                Uj = src.nbr_up(nb[k]);
+                dlen = dsqrt(dd[k].x * dd[k].x + dd[k].y * dd[k].y);
+            } else {
+                const Vec4<T> q = src.nbr_state(nb[k]);
+                sj.hc = q.x; sj.z = q.w; sj.ef = q.x + q.w;
+                primitives(q.x, q.y, q.z, h_eps, sj.uf, sj.vf);
+            }
+            interior_edge<T, SCHEME>(a, dt, si, sj, nb[k].own, ln[k].x, ln[k].y, dlen, Ui, Uj, c, nullptr);
+        } else {
+            c = boundary_edge<T>(a, si, nb[k].tag, ln[k].x, ln[k].y, bs);
+        }
+        accumulate(k, c, R0, R1, R2);
+    }
+    return cell_finish<T>(a, dt, hi, hui, hvi, R0, R1, R2, ln, nm, bs);
 }
 
 // Step epilogue: publish the block's wave speed and diagnostics; block 0

@@ -1,17 +1,22 @@
 // Fused tile kernel: one launch per time step does the whole second-order
 // step (MUSCL face values or WAF upwind data, edge fluxes, update, friction
 // and the wave-speed reduction) for a tile of consecutive (Morton-ordered)
-// cells, so the face values never go to HBM.
+// cells, so face values never go to HBM and every Riemann problem inside a
+// tile is solved once.
 //
-//   phase 0: primitives of the tile's cells (coalesced) and of its halo
-//            cells (gathered) into shared memory;
-//   phase 1: face values (MUSCL) or upwind means (WAF) of the tile's cells,
-//            from shared memory, and of the halo cells, from global memory
-//            (their own neighbours may lie outside the tile);
-//   phase 2: per cell, the fluxes of its three edges from shared memory and
-//            the update -- the same device code as the split kernels.
-// Each cell reads its state, bed, Manning n, normals, centroid offsets and
-// tile-local neighbour slots once and writes its state once.
+// A block holds a tile (nc cells, slots 0..nc-1) and its halo (H cells,
+// slots nc..nc+H-1), nc + H <= blockDim.x, so each thread owns one slot:
+//   phase 0: the slot's state -> primitives in shared memory;
+//   phase 1: the slot's face values (MUSCL) or upwind means (WAF): tile cells
+//            read their neighbours from shared memory, halo cells gather
+//            theirs from global memory;
+//   phase 2: the tile's edge list, one thread per edge: hydrostatic
+//            reconstruction and Riemann flux once per edge, contributions to
+//            both sides written to shared memory;
+//   phase 3: each tile cell adds its three contributions in edge order
+//            (boundary edges computed here) and updates.
+// The per-edge and per-cell arithmetic is the same device code as the split
+// kernels (swe_device.cuh), so both give the same bits.
 #include <cuda_runtime.h>
 
 #include "swe_dev.h"
@@ -20,16 +25,23 @@
 namespace {
 using namespace swe_dev;
 
-template <typename T> struct SmemSrc {
-    const Vec4<T> *Fs;      // MUSCL: [3*slots] face values; WAF: [3*slots] upwind means
-    const Vec4<T> *Ps;      // WAF: [slots] centre values (h, u, v, z)
-    int t;
-    __device__ Vec4<T> own_face(int k) const { return Fs[3 * t + k]; }
-    __device__ Vec4<T> nbr_face(const Nb &b) const { return Fs[3 * b.idx + b.kj]; }
-    __device__ Vec4<T> nbr_centre(const Nb &b) const { return Ps[b.idx]; }
-    __device__ Vec4<T> own_up(int k) const { return Fs[3 * t + k]; }
-    __device__ Vec4<T> nbr_up(const Nb &b) const { return Fs[3 * b.idx + b.kj]; }
-    __device__ Vec4<T> nbr_state(const Nb &) const { return Vec4<T>{}; }
+template <typename T> struct FusedSmem {
+    Vec4<T> *Ps;      // [B]     MUSCL: (eta, u, v, h); WAF: (h, u, v, z)
+    Vec4<T> *Fs;      // [3][B]  MUSCL: face values (eta, u, v, z); WAF: upwind means
+    Vec2<T> *LN;      // [3][B]  scaled normals of tile cells
+    T *DL;            // [3][B]  WAF: centroid distance to the neighbour
+    T *C0, *C1, *C2;  // [3][B]  edge contributions of tile cells
+
+    __device__ FusedSmem(unsigned char *base, int B)
+    {
+        Ps = reinterpret_cast<Vec4<T> *>(base);
+        Fs = Ps + B;
+        LN = reinterpret_cast<Vec2<T> *>(Fs + 3 * B);
+        DL = reinterpret_cast<T *>(LN + 3 * B);
+        C0 = DL + 3 * B;
+        C1 = C0 + 3 * B;
+        C2 = C1 + 3 * B;
+    }
 };
 
 // Upwind means of WAF for the three edges of a cell from its neighbours'
@@ -48,58 +60,63 @@ __device__ __forceinline__ void waf_upwind(const T qh[3], const T qu[3], const T
 }
 
 template <typename T, int SCHEME>
+__device__ __forceinline__ Side<T> slot_side(const FusedSmem<T> &sm, int B, int slot, int k)
+{
+    Side<T> s;
+    const Vec4<T> p = sm.Ps[slot];
+    if (SCHEME == SWE_SCHEME_MUSCL) {
+        const Vec4<T> f = sm.Fs[k * B + slot];
+        s.ef = f.x; s.uf = f.y; s.vf = f.z; s.z = f.w; s.hc = p.w;
+    } else {
+        s.hc = p.x; s.uf = p.y; s.vf = p.z; s.z = p.w; s.ef = p.x + p.w;
+    }
+    return s;
+}
+
+template <typename T, int SCHEME>
 __global__ void k_fused(StepArgs<T> a, FusedArgs f)
 {
     extern __shared__ __align__(32) unsigned char smem_raw[];
-    Vec4<T> *Ps = reinterpret_cast<Vec4<T> *>(smem_raw);          // [slots]
-    Vec4<T> *Fs = Ps + f.slots;                                     // [3*slots]
-    const int TC = f.tile;
+    const int B = blockDim.x;
+    FusedSmem<T> sm(smem_raw, B);
+    const int tile = blockIdx.x;
+    const int s0 = f.tile_start[tile], nc = f.tile_start[tile + 1] - s0;
+    const int hp0 = f.halo_ptr[tile], H = f.halo_ptr[tile + 1] - hp0;
+    const int ep0 = f.edge_ptr[tile], E = f.edge_ptr[tile + 1] - ep0;
     const int t = threadIdx.x;
-    const int64_t start = (int64_t)blockIdx.x * TC;
-    const int nt = (int)min((int64_t)TC, a.m.n - start);
-    const int hp0 = f.halo_ptr[blockIdx.x];
-    const int H = f.halo_ptr[blockIdx.x + 1] - hp0;
-    const int64_t i = start + t;
-    const bool valid = t < nt;
     const T h_eps = a.h_eps;
     bool dry;
     const T dt = block_dt(a, &dry);
 
-    // ---- phase 0: primitives into shared memory ----
-    // MUSCL: Ps = (eta, u, v, h); WAF: Ps = (h, u, v, z)
+    // ---- phase 0: primitives of the slot's cell ----
+    const bool is_cell = t < nc, is_halo = !is_cell && t < nc + H;
+    const int64_t cell = is_cell ? (int64_t)s0 + t : (is_halo ? (int64_t)f.halo_ids[hp0 + t - nc] : 0);
     T hi = T(0), hui = T(0), hvi = T(0), zi = T(0);
-    if (valid) {
-        hi = a.h[i]; hui = a.hu[i]; hvi = a.hv[i]; zi = a.m.z[i];
+    if (is_cell || is_halo) {
+        hi = a.h[cell]; hui = a.hu[cell]; hvi = a.hv[cell]; zi = a.m.z[cell];
         T u, v;
         primitives(hi, hui, hvi, h_eps, u, v);
         Vec4<T> p;
         if (SCHEME == SWE_SCHEME_MUSCL) { p.x = hi + zi; p.y = u; p.z = v; p.w = hi; }
         else { p.x = hi; p.y = u; p.z = v; p.w = zi; }
-        Ps[t] = p;
-    }
-    for (int q = t; q < H; q += blockDim.x) {
-        const int g = f.halo_ids[hp0 + q];
-        const T hg = a.h[g], zg = a.m.z[g];
-        T u, v;
-        primitives(hg, a.hu[g], a.hv[g], h_eps, u, v);
-        Vec4<T> p;
-        if (SCHEME == SWE_SCHEME_MUSCL) { p.x = hg + zg; p.y = u; p.z = v; p.w = hg; }
-        else { p.x = hg; p.y = u; p.z = v; p.w = zg; }
-        Ps[TC + q] = p;
+        sm.Ps[t] = p;
     }
     __syncthreads();
 
     // ---- phase 1: face values / upwind means ----
     Nb nb[3];
-    Vec2<T> ln[3], dd[3];
-    if (valid) {
+    Vec2<T> ln[3];
+    if (is_cell) {
+        Vec2<T> dd[3];
 #pragma unroll
         for (int k = 0; k < 3; k++) {
-            nb[k] = decode_local(f.nbr_local[3 * i + k]);
-            ln[k] = a.m.ln[3 * i + k];
-            dd[k] = a.m.dd[3 * i + k];
+            nb[k] = decode_local(f.nbr_local[3 * cell + k]);
+            ln[k] = a.m.ln[3 * cell + k];
+            dd[k] = a.m.dd[3 * cell + k];
+            sm.LN[k * B + t] = ln[k];
+            if (SCHEME == SWE_SCHEME_WAF) sm.DL[k * B + t] = dsqrt(dd[k].x * dd[k].x + dd[k].y * dd[k].y);
         }
-        const Vec4<T> pi = Ps[t];
+        const Vec4<T> pi = sm.Ps[t];
         if (SCHEME == SWE_SCHEME_MUSCL) {
             T qi[3] = {pi.x, pi.y, pi.z};
             T qn[3][3];
@@ -110,7 +127,7 @@ __global__ void k_fused(StepArgs<T> a, FusedArgs f)
             for (int k = 0; k < 3; k++) {
                 has[k] = nb[k].interior;
                 if (has[k]) {
-                    const Vec4<T> pj = Ps[nb[k].idx];
+                    const Vec4<T> pj = sm.Ps[nb[k].idx];
                     ok = ok && pj.w > h_eps;
                     qn[k][0] = pj.x; qn[k][1] = pj.y; qn[k][2] = pj.z;
                     cnt++;
@@ -121,23 +138,21 @@ __global__ void k_fused(StepArgs<T> a, FusedArgs f)
             Vec4<T> fv[3];
             muscl_faces(qi, zi, ok, cnt, qn, has, ln, dd, fv);
 #pragma unroll
-            for (int k = 0; k < 3; k++) Fs[3 * t + k] = fv[k];
+            for (int k = 0; k < 3; k++) sm.Fs[k * B + t] = fv[k];
         } else {
             T qh[3], qu[3], qv[3];
 #pragma unroll
             for (int k = 0; k < 3; k++) {
-                const Vec4<T> pj = nb[k].interior ? Ps[nb[k].idx] : pi;
+                const Vec4<T> pj = nb[k].interior ? sm.Ps[nb[k].idx] : pi;
                 qh[k] = pj.x; qu[k] = pj.y; qv[k] = pj.z;
             }
             Vec4<T> U[3];
             waf_upwind(qh, qu, qv, U);
 #pragma unroll
-            for (int k = 0; k < 3; k++) Fs[3 * t + k] = U[k];
+            for (int k = 0; k < 3; k++) sm.Fs[k * B + t] = U[k];
         }
-    }
-    for (int q = t; q < H; q += blockDim.x) {
-        const int64_t g = f.halo_ids[hp0 + q];
-        const Vec4<T> pg = Ps[TC + q];
+    } else if (is_halo) {
+        const Vec4<T> pg = sm.Ps[t];
         Vec4<T> out[3];
         if (SCHEME == SWE_SCHEME_MUSCL) {
             T qi[3] = {pg.x, pg.y, pg.z};
@@ -148,9 +163,9 @@ __global__ void k_fused(StepArgs<T> a, FusedArgs f)
             Vec2<T> lg[3], dg[3];
 #pragma unroll
             for (int k = 0; k < 3; k++) {
-                const int w = a.m.nbr[3 * g + k];
-                lg[k] = a.m.ln[3 * g + k];
-                dg[k] = a.m.dd[3 * g + k];
+                const int w = a.m.nbr[3 * cell + k];
+                lg[k] = a.m.ln[3 * cell + k];
+                dg[k] = a.m.dd[3 * cell + k];
                 has[k] = w >= 0;
                 if (has[k]) {
                     const int j = w >> 3;
@@ -163,12 +178,12 @@ __global__ void k_fused(StepArgs<T> a, FusedArgs f)
                     qn[k][0] = qi[0]; qn[k][1] = qi[1]; qn[k][2] = qi[2];
                 }
             }
-            muscl_faces(qi, a.m.z[g], ok, cnt, qn, has, lg, dg, out);
+            muscl_faces(qi, zi, ok, cnt, qn, has, lg, dg, out);
         } else {
             T qh[3], qu[3], qv[3];
 #pragma unroll
             for (int k = 0; k < 3; k++) {
-                const int w = a.m.nbr[3 * g + k];
+                const int w = a.m.nbr[3 * cell + k];
                 if (w >= 0) {
                     const int j = w >> 3;
                     qh[k] = a.h[j];
@@ -180,18 +195,52 @@ __global__ void k_fused(StepArgs<T> a, FusedArgs f)
             waf_upwind(qh, qu, qv, out);
         }
 #pragma unroll
-        for (int k = 0; k < 3; k++) Fs[3 * (TC + q) + k] = out[k];
+        for (int k = 0; k < 3; k++) sm.Fs[k * B + t] = out[k];
     }
     __syncthreads();
 
-    // ---- phase 2: fluxes and update ----
+    // ---- phase 2: one thread per edge of the tile ----
+    for (int e = t; e < E; e += B) {
+        const uint32_t w = f.edges[ep0 + e];
+        const int si = (int)(w & 511u), ki = (int)((w >> 9) & 3u);
+        const int sj = (int)((w >> 11) & 511u), kj = (int)((w >> 20) & 3u);
+        const bool own_i = (w >> 22) & 1u, jin = (w >> 23) & 1u;
+        const Side<T> Si = slot_side<T, SCHEME>(sm, B, si, ki);
+        const Side<T> Sj = slot_side<T, SCHEME>(sm, B, sj, kj);
+        const Vec2<T> l = sm.LN[ki * B + si];
+        Vec4<T> Ui{}, Uj{};
+        T dlen = T(0);
+        if (SCHEME == SWE_SCHEME_WAF) {
+            Ui = sm.Fs[ki * B + si];
+            Uj = sm.Fs[kj * B + sj];
+            dlen = sm.DL[ki * B + si];
+        }
+        Contrib<T> ci, cj;
+        interior_edge<T, SCHEME>(a, dt, Si, Sj, own_i, l.x, l.y, dlen, Ui, Uj, ci, jin ? &cj : nullptr);
+        sm.C0[ki * B + si] = ci.c0; sm.C1[ki * B + si] = ci.c1; sm.C2[ki * B + si] = ci.c2;
+        if (jin) { sm.C0[kj * B + sj] = cj.c0; sm.C1[kj * B + sj] = cj.c1; sm.C2[kj * B + sj] = cj.c2; }
+    }
+    __syncthreads();
+
+    // ---- phase 3: sums in edge order, update ----
     CellOut<T> o;
     o.smax = T(0); o.clip = T(0); o.bsum = T(0);
-    if (valid) {
-        const T nm = a.m.nman ? a.m.nman[i] : T(0);
-        SmemSrc<T> src{Fs, Ps, t};
-        o = cell_update<T, SCHEME>(a, dt, hi, hui, hvi, zi, nm, nb, ln, dd, src);
-        a.ho[i] = o.h; a.huo[i] = o.hu; a.hvo[i] = o.hv;
+    if (is_cell) {
+        T R0 = T(0), R1 = T(0), R2 = T(0), bs = T(0);
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            Contrib<T> c;
+            if (nb[k].interior) {
+                c.c0 = sm.C0[k * B + t]; c.c1 = sm.C1[k * B + t]; c.c2 = sm.C2[k * B + t];
+            } else {
+                const Side<T> s = slot_side<T, SCHEME>(sm, B, t, k);
+                c = boundary_edge<T>(a, s, nb[k].tag, ln[k].x, ln[k].y, bs);
+            }
+            accumulate(k, c, R0, R1, R2);
+        }
+        const T nm = a.m.nman ? a.m.nman[cell] : T(0);
+        o = cell_finish<T>(a, dt, hi, hui, hvi, R0, R1, R2, ln, nm, bs);
+        a.ho[cell] = o.h; a.huo[cell] = o.hu; a.hvo[cell] = o.hv;
         if (!(dfinite(o.h) && dfinite(o.hu) && dfinite(o.hv))) atomicOr(&a.sc->status, ST_NONFINITE);
     }
     step_epilogue<T>(a, dt, dry, o.smax, o.clip, o.bsum);
@@ -207,23 +256,22 @@ template <typename T> int fused_max_threads(int scheme)
     return e == cudaSuccess ? fa.maxThreadsPerBlock : 0;
 }
 
-template <typename T> size_t fused_smem_bytes(int scheme, int slots)
+template <typename T> size_t fused_smem_bytes(int scheme, int block)
 {
     (void)scheme;
-    return (size_t)slots * 4 * sizeof(Vec4<T>);
+    return (size_t)block * (4 * sizeof(Vec4<T>) + 3 * sizeof(Vec2<T>) + 12 * sizeof(T));
 }
 
 template <typename T>
 cudaError_t launch_fused(int scheme, const StepArgs<T> &a, const FusedArgs &f, cudaStream_t s)
 {
-    const size_t smem = fused_smem_bytes<T>(scheme, f.slots);
-    const unsigned grid = (unsigned)((a.m.n + f.tile - 1) / f.tile);
+    const size_t smem = fused_smem_bytes<T>(scheme, f.block);
     if (scheme == SWE_SCHEME_MUSCL) {
         cudaFuncSetAttribute(k_fused<T, SWE_SCHEME_MUSCL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_fused<T, SWE_SCHEME_MUSCL><<<grid, f.tile, smem, s>>>(a, f);
+        k_fused<T, SWE_SCHEME_MUSCL><<<f.n_tiles, f.block, smem, s>>>(a, f);
     } else if (scheme == SWE_SCHEME_WAF) {
         cudaFuncSetAttribute(k_fused<T, SWE_SCHEME_WAF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_fused<T, SWE_SCHEME_WAF><<<grid, f.tile, smem, s>>>(a, f);
+        k_fused<T, SWE_SCHEME_WAF><<<f.n_tiles, f.block, smem, s>>>(a, f);
     } else {
         return cudaErrorInvalidValue;
     }
@@ -233,6 +281,6 @@ cudaError_t launch_fused(int scheme, const StepArgs<T> &a, const FusedArgs &f, c
 template cudaError_t launch_fused<float>(int, const StepArgs<float> &, const FusedArgs &, cudaStream_t);
 template cudaError_t launch_fused<double>(int, const StepArgs<double> &, const FusedArgs &, cudaStream_t);
 template size_t fused_smem_bytes<float>(int, int);
+template size_t fused_smem_bytes<double>(int, int);
 template int fused_max_threads<float>(int);
 template int fused_max_threads<double>(int);
-template size_t fused_smem_bytes<double>(int, int);

@@ -89,6 +89,12 @@ template <typename T> struct StateT {
     // fused tile kernel
     bool fused = false;
     FusedArgs fa{};
+    // CUDA graphs of kGraphSteps CFL steps, keyed by (steps launched mod 6, cfl):
+    // the launch pattern (ping-pong buffer, CFL slot ring) repeats every 6 steps
+    static constexpr int kGraphSteps = 24;
+    std::map<std::pair<int, double>, cudaGraphExec_t> graphs;
+    cudaStream_t cap_stream = nullptr;
+    bool use_graphs = true;
     int64_t k = 0;            // steps launched (selects the smax slots)
     bool smax_valid = false;
     T qlen[SWE_MAX_GROUPS] = {}, level[SWE_MAX_GROUPS] = {};
@@ -102,6 +108,8 @@ template <typename T> struct StateT {
     }
     ~StateT()
     {
+        for (auto &g : graphs) cudaGraphExecDestroy(g.second);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
         for (auto &e : ev_used) { cudaEventDestroy(std::get<1>(e)); cudaEventDestroy(std::get<2>(e)); }
         for (auto e : ev_pool) cudaEventDestroy(e);
         for (auto &b : mem.blocks) dev_free(b.first, stream);
@@ -198,6 +206,43 @@ template <typename T> struct StateT {
         return SWE_OK;
     }
 
+    // kGraphSteps CFL steps through a cached CUDA graph (captured on a private
+    // stream on first use, launched on the state's stream).
+    int graph_steps(double cfl)
+    {
+        const std::pair<int, double> key((int)(k % 6), cfl);
+        auto it = graphs.find(key);
+        if (it == graphs.end()) {
+            if (!cap_stream) CK(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
+            const cudaStream_t user = stream;
+            const int64_t k0 = k;
+            const int cur0 = cur;
+            stream = cap_stream;
+            cudaError_t e = cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal);
+            int rc = SWE_OK;
+            for (int q = 0; q < kGraphSteps && rc == SWE_OK && e == cudaSuccess; q++) rc = one_step(cfl, nullptr);
+            cudaGraph_t g = nullptr;
+            cudaError_t e2 = cudaStreamEndCapture(cap_stream, &g);
+            stream = user;
+            k = k0;
+            cur = cur0;
+            if (e != cudaSuccess || e2 != cudaSuccess || rc != SWE_OK) {
+                if (g) cudaGraphDestroy(g);
+                swe_set_error("CUDA graph capture failed");
+                return rc != SWE_OK ? rc : SWE_ERR_CUDA;
+            }
+            cudaGraphExec_t ex = nullptr;
+            e = cudaGraphInstantiate(&ex, g, 0);
+            cudaGraphDestroy(g);
+            CK(e);
+            it = graphs.emplace(key, ex).first;
+        }
+        CK(cudaGraphLaunch(it->second, stream));
+        k += kGraphSteps;
+        cur = (cur + kGraphSteps) & 1;
+        return SWE_OK;
+    }
+
     int read_scalars(DevScalars &out)
     {
         CK(cudaMemcpyAsync(&out, sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, stream));
@@ -286,6 +331,7 @@ int state_init(StateT<T> &s, const swe_mesh *m, const double *h, const double *h
         }
         s.fa.block = block;
         s.fa.n_tiles = tl.n_tiles;
+        CK(fused_prepare<T>(s.p.scheme, block));
         s.fa.tile_start = s.template alloc<int32_t>(tl.tile_start.size());
         s.fa.halo_ptr = s.template alloc<int32_t>(tl.halo_ptr.size());
         s.fa.halo_ids = s.template alloc<int32_t>(std::max<size_t>(tl.halo_ids.size(), 1));
@@ -493,8 +539,16 @@ int swe_step(swe_state *s, int n_steps, double cfl)
     }
     return DISPATCH(s, ([&]() -> int {
         if (!S.smax_valid) { int rc = S.init_smax(); if (rc) return rc; }
-        for (int q = 0; q < n_steps; q++) {
-            int rc = S.one_step(cfl, nullptr);
+        int left = n_steps;
+        while (left > 0) {
+            int rc;
+            if (S.use_graphs && !S.prof && left >= S.kGraphSteps) {
+                rc = S.graph_steps(cfl);
+                left -= S.kGraphSteps;
+            } else {
+                rc = S.one_step(cfl, nullptr);
+                left -= 1;
+            }
             if (rc) return rc;
         }
         return SWE_OK;

@@ -105,6 +105,7 @@ template <typename T>
 cudaError_t launch_fused(int scheme, const StepArgs<T> &a, const FusedArgs &f, cudaStream_t s);
 template <typename T> size_t fused_smem_bytes(int scheme, int block);
 template <typename T> int fused_max_threads(int scheme);     // launch limit of the fused kernel (registers)
+template <typename T> cudaError_t fused_prepare(int scheme, int block);   // shared-memory attribute, once
 template <typename T> int split_max_threads(int scheme);     // launch limit of the split kernels
 
 int mass_partials_needed(int64_t n);

@@ -28,17 +28,13 @@ using namespace swe_dev;
 template <typename T> struct FusedSmem {
     Vec4<T> *Ps;      // [B]     MUSCL: (eta, u, v, h); WAF: (h, u, v, z)
     Vec4<T> *Fs;      // [3][B]  MUSCL: face values (eta, u, v, z); WAF: upwind means
-    Vec2<T> *LN;      // [3][B]  scaled normals of tile cells
-    T *DL;            // [3][B]  WAF: centroid distance to the neighbour
     T *C0, *C1, *C2;  // [3][B]  edge contributions of tile cells
 
     __device__ FusedSmem(unsigned char *base, int B)
     {
         Ps = reinterpret_cast<Vec4<T> *>(base);
         Fs = Ps + B;
-        LN = reinterpret_cast<Vec2<T> *>(Fs + 3 * B);
-        DL = reinterpret_cast<T *>(LN + 3 * B);
-        C0 = DL + 3 * B;
+        C0 = reinterpret_cast<T *>(Fs + 3 * B);
         C1 = C0 + 3 * B;
         C2 = C1 + 3 * B;
     }
@@ -74,7 +70,7 @@ __device__ __forceinline__ Side<T> slot_side(const FusedSmem<T> &sm, int B, int 
 }
 
 template <typename T, int SCHEME>
-__global__ void k_fused(StepArgs<T> a, FusedArgs f)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_fused(StepArgs<T> a, FusedArgs f)
 {
     extern __shared__ __align__(32) unsigned char smem_raw[];
     const int B = blockDim.x;
@@ -90,7 +86,7 @@ __global__ void k_fused(StepArgs<T> a, FusedArgs f)
 
     // ---- phase 0: primitives of the slot's cell ----
     const bool is_cell = t < nc, is_halo = !is_cell && t < nc + H;
-    const int64_t cell = is_cell ? (int64_t)s0 + t : (is_halo ? (int64_t)f.halo_ids[hp0 + t - nc] : 0);
+    const int cell = is_cell ? s0 + t : (is_halo ? f.halo_ids[hp0 + t - nc] : 0);
     T hi = T(0), hui = T(0), hvi = T(0), zi = T(0);
     if (is_cell || is_halo) {
         hi = a.h[cell]; hui = a.hu[cell]; hvi = a.hv[cell]; zi = a.m.z[cell];
@@ -113,8 +109,6 @@ __global__ void k_fused(StepArgs<T> a, FusedArgs f)
             nb[k] = decode_local(f.nbr_local[3 * cell + k]);
             ln[k] = a.m.ln[3 * cell + k];
             dd[k] = a.m.dd[3 * cell + k];
-            sm.LN[k * B + t] = ln[k];
-            if (SCHEME == SWE_SCHEME_WAF) sm.DL[k * B + t] = dsqrt(dd[k].x * dd[k].x + dd[k].y * dd[k].y);
         }
         const Vec4<T> pi = sm.Ps[t];
         if (SCHEME == SWE_SCHEME_MUSCL) {
@@ -207,13 +201,15 @@ __global__ void k_fused(StepArgs<T> a, FusedArgs f)
         const bool own_i = (w >> 22) & 1u, jin = (w >> 23) & 1u;
         const Side<T> Si = slot_side<T, SCHEME>(sm, B, si, ki);
         const Side<T> Sj = slot_side<T, SCHEME>(sm, B, sj, kj);
-        const Vec2<T> l = sm.LN[ki * B + si];
+        const int ei = 3 * (s0 + si) + ki;
+        const Vec2<T> l = a.m.ln[ei];           // just read by the tile's thread: an L1 hit
         Vec4<T> Ui{}, Uj{};
         T dlen = T(0);
         if (SCHEME == SWE_SCHEME_WAF) {
             Ui = sm.Fs[ki * B + si];
             Uj = sm.Fs[kj * B + sj];
-            dlen = sm.DL[ki * B + si];
+            const Vec2<T> d = a.m.dd[ei];
+            dlen = dsqrt(d.x * d.x + d.y * d.y);
         }
         Contrib<T> ci, cj;
         interior_edge<T, SCHEME>(a, dt, Si, Sj, own_i, l.x, l.y, dlen, Ui, Uj, ci, jin ? &cj : nullptr);
@@ -256,10 +252,22 @@ template <typename T> int fused_max_threads(int scheme)
     return e == cudaSuccess ? fa.maxThreadsPerBlock : 0;
 }
 
+// Allow the kernel the dynamic shared memory of a block of `block` threads
+// (called once when a state is set up, outside any stream capture).
+template <typename T> cudaError_t fused_prepare(int scheme, int block)
+{
+    const int smem = (int)fused_smem_bytes<T>(scheme, block);
+    auto kern = scheme == SWE_SCHEME_WAF ? k_fused<T, SWE_SCHEME_WAF> : k_fused<T, SWE_SCHEME_MUSCL>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    return e;
+}
+
 template <typename T> size_t fused_smem_bytes(int scheme, int block)
 {
     (void)scheme;
-    return (size_t)block * (4 * sizeof(Vec4<T>) + 3 * sizeof(Vec2<T>) + 12 * sizeof(T));
+    return (size_t)block * (4 * sizeof(Vec4<T>) + 9 * sizeof(T));
 }
 
 template <typename T>
@@ -267,10 +275,8 @@ cudaError_t launch_fused(int scheme, const StepArgs<T> &a, const FusedArgs &f, c
 {
     const size_t smem = fused_smem_bytes<T>(scheme, f.block);
     if (scheme == SWE_SCHEME_MUSCL) {
-        cudaFuncSetAttribute(k_fused<T, SWE_SCHEME_MUSCL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_fused<T, SWE_SCHEME_MUSCL><<<f.n_tiles, f.block, smem, s>>>(a, f);
     } else if (scheme == SWE_SCHEME_WAF) {
-        cudaFuncSetAttribute(k_fused<T, SWE_SCHEME_WAF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_fused<T, SWE_SCHEME_WAF><<<f.n_tiles, f.block, smem, s>>>(a, f);
     } else {
         return cudaErrorInvalidValue;
@@ -283,4 +289,6 @@ template cudaError_t launch_fused<double>(int, const StepArgs<double> &, const F
 template size_t fused_smem_bytes<float>(int, int);
 template size_t fused_smem_bytes<double>(int, int);
 template int fused_max_threads<float>(int);
+template cudaError_t fused_prepare<float>(int, int);
+template cudaError_t fused_prepare<double>(int, int);
 template int fused_max_threads<double>(int);

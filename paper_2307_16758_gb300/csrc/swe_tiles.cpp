@@ -69,6 +69,7 @@ int swe_build_tiling(const swe_mesh &m, int block, Tiling &out)
             return nc + (int)(std::lower_bound(halo.begin(), halo.end(), j) - halo.begin());
         };
         int ne = 0;
+        const size_t e0 = out.edges.size();
         for (int64_t c = s; c < s + nc; c++)
             for (int k = 0; k < 3; k++) {
                 const int64_t e = 3 * c + k;
@@ -84,6 +85,12 @@ int swe_build_tiling(const swe_mesh &m, int block, Tiling &out)
                 out.edges.push_back(w);
                 ne++;
             }
+        // order by (k_i, slot_i): neighbouring threads then touch neighbouring
+        // shared-memory words (no bank conflicts on side i)
+        std::sort(out.edges.begin() + e0, out.edges.end(), [](uint32_t x, uint32_t y) {
+            const uint32_t kx = (x >> 9) & 3u, ky = (y >> 9) & 3u;
+            return kx != ky ? kx < ky : (x & 511u) < (y & 511u);
+        });
         out.edge_ptr.push_back((int32_t)out.edges.size());
         out.max_edges = std::max(out.max_edges, ne);
         tile++;

@@ -135,6 +135,140 @@ template <typename T> struct StateT {
         return e;
     }
 
+    void release(void *ptr)
+    {
+        if (!ptr) return;
+        for (auto it = mem.blocks.begin(); it != mem.blocks.end(); ++it)
+            if (it->first == ptr) {
+                dev_free(it->first, stream);
+                mem.bytes -= (int64_t)((it->second + 255) & ~size_t(255));
+                mem.blocks.erase(it);
+                return;
+            }
+    }
+
+    void clear_graphs()
+    {
+        for (auto &g : graphs) cudaGraphExecDestroy(g.second);
+        graphs.clear();
+    }
+
+    // Select the split kernels or the fused tile kernel with `block` threads
+    // (building the tiling from the mesh); allocates what that kernel needs.
+    int configure(bool want_fused, int block, const swe_mesh *m)
+    {
+        const int lim = want_fused ? fused_max_threads<T>(p.scheme) : split_max_threads<T>(p.scheme);
+        if (lim <= 0) { swe_set_error("cannot query the kernels (no usable GPU?)"); return SWE_ERR_CUDA; }
+        if (block <= 0 || block % 32 || block > lim) {
+            swe_set_error("block of " + std::to_string(block) + " threads is not a multiple of 32 within the kernel's limit of " +
+                          std::to_string(lim));
+            return SWE_ERR_ARG;
+        }
+        CK(cudaStreamSynchronize(stream));
+        clear_graphs();
+        if (want_fused) {
+            if (!m || m->n != n) { swe_set_error("the fused kernel needs the state's mesh"); return SWE_ERR_ARG; }
+            Tiling tl;
+            if (swe_build_tiling(*m, block, tl) != 0) { swe_set_error("unsupported tile block"); return SWE_ERR_ARG; }
+            if (fused_smem_bytes<T>(p.scheme, block) > 227 * 1024) {
+                swe_set_error("tile needs more shared memory than a block has");
+                return SWE_ERR_ARG;
+            }
+            CK(fused_prepare<T>(p.scheme, block));
+            release((void *)fa.tile_start); release((void *)fa.halo_ptr); release((void *)fa.halo_ids);
+            release((void *)fa.edge_ptr); release((void *)fa.edges); release((void *)fa.nbr_local);
+            fa = FusedArgs{};
+            fa.block = block;
+            fa.n_tiles = tl.n_tiles;
+            fa.tile_start = alloc<int32_t>(tl.tile_start.size());
+            fa.halo_ptr = alloc<int32_t>(tl.halo_ptr.size());
+            fa.halo_ids = alloc<int32_t>(std::max<size_t>(tl.halo_ids.size(), 1));
+            fa.edge_ptr = alloc<int32_t>(tl.edge_ptr.size());
+            fa.edges = alloc<uint32_t>(std::max<size_t>(tl.edges.size(), 1));
+            fa.nbr_local = alloc<uint16_t>(3 * n);
+            if (!fa.tile_start || !fa.halo_ptr || !fa.halo_ids || !fa.edge_ptr || !fa.edges || !fa.nbr_local) {
+                swe_set_error("device allocation failed");
+                return SWE_ERR_NOMEM;
+            }
+            auto up = [&](const void *dst, const void *src, size_t bytes) {
+                return bytes ? cudaMemcpy((void *)dst, src, bytes, cudaMemcpyHostToDevice) : cudaSuccess;
+            };
+            CK(up(fa.tile_start, tl.tile_start.data(), sizeof(int32_t) * tl.tile_start.size()));
+            CK(up(fa.halo_ptr, tl.halo_ptr.data(), sizeof(int32_t) * tl.halo_ptr.size()));
+            CK(up(fa.halo_ids, tl.halo_ids.data(), sizeof(int32_t) * tl.halo_ids.size()));
+            CK(up(fa.edge_ptr, tl.edge_ptr.data(), sizeof(int32_t) * tl.edge_ptr.size()));
+            CK(up(fa.edges, tl.edges.data(), sizeof(uint32_t) * tl.edges.size()));
+            CK(up(fa.nbr_local, tl.nbr_local.data(), sizeof(uint16_t) * 3 * n));
+            p.kernel = SWE_KERNEL_FUSED;
+        } else {
+            if (p.scheme == SWE_SCHEME_MUSCL && !F) F = alloc<Vec4<T>>(3 * n);
+            if (p.scheme == SWE_SCHEME_WAF && !F) { F = alloc<Vec4<T>>(n); U = alloc<Vec4<T>>(3 * n); }
+            if (p.scheme != SWE_SCHEME_HLLC && (!F || (p.scheme == SWE_SCHEME_WAF && !U))) {
+                swe_set_error("device allocation failed");
+                return SWE_ERR_NOMEM;
+            }
+            p.kernel = SWE_KERNEL_SPLIT;
+        }
+        fused = want_fused;
+        p.block = block;
+        return SWE_OK;
+    }
+
+    // Copy of the evolving data (state, scalars, dt history) for trial runs.
+    struct Snapshot {
+        T *h = nullptr, *hu = nullptr, *hv = nullptr;
+        DevScalars *sc = nullptr;
+        double *hist = nullptr;
+        int64_t k = 0;
+        int cur = 0;
+        bool smax_valid = false;
+    };
+
+    int snapshot(Snapshot &sn)
+    {
+        if (!sn.h) {
+            sn.h = alloc<T>(n); sn.hu = alloc<T>(n); sn.hv = alloc<T>(n);
+            sn.sc = alloc<DevScalars>(1); sn.hist = alloc<double>(SWE_DT_HISTORY);
+            if (!sn.h || !sn.hu || !sn.hv || !sn.sc || !sn.hist) { swe_set_error("device allocation failed"); return SWE_ERR_NOMEM; }
+        }
+        CK(cudaMemcpyAsync(sn.h, h[cur], sizeof(T) * n, cudaMemcpyDeviceToDevice, stream));
+        CK(cudaMemcpyAsync(sn.hu, hu[cur], sizeof(T) * n, cudaMemcpyDeviceToDevice, stream));
+        CK(cudaMemcpyAsync(sn.hv, hv[cur], sizeof(T) * n, cudaMemcpyDeviceToDevice, stream));
+        CK(cudaMemcpyAsync(sn.sc, sc, sizeof(DevScalars), cudaMemcpyDeviceToDevice, stream));
+        CK(cudaMemcpyAsync(sn.hist, dt_hist, sizeof(double) * SWE_DT_HISTORY, cudaMemcpyDeviceToDevice, stream));
+        sn.k = k; sn.cur = cur; sn.smax_valid = smax_valid;
+        return SWE_OK;
+    }
+
+    int restore(const Snapshot &sn)
+    {
+        k = sn.k; cur = sn.cur; smax_valid = sn.smax_valid;
+        CK(cudaMemcpyAsync(h[cur], sn.h, sizeof(T) * n, cudaMemcpyDeviceToDevice, stream));
+        CK(cudaMemcpyAsync(hu[cur], sn.hu, sizeof(T) * n, cudaMemcpyDeviceToDevice, stream));
+        CK(cudaMemcpyAsync(hv[cur], sn.hv, sizeof(T) * n, cudaMemcpyDeviceToDevice, stream));
+        CK(cudaMemcpyAsync(sc, sn.sc, sizeof(DevScalars), cudaMemcpyDeviceToDevice, stream));
+        CK(cudaMemcpyAsync(dt_hist, sn.hist, sizeof(double) * SWE_DT_HISTORY, cudaMemcpyDeviceToDevice, stream));
+        return SWE_OK;
+    }
+
+    void drop(Snapshot &sn)
+    {
+        cudaStreamSynchronize(stream);
+        release(sn.h); release(sn.hu); release(sn.hv); release(sn.sc); release(sn.hist);
+        sn = Snapshot{};
+    }
+
+    // Step arguments for phase p = (steps taken) mod 6 of the launch pattern.
+    StepArgs<T> args_for_phase(int ph, double cfl)
+    {
+        const int64_t k0 = k;
+        k = ph;
+        StepArgs<T> a = args(ph & 1, (ph & 1) ^ 1);
+        k = k0;
+        a.cfl_rmin = cfl * r_min;
+        return a;
+    }
+
     DevMesh<T> dmesh() const
     {
         DevMesh<T> m;
@@ -308,40 +442,6 @@ int state_init(StateT<T> &s, const swe_mesh *m, const double *h, const double *h
     for (int b = 0; b < nbuf; b++) {
         s.h[b] = s.template alloc<T>(n); s.hu[b] = s.template alloc<T>(n); s.hv[b] = s.template alloc<T>(n);
     }
-    // automatic choice: the split kernels (measured faster on GB300 for both
-    // precisions); the fused tile kernel on request
-    s.fused = s.p.scheme != SWE_SCHEME_HLLC && s.p.kernel == SWE_KERNEL_FUSED;
-    {
-        const int want = s.p.block > 0 ? s.p.block : 256;
-        const int lim = s.fused ? fused_max_threads<T>(s.p.scheme) : split_max_threads<T>(s.p.scheme);
-        if (lim <= 0) { swe_set_error("swe_state_init: cannot query the kernels (no usable GPU?)"); return SWE_ERR_CUDA; }
-        if (want > lim) {
-            swe_set_error("swe_state_init: block of " + std::to_string(want) + " threads exceeds the kernel's limit of " +
-                          std::to_string(lim));
-            return SWE_ERR_ARG;
-        }
-    }
-    Tiling tl;
-    if (s.fused) {
-        const int block = s.p.block > 0 ? s.p.block : 256;
-        if (swe_build_tiling(*m, block, tl) != 0) { swe_set_error("swe_state_init: unsupported tile block"); return SWE_ERR_ARG; }
-        if (fused_smem_bytes<T>(s.p.scheme, block) > 227 * 1024) {
-            swe_set_error("swe_state_init: tile needs more shared memory than a block has");
-            return SWE_ERR_ARG;
-        }
-        s.fa.block = block;
-        s.fa.n_tiles = tl.n_tiles;
-        CK(fused_prepare<T>(s.p.scheme, block));
-        s.fa.tile_start = s.template alloc<int32_t>(tl.tile_start.size());
-        s.fa.halo_ptr = s.template alloc<int32_t>(tl.halo_ptr.size());
-        s.fa.halo_ids = s.template alloc<int32_t>(std::max<size_t>(tl.halo_ids.size(), 1));
-        s.fa.edge_ptr = s.template alloc<int32_t>(tl.edge_ptr.size());
-        s.fa.edges = s.template alloc<uint32_t>(std::max<size_t>(tl.edges.size(), 1));
-        s.fa.nbr_local = s.template alloc<uint16_t>(3 * n);
-    } else {
-        if (s.p.scheme == SWE_SCHEME_MUSCL) s.F = s.template alloc<Vec4<T>>(3 * n);
-        if (s.p.scheme == SWE_SCHEME_WAF) { s.F = s.template alloc<Vec4<T>>(n); s.U = s.template alloc<Vec4<T>>(3 * n); }
-    }
     s.sc = s.template alloc<DevScalars>(1);
     s.n_part = mass_partials_needed(n);
     s.mass_part = s.template alloc<double>(s.n_part);
@@ -360,16 +460,11 @@ int state_init(StateT<T> &s, const swe_mesh *m, const double *h, const double *h
     if (s.nman) CK(cudaMemcpyAsync(s.nman, nt.data(), sizeof(T) * n, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(s.area, m->area.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(s.sc, 0, sizeof(DevScalars), st));
-    if (s.fused) {
-        auto up = [&](const void *dst, const void *src, size_t bytes) {
-            return bytes ? cudaMemcpyAsync((void *)dst, src, bytes, cudaMemcpyHostToDevice, st) : cudaSuccess;
-        };
-        CK(up(s.fa.tile_start, tl.tile_start.data(), sizeof(int32_t) * tl.tile_start.size()));
-        CK(up(s.fa.halo_ptr, tl.halo_ptr.data(), sizeof(int32_t) * tl.halo_ptr.size()));
-        CK(up(s.fa.halo_ids, tl.halo_ids.data(), sizeof(int32_t) * tl.halo_ids.size()));
-        CK(up(s.fa.edge_ptr, tl.edge_ptr.data(), sizeof(int32_t) * tl.edge_ptr.size()));
-        CK(up(s.fa.edges, tl.edges.data(), sizeof(uint32_t) * tl.edges.size()));
-        CK(up(s.fa.nbr_local, tl.nbr_local.data(), sizeof(uint16_t) * 3 * n));
+    {
+        // kernel choice: the split kernels unless the fused tile kernel is requested
+        const bool want_fused = s.p.scheme != SWE_SCHEME_HLLC && s.p.kernel == SWE_KERNEL_FUSED;
+        int rc = s.configure(want_fused, s.p.block > 0 ? s.p.block : 256, m);
+        if (rc) return rc;
     }
     // initial state through the same path as swe_set_state
     CK(cudaMemcpyAsync(s.staging, h, sizeof(double) * n, cudaMemcpyHostToDevice, st));

@@ -540,11 +540,12 @@ __device__ __forceinline__ CellOut<T> cell_update(const StepArgs<T> &a, T dt, T 
 // Step epilogue: publish the block's wave speed and diagnostics; block 0
 // advances time and the step count and clears the stale CFL slot.
 template <typename T>
-__device__ __forceinline__ void step_epilogue(const StepArgs<T> &a, T dt, bool dry, T smax, T clip, T bsum)
+__device__ __forceinline__ void step_epilogue(const StepArgs<T> &a, T dt, bool dry, T smax, T clip, T bsum,
+                                              bool first_block)
 {
     const bool euler = a.mode == MODE_EULER;
     block_publish<T>(smax, clip, bsum, a.sc, a.slot_next, euler, euler ? 1.0 : 0.5);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (first_block && threadIdx.x == 0) {
         if (dry) atomicOr(&a.sc->status, ST_DRY);
         if (euler) {
             a.dt_hist[a.sc->steps % SWE_DT_HISTORY] = (double)dt;

@@ -1,0 +1,121 @@
+// Batched ensemble kernels: one launch advances every member of an ensemble
+// of independent meshes by one explicit step.  The grid is the concatenation
+// of the members' grids; a block finds its member by binary search over the
+// members' first-block offsets and runs the same per-mesh device code as the
+// single-mesh kernels, with that member's arguments (its own buffers, CFL
+// slots and time step).
+#include <cuda_runtime.h>
+
+#include "swe_dev.h"
+#include "swe_device.cuh"
+#include "swe_fused.cuh"
+#include "swe_split.cuh"
+
+namespace {
+using namespace swe_dev;
+
+// Member of block b: the largest m with begin[m] <= b (thread 0 searches, the
+// block shares the answer).
+__device__ __forceinline__ int block_member(const int *begin, int n_mem)
+{
+    __shared__ int sh_m;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = n_mem - 1;
+        const int b = (int)blockIdx.x;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (begin[mid] <= b) lo = mid;
+            else hi = mid - 1;
+        }
+        sh_m = lo;
+    }
+    __syncthreads();
+    return sh_m;
+}
+
+template <typename T, int SCHEME>
+__global__ void k_prep_ens(const EnsEntry<T> *tab, const int *begin, int n_mem, int phase)
+{
+    const int m = block_member(begin, n_mem);
+    const EnsEntry<T> &e = tab[m];
+    const StepArgs<T> &a = e.a[phase];
+    const int i = ((int)blockIdx.x - begin[m]) * blockDim.x + threadIdx.x;
+    if (i >= a.m.n) return;
+    if (SCHEME == SWE_SCHEME_MUSCL) prep_muscl_cell(a, i, e.F);
+    else prep_waf_cell(a, i, e.F, e.U);
+}
+
+template <typename T, int SCHEME>
+__global__ void k_flux_ens(const EnsEntry<T> *tab, const int *begin, int n_mem, int phase)
+{
+    const int m = block_member(begin, n_mem);
+    flux_block<T, SCHEME>(tab[m].a[phase], (int)blockIdx.x - begin[m]);
+}
+
+template <typename T, int SCHEME>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
+    k_fused_ens(const EnsEntry<T> *tab, const int *begin, int n_mem, int phase)
+{
+    extern __shared__ __align__(32) unsigned char smem_raw[];
+    const int m = block_member(begin, n_mem);
+    fused_tile<T, SCHEME>(tab[m].a[phase], tab[m].f, (int)blockIdx.x - begin[m], smem_raw);
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_ensemble(int scheme, bool fused, const EnsEntry<T> *tab, const int *begin, int n_mem,
+                            int phase, int grid, int block, cudaStream_t s)
+{
+    if (fused) {
+        const size_t smem = fused_smem_bytes<T>(scheme, block);
+        auto kern = scheme == SWE_SCHEME_WAF ? k_fused_ens<T, SWE_SCHEME_WAF> : k_fused_ens<T, SWE_SCHEME_MUSCL>;
+        kern<<<grid, block, smem, s>>>(tab, begin, n_mem, phase);
+        return cudaGetLastError();
+    }
+    const int nw = block / 32;
+    if (scheme == SWE_SCHEME_MUSCL) {
+        k_prep_ens<T, SWE_SCHEME_MUSCL><<<grid, block, 0, s>>>(tab, begin, n_mem, phase);
+        k_flux_ens<T, SWE_SCHEME_MUSCL>
+            <<<grid, block, nw * flux_smem_per_warp<T, SWE_SCHEME_MUSCL>(), s>>>(tab, begin, n_mem, phase);
+    } else if (scheme == SWE_SCHEME_WAF) {
+        k_prep_ens<T, SWE_SCHEME_WAF><<<grid, block, 0, s>>>(tab, begin, n_mem, phase);
+        k_flux_ens<T, SWE_SCHEME_WAF>
+            <<<grid, block, nw * flux_smem_per_warp<T, SWE_SCHEME_WAF>(), s>>>(tab, begin, n_mem, phase);
+    } else {
+        k_flux_ens<T, SWE_SCHEME_HLLC>
+            <<<grid, block, nw * flux_smem_per_warp<T, SWE_SCHEME_HLLC>(), s>>>(tab, begin, n_mem, phase);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T> cudaError_t ensemble_prepare(int scheme, bool fused, int block)
+{
+    if (!fused) {
+        const int nw = block / 32;
+        cudaError_t e = cudaSuccess;
+        if (scheme == SWE_SCHEME_MUSCL)
+            e = cudaFuncSetAttribute(k_flux_ens<T, SWE_SCHEME_MUSCL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(nw * flux_smem_per_warp<T, SWE_SCHEME_MUSCL>()));
+        else if (scheme == SWE_SCHEME_WAF)
+            e = cudaFuncSetAttribute(k_flux_ens<T, SWE_SCHEME_WAF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(nw * flux_smem_per_warp<T, SWE_SCHEME_WAF>()));
+        else
+            e = cudaFuncSetAttribute(k_flux_ens<T, SWE_SCHEME_HLLC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(nw * flux_smem_per_warp<T, SWE_SCHEME_HLLC>()));
+        return e;
+    }
+    const int smem = (int)fused_smem_bytes<T>(scheme, block);
+    auto kern = scheme == SWE_SCHEME_WAF ? k_fused_ens<T, SWE_SCHEME_WAF> : k_fused_ens<T, SWE_SCHEME_MUSCL>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    return e;
+}
+
+template cudaError_t launch_ensemble<float>(int, bool, const EnsEntry<float> *, const int *, int, int, int, int,
+                                            cudaStream_t);
+template cudaError_t launch_ensemble<double>(int, bool, const EnsEntry<double> *, const int *, int, int, int, int,
+                                             cudaStream_t);
+template cudaError_t ensemble_prepare<float>(int, bool, int);
+template cudaError_t ensemble_prepare<double>(int, bool, int);

@@ -18,8 +18,11 @@
 // right) from the same inputs, so the mass flux is bitwise antisymmetric.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "swe_dev.h"
 #include "swe_device.cuh"
+#include "swe_split.cuh"
 
 namespace {
 using namespace swe_dev;
@@ -34,121 +37,21 @@ using namespace swe_dev;
 template <typename T>
 __global__ void k_prep_muscl(StepArgs<T> a, Vec4<T> *F)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.m.n) return;
-    const T h_eps = a.h_eps;
-    T hi = a.h[i], zi = a.m.z[i];
-    T ui, vi;
-    primitives(hi, a.hu[i], a.hv[i], h_eps, ui, vi);
-    T qi[3] = {hi + zi, ui, vi};
-    Vec2<T> ln[3], dd[3];
-    T qn[3][3];
-    bool has[3];
-    bool ok = hi > h_eps;
-    int cnt = 0;
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-        const int w = a.m.nbr[3 * i + k];
-        ln[k] = a.m.ln[3 * i + k];
-        dd[k] = a.m.dd[3 * i + k];
-        has[k] = w >= 0;
-        if (has[k]) {
-            const int j = w >> 3;
-            T hj = a.h[j], uj, vj;
-            primitives(hj, a.hu[j], a.hv[j], h_eps, uj, vj);
-            ok = ok && hj > h_eps;
-            qn[k][0] = hj + a.m.z[j]; qn[k][1] = uj; qn[k][2] = vj;
-            cnt++;
-        } else {
-            qn[k][0] = qi[0]; qn[k][1] = qi[1]; qn[k][2] = qi[2];
-        }
-    }
-    Vec4<T> f[3];
-    muscl_faces(qi, zi, ok, cnt, qn, has, ln, dd, f);
-#pragma unroll
-    for (int k = 0; k < 3; k++) F[3 * i + k] = f[k];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < a.m.n) prep_muscl_cell(a, i, F);
 }
 
-// WAF: centre primitives P[i] = (h, u, v, z) and, per edge k, the mean of
-// (h, u, v) over the neighbours across edges k+1 and k+2 (a missing neighbour
-// stands in with the cell itself).
 template <typename T>
 __global__ void k_prep_waf(StepArgs<T> a, Vec4<T> *P, Vec4<T> *U)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.m.n) return;
-    T hi = a.h[i], ui, vi;
-    primitives(hi, a.hu[i], a.hv[i], a.h_eps, ui, vi);
-    T qh[3], qu[3], qv[3];
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-        int nb = a.m.nbr[3 * i + k];
-        if (nb >= 0) {
-            int j = nb >> 3;
-            qh[k] = a.h[j];
-            primitives(qh[k], a.hu[j], a.hv[j], a.h_eps, qu[k], qv[k]);
-        } else {
-            qh[k] = hi; qu[k] = ui; qv[k] = vi;
-        }
-    }
-    Vec4<T> p;
-    p.x = hi; p.y = ui; p.z = vi; p.w = a.m.z[i];
-    P[i] = p;
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-        int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
-        Vec4<T> u;
-        u.x = (qh[k1] + qh[k2]) / T(2);
-        u.y = (qu[k1] + qu[k2]) / T(2);
-        u.z = (qv[k1] + qv[k2]) / T(2);
-        u.w = T(0);
-        U[3 * i + k] = u;
-    }
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < a.m.n) prep_waf_cell(a, i, P, U);
 }
-
-// ---------------------------------------------------------------------------
-// flux + update kernel (split path): neighbours through global memory
-// ---------------------------------------------------------------------------
-template <typename T> struct GlobalSrc {
-    const StepArgs<T> &a;
-    int64_t i;
-    __device__ Vec4<T> own_face(int k) const { return a.F[3 * i + k]; }
-    __device__ Vec4<T> nbr_face(const Nb &b) const { return a.F[3 * (int64_t)b.idx + b.kj]; }
-    __device__ Vec4<T> nbr_centre(const Nb &b) const { return a.F[b.idx]; }
-    __device__ Vec4<T> own_up(int k) const { return a.U[3 * i + k]; }
-    __device__ Vec4<T> nbr_up(const Nb &b) const { return a.U[3 * (int64_t)b.idx + b.kj]; }
-    __device__ Vec4<T> nbr_state(const Nb &b) const
-    {
-        Vec4<T> q;
-        q.x = a.h[b.idx]; q.y = a.hu[b.idx]; q.z = a.hv[b.idx]; q.w = a.m.z[b.idx];
-        return q;
-    }
-};
 
 template <typename T, int SCHEME>
 __global__ void k_flux(StepArgs<T> a)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    bool dry;
-    const T dt = block_dt(a, &dry);
-    CellOut<T> o;
-    o.smax = T(0); o.clip = T(0); o.bsum = T(0);
-    if (i < a.m.n) {
-        Nb nb[3];
-        Vec2<T> ln[3], dd[3];
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            nb[k] = decode_global(a.m.nbr[3 * i + k]);
-            ln[k] = a.m.ln[3 * i + k];
-            if (SCHEME == SWE_SCHEME_WAF) dd[k] = a.m.dd[3 * i + k];
-        }
-        const T nm = a.m.nman ? a.m.nman[i] : T(0);
-        GlobalSrc<T> src{a, i};
-        o = cell_update<T, SCHEME>(a, dt, a.h[i], a.hu[i], a.hv[i], a.m.z[i], nm, nb, ln, dd, src);
-        a.ho[i] = o.h; a.huo[i] = o.hu; a.hvo[i] = o.hv;
-        if (!(dfinite(o.h) && dfinite(o.hu) && dfinite(o.hv))) atomicOr(&a.sc->status, ST_NONFINITE);
-    }
-    step_epilogue<T>(a, dt, dry, o.smax, o.clip, o.bsum);
+    flux_block<T, SCHEME>(a, blockIdx.x);
 }
 
 // Wave speed of the current state into slot `slot` (CFL rule of Sec. 6.1).
@@ -264,10 +167,20 @@ template <typename T> int split_max_threads(int scheme)
 {
     cudaFuncAttributes fa{};
     cudaError_t e;
-    if (scheme == SWE_SCHEME_MUSCL) e = cudaFuncGetAttributes(&fa, k_flux<T, SWE_SCHEME_MUSCL>);
-    else if (scheme == SWE_SCHEME_WAF) e = cudaFuncGetAttributes(&fa, k_flux<T, SWE_SCHEME_WAF>);
-    else e = cudaFuncGetAttributes(&fa, k_flux<T, SWE_SCHEME_HLLC>);
-    return e == cudaSuccess ? fa.maxThreadsPerBlock : 0;
+    size_t per_warp;
+    if (scheme == SWE_SCHEME_MUSCL) {
+        e = cudaFuncGetAttributes(&fa, k_flux<T, SWE_SCHEME_MUSCL>);
+        per_warp = flux_smem_per_warp<T, SWE_SCHEME_MUSCL>();
+    } else if (scheme == SWE_SCHEME_WAF) {
+        e = cudaFuncGetAttributes(&fa, k_flux<T, SWE_SCHEME_WAF>);
+        per_warp = flux_smem_per_warp<T, SWE_SCHEME_WAF>();
+    } else {
+        e = cudaFuncGetAttributes(&fa, k_flux<T, SWE_SCHEME_HLLC>);
+        per_warp = flux_smem_per_warp<T, SWE_SCHEME_HLLC>();
+    }
+    if (e != cudaSuccess) return 0;
+    const int by_smem = (int)((227 * 1024) / per_warp) * 32;
+    return std::min(fa.maxThreadsPerBlock, by_smem);
 }
 template int split_max_threads<float>(int);
 template int split_max_threads<double>(int);
@@ -282,14 +195,23 @@ cudaError_t launch_prep(int scheme, const StepArgs<T> &a, Vec4<T> *F, Vec4<T> *U
     return cudaGetLastError();
 }
 
+template <typename T, int SCHEME> cudaError_t launch_flux_s(const StepArgs<T> &a, int block, cudaStream_t s)
+{
+    const size_t smem = (size_t)(block / 32) * flux_smem_per_warp<T, SCHEME>();
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_flux<T, SCHEME>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_flux<T, SCHEME><<<grid_for(a.m.n, block), block, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_flux(int scheme, const StepArgs<T> &a, int block, cudaStream_t s)
 {
-    unsigned gr = grid_for(a.m.n, block);
-    if (scheme == SWE_SCHEME_MUSCL) k_flux<T, SWE_SCHEME_MUSCL><<<gr, block, 0, s>>>(a);
-    else if (scheme == SWE_SCHEME_WAF) k_flux<T, SWE_SCHEME_WAF><<<gr, block, 0, s>>>(a);
-    else k_flux<T, SWE_SCHEME_HLLC><<<gr, block, 0, s>>>(a);
-    return cudaGetLastError();
+    if (scheme == SWE_SCHEME_MUSCL) return launch_flux_s<T, SWE_SCHEME_MUSCL>(a, block, s);
+    if (scheme == SWE_SCHEME_WAF) return launch_flux_s<T, SWE_SCHEME_WAF>(a, block, s);
+    return launch_flux_s<T, SWE_SCHEME_HLLC>(a, block, s);
 }
 
 template <typename T>

@@ -212,15 +212,36 @@ int swe_muscl_step_noalloc(int64_t n_cells, const int32_t *nbr, const float *ln,
                            const swe_params *p, const float *inflow_qlen, int n_inflow,
                            const float *level, int n_level, void *stream);
 
+/* ---- Autotuner ----------------------------------------------------------- */
+
+/* Not in the paper.  Time trial_steps CFL steps of each kernel configuration
+ * (split kernels with 128/256/512 threads per block; for MUSCL and WAF also
+ * the fused tile kernel with 128/256) on a copy of the current state and keep
+ * the fastest; the simulation state, time and step count are left as they
+ * were (every configuration computes the same bits).  m is the state's mesh
+ * (needed to tile it for the fused kernel; NULL limits the search to the split
+ * kernels).  Outputs (may be NULL): SWE_KERNEL_*, threads per block, ms per step. */
+int swe_autotune(swe_state *s, const swe_mesh *m, int trial_steps, double cfl, int *kernel, int *block,
+                 double *ms_per_step);
+
 /* ---- Ensemble ---------------------------------------------------------- */
 
-/* Group independent states (same precision, scheme and time scheme) so that
- * one launch per step advances all of them, each with its own CFL time step.
- * The members stay owned by the caller and must outlive the ensemble. */
+/* Group independent states so that one batched launch per step (two for the
+ * split kernels) advances all of them, each with its own CFL time step, its
+ * own boundary values and its own time (the batched form of running many
+ * scenarios; cf. the paper's one-sub-domain-per-GPU layout, Sec. 6.4).
+ * Members must share precision, scheme, Euler time stepping, kernel, block,
+ * stream and step phase (steps taken mod 6; freshly initialised states do).
+ * Members stay owned by the caller, must outlive the ensemble, and can be
+ * queried (swe_get_state, swe_mass, swe_time) as usual. */
 int swe_ensemble_create(swe_state *const *members, int n_members, swe_ensemble **out);
 int swe_ensemble_destroy(swe_ensemble *e);
 int swe_ensemble_step(swe_ensemble *e, int n_steps, double cfl);
 int swe_ensemble_sync(swe_ensemble *e);
+/* Autotune the members' common kernel configuration on the whole ensemble
+ * (as swe_autotune; meshes[i] is member i's mesh, NULL for split kernels only). */
+int swe_ensemble_autotune(swe_ensemble *e, const swe_mesh *const *meshes, int trial_steps, double cfl,
+                          int *kernel, int *block, double *ms_per_step);
 
 #ifdef __cplusplus
 }

@@ -395,6 +395,222 @@ template <typename T> struct StateT {
     }
 };
 
+// ---- autotuner --------------------------------------------------------------
+
+struct Candidate { bool fused; int block; };
+
+template <typename T> std::vector<Candidate> candidates(const StateT<T> &S, const swe_mesh *m)
+{
+    std::vector<Candidate> c;
+    const int ls = split_max_threads<T>(S.p.scheme);
+    for (int b : {128, 256, 512})
+        if (b <= ls) c.push_back({false, b});
+    if (S.p.scheme != SWE_SCHEME_HLLC && m) {
+        const int lf = fused_max_threads<T>(S.p.scheme);
+        for (int b : {128, 256})
+            if (b <= lf) c.push_back({true, b});
+    }
+    return c;
+}
+
+// Time `trials` CFL steps of every candidate kernel configuration on copies
+// of the current state, keep the fastest; the state is left as it was.
+template <typename T>
+int autotune(StateT<T> &S, const swe_mesh *m, int trials, double cfl, int &best_kernel, int &best_block,
+             double &best_ms)
+{
+    if (trials < 1 || !(cfl > 0)) { swe_set_error("swe_autotune: bad argument"); return SWE_ERR_ARG; }
+    if (m && m->n != S.n) { swe_set_error("swe_autotune: mesh does not match the state"); return SWE_ERR_ARG; }
+    if (!S.smax_valid) { int rc = S.init_smax(); if (rc) return rc; }
+    typename StateT<T>::Snapshot sn;
+    int rc = S.snapshot(sn);
+    if (rc) return rc;
+    const bool fused0 = S.fused;
+    const int block0 = S.block();
+    best_ms = 1e30;
+    Candidate best{fused0, block0};
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (const Candidate &c : candidates(S, m)) {
+        if (S.configure(c.fused, c.block, m) != SWE_OK) continue;
+        rc = S.one_step(cfl, nullptr);                      // warm-up
+        if (rc == SWE_OK) rc = S.restore(sn);
+        if (rc == SWE_OK) rc = (cudaEventRecord(e0, S.stream) == cudaSuccess) ? SWE_OK : SWE_ERR_CUDA;
+        for (int q = 0; q < trials && rc == SWE_OK; q++) rc = S.one_step(cfl, nullptr);
+        float ms = 0.f;
+        if (rc == SWE_OK && cudaEventRecord(e1, S.stream) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
+            if (ms / trials < best_ms) { best_ms = ms / trials; best = c; }
+        }
+        int rr = S.restore(sn);
+        if (rc == SWE_OK) rc = rr;
+        if (rc != SWE_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int rc2 = S.configure(best.fused, best.block, m);
+    if (rc2 == SWE_OK) rc2 = S.restore(sn);
+    S.drop(sn);
+    if (rc != SWE_OK) return rc;
+    if (rc2 != SWE_OK) return rc2;
+    best_kernel = best.fused ? SWE_KERNEL_FUSED : SWE_KERNEL_SPLIT;
+    best_block = best.block;
+    return SWE_OK;
+}
+
+// ---- ensemble -----------------------------------------------------------------
+
+template <typename T> struct EnsembleT {
+    std::vector<StateT<T> *> mem;
+    cudaStream_t stream = nullptr;
+    int scheme = 0;
+    double cfl = -1.0;                 // CFL number baked into the table
+    bool built_fused = false;
+    int built_block = 0;
+    EnsEntry<T> *d_tab = nullptr;
+    int *d_begin = nullptr;
+    size_t tab_cap = 0;
+    int grid = 0;
+
+    ~EnsembleT()
+    {
+        if (stream) cudaStreamSynchronize(stream);
+        dev_free(d_tab, stream);
+        dev_free(d_begin, stream);
+    }
+
+    int check_uniform()
+    {
+        StateT<T> &s0 = *mem[0];
+        for (StateT<T> *s : mem) {
+            if (s->p.scheme != s0.p.scheme || s->p.time_scheme != SWE_EULER || s->fused != s0.fused ||
+                s->block() != s0.block() || s->stream != s0.stream || (s->k % 6) != (s0.k % 6)) {
+                swe_set_error("ensemble members need the same scheme, Euler steps, kernel, block, stream and step phase");
+                return SWE_ERR_ARG;
+            }
+        }
+        return SWE_OK;
+    }
+
+    int build(double cfl_)
+    {
+        int rc = check_uniform();
+        if (rc) return rc;
+        const size_t nm = mem.size();
+        std::vector<EnsEntry<T>> h(nm);
+        std::vector<int> begin(nm + 1, 0);
+        const bool fused = mem[0]->fused;
+        const int block = mem[0]->block();
+        for (size_t m = 0; m < nm; m++) {
+            StateT<T> &s = *mem[m];
+            for (int ph = 0; ph < 6; ph++) h[m].a[ph] = s.args_for_phase(ph, cfl_);
+            h[m].f = s.fa;
+            h[m].F = s.F;
+            h[m].U = s.U;
+            const int64_t blocks = fused ? s.fa.n_tiles : (s.n + block - 1) / block;
+            if ((int64_t)begin[m] + blocks > INT32_MAX) { swe_set_error("ensemble too large"); return SWE_ERR_ARG; }
+            begin[m + 1] = begin[m] + (int)blocks;
+        }
+        if (tab_cap < nm) {
+            dev_free(d_tab, stream);
+            dev_free(d_begin, stream);
+            d_tab = (EnsEntry<T> *)dev_alloc(sizeof(EnsEntry<T>) * nm, stream);
+            d_begin = (int *)dev_alloc(sizeof(int) * (nm + 1), stream);
+            if (!d_tab || !d_begin) { swe_set_error("device allocation failed"); return SWE_ERR_NOMEM; }
+            tab_cap = nm;
+        }
+        CK(cudaMemcpyAsync(d_tab, h.data(), sizeof(EnsEntry<T>) * nm, cudaMemcpyHostToDevice, stream));
+        CK(cudaMemcpyAsync(d_begin, begin.data(), sizeof(int) * (nm + 1), cudaMemcpyHostToDevice, stream));
+        CK(cudaStreamSynchronize(stream));
+        CK(ensemble_prepare<T>(mem[0]->p.scheme, fused, block));
+        grid = begin[nm];
+        cfl = cfl_;
+        built_fused = fused;
+        built_block = block;
+        return SWE_OK;
+    }
+
+    int step(int n, double cfl_)
+    {
+        if (n < 0 || !(cfl_ > 0.0)) { swe_set_error("swe_ensemble_step: bad argument"); return SWE_ERR_ARG; }
+        if (cfl_ != cfl || built_fused != mem[0]->fused || built_block != mem[0]->block()) {
+            int rc = build(cfl_);
+            if (rc) return rc;
+        }
+        for (StateT<T> *s : mem)
+            if (!s->smax_valid) { int rc = s->init_smax(); if (rc) return rc; }
+        for (int q = 0; q < n; q++) {
+            const int phase = (int)(mem[0]->k % 6);
+            CK(launch_ensemble<T>(scheme, built_fused, d_tab, d_begin, (int)mem.size(), phase, grid, built_block, stream));
+            for (StateT<T> *s : mem) { s->k++; s->cur ^= 1; }
+        }
+        return SWE_OK;
+    }
+
+    int sync()
+    {
+        CK(cudaStreamSynchronize(stream));
+        for (StateT<T> *s : mem) {
+            int rc = s->status();
+            if (rc) return rc;
+        }
+        return SWE_OK;
+    }
+
+    int autotune(const swe_mesh *const *meshes, int trials, double cfl_, int &best_kernel, int &best_block,
+                 double &best_ms)
+    {
+        if (trials < 1 || !(cfl_ > 0)) { swe_set_error("swe_ensemble_autotune: bad argument"); return SWE_ERR_ARG; }
+        const size_t nm = mem.size();
+        for (size_t m = 0; m < nm; m++)
+            if (meshes && (!meshes[m] || meshes[m]->n != mem[m]->n)) {
+                swe_set_error("swe_ensemble_autotune: meshes do not match the members");
+                return SWE_ERR_ARG;
+            }
+        for (StateT<T> *s : mem)
+            if (!s->smax_valid) { int rc = s->init_smax(); if (rc) return rc; }
+        std::vector<typename StateT<T>::Snapshot> sn(nm);
+        for (size_t m = 0; m < nm; m++) { int rc = mem[m]->snapshot(sn[m]); if (rc) return rc; }
+        const Candidate start{mem[0]->fused, mem[0]->block()};
+        Candidate best = start;
+        best_ms = 1e30;
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        int rc = SWE_OK;
+        for (const Candidate &c : candidates(*mem[0], meshes ? meshes[0] : nullptr)) {
+            bool ok = true;
+            for (size_t m = 0; m < nm && ok; m++) ok = mem[m]->configure(c.fused, c.block, meshes ? meshes[m] : nullptr) == SWE_OK;
+            if (!ok || build(cfl_) != SWE_OK) continue;
+            rc = step(1, cfl_);
+            for (size_t m = 0; m < nm && rc == SWE_OK; m++) rc = mem[m]->restore(sn[m]);
+            if (rc == SWE_OK) rc = cudaEventRecord(e0, stream) == cudaSuccess ? SWE_OK : SWE_ERR_CUDA;
+            if (rc == SWE_OK) rc = step(trials, cfl_);
+            float ms = 0.f;
+            if (rc == SWE_OK && cudaEventRecord(e1, stream) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+                cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms / trials < best_ms) {
+                best_ms = ms / trials;
+                best = c;
+            }
+            for (size_t m = 0; m < nm; m++) { int rr = mem[m]->restore(sn[m]); if (rc == SWE_OK) rc = rr; }
+            if (rc != SWE_OK) break;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        int rc2 = SWE_OK;
+        for (size_t m = 0; m < nm && rc2 == SWE_OK; m++) rc2 = mem[m]->configure(best.fused, best.block, meshes ? meshes[m] : nullptr);
+        for (size_t m = 0; m < nm && rc2 == SWE_OK; m++) rc2 = mem[m]->restore(sn[m]);
+        for (size_t m = 0; m < nm; m++) mem[m]->drop(sn[m]);
+        if (rc2 == SWE_OK) rc2 = build(cfl_);
+        if (rc != SWE_OK) return rc;
+        if (rc2 != SWE_OK) return rc2;
+        best_kernel = best.fused ? SWE_KERNEL_FUSED : SWE_KERNEL_SPLIT;
+        best_block = best.block;
+        return SWE_OK;
+    }
+};
+
 bool valid_params(const swe_params *p)
 {
     return p && p->scheme >= 0 && p->scheme <= 2 && (p->precision == SWE_FP64 || p->precision == SWE_FP32) &&
@@ -787,15 +1003,90 @@ int swe_dt_history(swe_state *s, double *dt, int n)
     })());
 }
 
-// Ensembles are added with the batched kernel.
-int swe_ensemble_create(swe_state *const *, int, swe_ensemble **out)
+struct swe_ensemble {
+    int precision = SWE_FP64;
+    std::unique_ptr<EnsembleT<float>> f;
+    std::unique_ptr<EnsembleT<double>> d;
+};
+
+int swe_ensemble_create(swe_state *const *members, int n_members, swe_ensemble **out)
 {
     if (out) *out = nullptr;
-    swe_set_error("swe_ensemble_create: not available in this build");
-    return SWE_ERR_ARG;
+    if (!members || n_members < 1 || !out) { swe_set_error("swe_ensemble_create: bad argument"); return SWE_ERR_ARG; }
+    for (int m = 0; m < n_members; m++)
+        if (!members[m] || members[m]->precision != members[0]->precision) {
+            swe_set_error("swe_ensemble_create: members must exist and share the precision");
+            return SWE_ERR_ARG;
+        }
+    auto *e = new swe_ensemble();
+    e->precision = members[0]->precision;
+    auto fill = [&](auto &E, auto getter) -> int {
+        for (int m = 0; m < n_members; m++) E.mem.push_back(getter(members[m]));
+        E.stream = E.mem[0]->stream;
+        E.scheme = E.mem[0]->p.scheme;
+        return E.check_uniform();
+    };
+    int rc;
+    if (e->precision == SWE_FP32) {
+        e->f.reset(new EnsembleT<float>());
+        rc = fill(*e->f, [](swe_state *s) { return s->f.get(); });
+    } else {
+        e->d.reset(new EnsembleT<double>());
+        rc = fill(*e->d, [](swe_state *s) { return s->d.get(); });
+    }
+    if (rc) { delete e; return rc; }
+    *out = e;
+    return SWE_OK;
 }
-int swe_ensemble_destroy(swe_ensemble *) { return SWE_OK; }
-int swe_ensemble_step(swe_ensemble *, int, double) { return SWE_ERR_ARG; }
-int swe_ensemble_sync(swe_ensemble *) { return SWE_ERR_ARG; }
+
+int swe_ensemble_destroy(swe_ensemble *e)
+{
+    delete e;
+    return SWE_OK;
+}
+
+int swe_ensemble_step(swe_ensemble *e, int n_steps, double cfl)
+{
+    if (!e) { swe_set_error("swe_ensemble_step: NULL ensemble"); return SWE_ERR_ARG; }
+    return e->precision == SWE_FP32 ? e->f->step(n_steps, cfl) : e->d->step(n_steps, cfl);
+}
+
+int swe_ensemble_sync(swe_ensemble *e)
+{
+    if (!e) { swe_set_error("swe_ensemble_sync: NULL ensemble"); return SWE_ERR_ARG; }
+    return e->precision == SWE_FP32 ? e->f->sync() : e->d->sync();
+}
+
+int swe_ensemble_autotune(swe_ensemble *e, const swe_mesh *const *meshes, int trial_steps, double cfl,
+                          int *kernel, int *block, double *ms_per_step)
+{
+    if (!e) { swe_set_error("swe_ensemble_autotune: NULL ensemble"); return SWE_ERR_ARG; }
+    int k = 0, b = 0;
+    double ms = 0.0;
+    int rc = e->precision == SWE_FP32 ? e->f->autotune(meshes, trial_steps, cfl, k, b, ms)
+                                      : e->d->autotune(meshes, trial_steps, cfl, k, b, ms);
+    if (rc == SWE_OK) {
+        if (kernel) *kernel = k;
+        if (block) *block = b;
+        if (ms_per_step) *ms_per_step = ms;
+    }
+    return rc;
+}
+
+int swe_autotune(swe_state *s, const swe_mesh *m, int trial_steps, double cfl, int *kernel, int *block,
+                 double *ms_per_step)
+{
+    if (!s) { swe_set_error("swe_autotune: NULL state"); return SWE_ERR_ARG; }
+    int k = 0, b = 0;
+    double ms = 0.0;
+    int rc = s->precision == SWE_FP32 ? autotune(*s->f, m, trial_steps, cfl, k, b, ms)
+                                      : autotune(*s->d, m, trial_steps, cfl, k, b, ms);
+    if (rc == SWE_OK) {
+        if (kernel) *kernel = k;
+        if (block) *block = b;
+        if (ms_per_step) *ms_per_step = ms;
+    }
+    return rc;
+}
 
 }  // extern "C"

@@ -116,8 +116,8 @@ template <typename T, int SCHEME> struct WarpSmem {
     __device__ WarpSmem(unsigned char *base)
     {
         S = reinterpret_cast<Vec4<T> *>(base);
-        U = S + (SCHEME == SWE_SCHEME_WAF ? 96 : 0);
-        LN = reinterpret_cast<Vec2<T> *>(U + (SCHEME == SWE_SCHEME_WAF ? 96 : 0));
+        U = S + 96;                                   // used by WAF only
+        LN = reinterpret_cast<Vec2<T> *>(S + (SCHEME == SWE_SCHEME_WAF ? 192 : 96));
         HC = reinterpret_cast<T *>(LN + 96);
         DL = HC + 32;
         C = DL + (SCHEME == SWE_SCHEME_WAF ? 96 : 0);

@@ -36,7 +36,7 @@ EXPORTED = [
     "swe_set_state", "swe_step", "swe_step_dt", "swe_sync", "swe_get_state", "swe_mass", "swe_time",
     "swe_state_info", "swe_ensemble_create", "swe_ensemble_destroy", "swe_ensemble_step",
     "swe_ensemble_sync", "swe_profile_begin", "swe_profile_end", "swe_dt_history",
-    "swe_muscl_step_noalloc",
+    "swe_muscl_step_noalloc", "swe_autotune", "swe_ensemble_autotune",
 ]
 NOALLOC_MAX_CELLS = 262144
 KERNEL_KINDS = ["prep", "flux", "heun_avg", "smax", "fused", "ensemble", "k6", "k7"]
@@ -100,6 +100,8 @@ def load_library(path: str = LIB_PATH, use_torch_allocator: bool = True):
     lib.swe_profile_begin.argtypes = [vp]
     lib.swe_profile_end.argtypes = [vp, vp, vp]
     lib.swe_dt_history.argtypes = [vp, vp, i32]
+    lib.swe_autotune.argtypes = [vp, vp, i32, dp, C.POINTER(i32), C.POINTER(i32), C.POINTER(dp)]
+    lib.swe_ensemble_autotune.argtypes = [vp, C.POINTER(vp), i32, dp, C.POINTER(i32), C.POINTER(i32), C.POINTER(dp)]
     lib.swe_muscl_step_noalloc.argtypes = [i64] + [vp] * 11 + [dp, C.POINTER(Params), vp, i32, vp, i32, vp]
     if use_torch_allocator:
         import torch
@@ -285,6 +287,23 @@ def swe_muscl_step_noalloc(n_cells, nbr, ln, dd, z, manning_n, h, hu, hv, h_out,
         stream if stream is not None else _current_stream()))
 
 
+def swe_autotune(s, mesh=None, trial_steps=8, cfl=0.9):
+    """Returns (kernel name, block, ms per step) of the fastest configuration, now in use."""
+    k, b, ms = C.c_int(), C.c_int(), C.c_double()
+    _check(load_library().swe_autotune(s, mesh, int(trial_steps), float(cfl), C.byref(k), C.byref(b), C.byref(ms)))
+    return {1: "split", 2: "fused"}.get(k.value, k.value), b.value, ms.value
+
+
+def swe_ensemble_autotune(e, meshes=None, trial_steps=8, cfl=0.9):
+    k, b, ms = C.c_int(), C.c_int(), C.c_double()
+    arr = None
+    if meshes is not None:
+        arr = (C.c_void_p * len(meshes))(*[m.value if isinstance(m, C.c_void_p) else m for m in meshes])
+    _check(load_library().swe_ensemble_autotune(e, arr, int(trial_steps), float(cfl), C.byref(k), C.byref(b),
+                                                C.byref(ms)))
+    return {1: "split", 2: "fused"}.get(k.value, k.value), b.value, ms.value
+
+
 def swe_ensemble_create(states):
     arr = (C.c_void_p * len(states))(*[s.value if isinstance(s, C.c_void_p) else s for s in states])
     out = C.c_void_p()
@@ -375,6 +394,38 @@ class State:
 
     def profile_end(self):
         return swe_profile_end(self.handle)
+
+    def autotune(self, mesh=None, trial_steps=8, cfl=0.9):
+        return swe_autotune(self.handle, mesh.handle if mesh is not None else None, trial_steps, cfl)
+
+
+class Ensemble:
+    """Owning wrapper of a swe_ensemble handle (the member states stay owned by the caller)."""
+
+    def __init__(self, states):
+        self.states = list(states)
+        self.handle = swe_ensemble_create([st.handle for st in self.states])
+
+    def step(self, n_steps, cfl=0.9):
+        swe_ensemble_step(self.handle, n_steps, cfl)
+
+    def sync(self):
+        swe_ensemble_sync(self.handle)
+
+    def autotune(self, meshes=None, trial_steps=8, cfl=0.9):
+        return swe_ensemble_autotune(self.handle, [m.handle for m in meshes] if meshes is not None else None,
+                                     trial_steps, cfl)
+
+    def close(self):
+        if self.handle:
+            swe_ensemble_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
     def close(self):
         if self.handle:

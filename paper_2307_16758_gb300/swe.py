@@ -398,6 +398,17 @@ class State:
     def autotune(self, mesh=None, trial_steps=8, cfl=0.9):
         return swe_autotune(self.handle, mesh.handle if mesh is not None else None, trial_steps, cfl)
 
+    def close(self):
+        if self.handle:
+            swe_state_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
 
 class Ensemble:
     """Owning wrapper of a swe_ensemble handle (the member states stay owned by the caller)."""
@@ -419,17 +430,6 @@ class Ensemble:
     def close(self):
         if self.handle:
             swe_ensemble_destroy(self.handle)
-            self.handle = None
-
-    def __del__(self):
-        try:
-            self.close()
-        except Exception:
-            pass
-
-    def close(self):
-        if self.handle:
-            swe_state_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -131,3 +131,12 @@ def test_inflow_lengths_and_packed_tags(lib):
     assert inflow.sum() >= 1
     lens = np.hypot(a["lnx"], a["lny"])
     assert lens[inflow].sum() > 0
+
+
+def test_binding_classes_own_their_handles():
+    for cls, methods in ((swe.Mesh, ("export", "close")),
+                         (swe.State, ("step", "step_dt", "get_state", "mass", "time", "autotune", "close")),
+                         (swe.Ensemble, ("step", "sync", "autotune", "close"))):
+        for m in methods:
+            assert callable(getattr(cls, m, None)), (cls.__name__, m)
+    assert swe.State.close is not swe.Ensemble.close

@@ -179,7 +179,7 @@ template <typename T> int split_max_threads(int scheme)
         per_warp = flux_smem_per_warp<T, SWE_SCHEME_HLLC>();
     }
     if (e != cudaSuccess) return 0;
-    const int by_smem = (int)((227 * 1024) / per_warp) * 32;
+    const int by_smem = per_warp ? (int)((227 * 1024) / per_warp) * 32 : 1024;
     return std::min(fa.maxThreadsPerBlock, by_smem);
 }
 template int split_max_threads<float>(int);

@@ -150,6 +150,18 @@ __device__ __forceinline__ Flux<T> riemann(T hsL, T uL, T vL, T hsR, T uR, T vR,
 // Offsets from the centroid to the three edge midpoints, from the scaled
 // outward normals: with e_k = (-ln_k.y, ln_k.x) the edge vectors,
 // m_0 - c = (e_2 - e_1)/6, m_1 - c = (e_0 - e_2)/6, m_2 - c = (e_1 - e_0)/6.
+// Products and sums that the compiler must not fuse, so that an edge's
+// contribution and a cell's sum of contributions have the same bits whether
+// the edge is evaluated by the cell (split kernels) or once per edge (fused).
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+// A fused multiply-add written out (a*b + c, one rounding): the compiler's own
+// contraction choices can differ between kernels that inline the same code.
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 template <typename T>
 __device__ __forceinline__ void midpoint_offsets(const Vec2<T> ln[3], T ox[3], T oy[3])
 {
@@ -255,6 +267,8 @@ __device__ __forceinline__ void muscl_faces(const T qi[3], T zi, bool ok, int cn
     T gx[3] = {T(0), T(0), T(0)}, gy[3] = {T(0), T(0), T(0)};
     T ox[3], oy[3];
     midpoint_offsets(ln, ox, oy);
+    // Every product below is either fused explicitly (fma_rn) or rounded on
+    // its own (mul_rn), so all kernels that inline this give the same bits.
     if (ok && cnt >= 2) {
         T Mxx = T(0), Mxy = T(0), Myy = T(0);
         T bx[3] = {T(0), T(0), T(0)}, by[3] = {T(0), T(0), T(0)};
@@ -262,19 +276,19 @@ __device__ __forceinline__ void muscl_faces(const T qi[3], T zi, bool ok, int cn
         for (int k = 0; k < 3; k++) {
             if (!has[k]) continue;
             T dx = dd[k].x, dy = dd[k].y;
-            Mxx += dx * dx; Mxy += dx * dy; Myy += dy * dy;
+            Mxx = fma_rn(dx, dx, Mxx); Mxy = fma_rn(dx, dy, Mxy); Myy = fma_rn(dy, dy, Myy);
 #pragma unroll
             for (int s = 0; s < 3; s++) {
                 T dq = qn[k][s] - qi[s];
-                bx[s] += dx * dq; by[s] += dy * dq;
+                bx[s] = fma_rn(dx, dq, bx[s]); by[s] = fma_rn(dy, dq, by[s]);
             }
         }
-        T det = Mxx * Myy - Mxy * Mxy, tr = Mxx + Myy;
-        if (det > T(1e-12) * tr * tr) {
+        T det = fma_rn(Mxx, Myy, -mul_rn(Mxy, Mxy)), tr = Mxx + Myy;
+        if (det > mul_rn(mul_rn(T(1e-12), tr), tr)) {
 #pragma unroll
             for (int s = 0; s < 3; s++) {
-                T px = ddiv(Myy * bx[s] - Mxy * by[s], det);
-                T py = ddiv(Mxx * by[s] - Mxy * bx[s], det);
+                T px = ddiv(fma_rn(Myy, bx[s], -mul_rn(Mxy, by[s])), det);
+                T py = ddiv(fma_rn(Mxx, by[s], -mul_rn(Mxy, bx[s])), det);
                 T qmin = qi[s], qmax = qi[s];
 #pragma unroll
                 for (int k = 0; k < 3; k++) {
@@ -285,21 +299,21 @@ __device__ __forceinline__ void muscl_faces(const T qi[3], T zi, bool ok, int cn
                 T phi = T(1);
 #pragma unroll
                 for (int k = 0; k < 3; k++) {
-                    T d = px * ox[k] + py * oy[k];
+                    T d = fma_rn(px, ox[k], mul_rn(py, oy[k]));
                     T ph = T(1);
                     if (d > T(0)) ph = ddiv(qmax - qi[s], d);
                     else if (d < T(0)) ph = ddiv(qmin - qi[s], d);
                     phi = dmin(phi, ph);
                 }
-                gx[s] = phi * px; gy[s] = phi * py;
+                gx[s] = mul_rn(phi, px); gy[s] = mul_rn(phi, py);
             }
         }
     }
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-        F[k].x = qi[0] + (gx[0] * ox[k] + gy[0] * oy[k]);
-        F[k].y = qi[1] + (gx[1] * ox[k] + gy[1] * oy[k]);
-        F[k].z = qi[2] + (gx[2] * ox[k] + gy[2] * oy[k]);
+        F[k].x = qi[0] + fma_rn(gx[0], ox[k], mul_rn(gy[0], oy[k]));
+        F[k].y = qi[1] + fma_rn(gx[1], ox[k], mul_rn(gy[1], oy[k]));
+        F[k].z = qi[2] + fma_rn(gx[2], ox[k], mul_rn(gy[2], oy[k]));
         F[k].w = zi;
     }
 }
@@ -331,13 +345,6 @@ __device__ __forceinline__ Nb decode_local(unsigned w)
 
 template <typename T> struct CellOut { T h, hu, hv, smax, clip, bsum; };
 
-// Products and sums that the compiler must not fuse, so that an edge's
-// contribution and a cell's sum of contributions have the same bits whether
-// the edge is evaluated by the cell (split kernels) or once per edge (fused).
-__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
-__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
 
 // Edge length and unit normal from the scaled normal (FP32: one rsqrt).
 __device__ __forceinline__ void unit_normal(float lx, float ly, float &L, float &nx, float &ny)

@@ -48,8 +48,16 @@ __global__ void k_prep_waf(StepArgs<T> a, Vec4<T> *P, Vec4<T> *U)
     if (i < a.m.n) prep_waf_cell(a, i, P, U);
 }
 
+// Register cap of the FP32 MUSCL flux kernel: 48 registers fit five
+// 256-thread blocks per SM without spills (the other instances are left to
+// the compiler, which would spill under the same cap).
+template <typename T, int SCHEME> constexpr int flux_maxnreg()
+{
+    return sizeof(T) == 4 && SCHEME == SWE_SCHEME_MUSCL ? 48 : 255;
+}
+
 template <typename T, int SCHEME>
-__global__ void k_flux(StepArgs<T> a)
+__global__ void __maxnreg__((flux_maxnreg<T, SCHEME>())) k_flux(StepArgs<T> a)
 {
     flux_block<T, SCHEME>(a, blockIdx.x);
 }

@@ -43,19 +43,20 @@ SEED = 20230733
 
 # Algorithmic bytes per cell and launch: every array element the kernel must
 # touch counted once (neighbour gathers assumed to hit in cache).
-#   split MUSCL prep : state 3 + z + nbr(3 int) + scaled normals 6 + centroid offsets 6, writes 12 face values
+#   split MUSCL prep : state 3 + z + nbr(3 int) + scaled normals 6, writes 12 face values (the
+#                      centroid offsets of the gradient come from the neighbours' normals)
 #   split MUSCL flux : state 3 + z + nbr + normals 6 + own face values 12 + Manning n, writes state 3
-#   fused MUSCL      : state 3 + z + nbr + normals 6 + offsets 6 + n, writes state 3 (the whole step)
+#   fused MUSCL      : state 3 + z + nbr + normals 6 + n, writes state 3 (the whole step)
 #   HLLC flux        : state 3 + z + nbr + normals 6 + n, writes state 3
 def algo_bytes(kind: str, scheme: str, precision: str) -> int:
     f = 4 if precision == "fp32" else 8
     nbr = 12
     if scheme == "muscl" and kind == "prep":
-        return 3 * f + f + nbr + 6 * f + 6 * f + 12 * f
+        return 3 * f + f + nbr + 6 * f + 12 * f
     if scheme == "muscl" and kind == "flux":
         return 3 * f + f + nbr + 6 * f + 12 * f + f + 3 * f
     if kind == "fused":
-        return 3 * f + f + nbr + 6 * f + 6 * f + f + 3 * f
+        return 3 * f + f + nbr + 6 * f + f + 3 * f
     if scheme == "hllc" and kind == "flux":
         return 3 * f + f + nbr + 6 * f + f + 3 * f
     if scheme == "waf" and kind == "prep":

@@ -192,8 +192,9 @@ int swe_dt_history(swe_state *s, double *dt, int n);
  *  nbr[3n]  packed neighbour words: (nbr << 3) | (nbr_edge << 1) | owner for
  *           an interior edge, owner = 1 when perm[i] < perm[nbr]; -1 - btag on
  *           a boundary edge;
- *  ln[3n][2] scaled outward normals (lnx, lny), dd[3n][2] centroid offsets
- *           (dx, dy), z[n] bed, manning_n[n] (may be NULL), h, hu, hv[n];
+ *  ln[3n][2] scaled outward normals (lnx, lny; the centroid offsets of the
+ *           gradient are derived from them), z[n] bed, manning_n[n] (may be
+ *           NULL), h, hu, hv[n];
  *  p: scheme SWE_SCHEME_MUSCL and precision SWE_FP32 (g, h_eps, r_eps, block
  *     are used); inflow_qlen[n_inflow] inflow discharge per unit length
  *     (m^2/s) per group; level[n_level] fixed levels; stream a cudaStream_t.
@@ -206,8 +207,8 @@ int swe_dt_history(swe_state *s, double *dt, int n);
  * array, so calls that overlap on the GPU race.  Asynchronous on `stream`;
  * no status is read back. */
 #define SWE_NOALLOC_MAX_CELLS 262144
-int swe_muscl_step_noalloc(int64_t n_cells, const int32_t *nbr, const float *ln, const float *dd,
-                           const float *z, const float *manning_n, const float *h, const float *hu,
+int swe_muscl_step_noalloc(int64_t n_cells, const int32_t *nbr, const float *ln, const float *z,
+                           const float *manning_n, const float *h, const float *hu,
                            const float *hv, float *h_out, float *hu_out, float *hv_out, double dt,
                            const swe_params *p, const float *inflow_qlen, int n_inflow,
                            const float *level, int n_level, void *stream);

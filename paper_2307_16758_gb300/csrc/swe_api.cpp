@@ -265,7 +265,7 @@ template <typename T> struct StateT {
         k = ph;
         StepArgs<T> a = args(ph & 1, (ph & 1) ^ 1);
         k = k0;
-        a.cfl_rmin = cfl * r_min;
+        a.cfl_rmin = (T)(cfl * r_min);
         return a;
     }
 
@@ -319,7 +319,7 @@ template <typename T> struct StateT {
     {
         const int nxt = cur ^ 1;
         StepArgs<T> a = args(cur, nxt);
-        a.cfl_rmin = cfl * r_min;
+        a.cfl_rmin = (T)(cfl * r_min);
         a.dtv = dt_dev;
         const int bl = block();
         if (p.time_scheme == SWE_EULER) {
@@ -650,7 +650,7 @@ int state_init(StateT<T> &s, const swe_mesh *m, const double *h, const double *h
     s.nbr = s.template alloc<int32_t>(3 * n);
     s.perm = s.template alloc<int32_t>(n);
     s.ln = s.template alloc<Vec2<T>>(3 * n);
-    s.dd = s.template alloc<Vec2<T>>(3 * n);
+    if (s.p.scheme == SWE_SCHEME_WAF) s.dd = s.template alloc<Vec2<T>>(3 * n);   // WAF's centroid distance
     s.z = s.template alloc<T>(n);
     if (friction) s.nman = s.template alloc<T>(n);
     s.area = s.template alloc<double>(n);
@@ -671,7 +671,7 @@ int state_init(StateT<T> &s, const swe_mesh *m, const double *h, const double *h
     CK(cudaMemcpyAsync(s.nbr, nbr.data(), sizeof(int32_t) * 3 * n, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(s.perm, m->perm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(s.ln, ln.data(), sizeof(Vec2<T>) * 3 * n, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(s.dd, dd.data(), sizeof(Vec2<T>) * 3 * n, cudaMemcpyHostToDevice, st));
+    if (s.dd) CK(cudaMemcpyAsync(s.dd, dd.data(), sizeof(Vec2<T>) * 3 * n, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(s.z, zt.data(), sizeof(T) * n, cudaMemcpyHostToDevice, st));
     if (s.nman) CK(cudaMemcpyAsync(s.nman, nt.data(), sizeof(T) * n, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(s.area, m->area.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));

@@ -17,9 +17,10 @@ template <> struct alignas(16) Vec4<float> { float x, y, z, w; };
 template <> struct alignas(32) Vec4<double> { double x, y, z, w; };
 
 // Per-state scalars updated on the device.  smax[] is a ring of three slots
-// holding the bit pattern of a non-negative double (so atomicMax on the bits
-// is a max on the values): step k reads slot k%3, writes slot (k+1)%3 and
-// clears slot (k+2)%3.
+// holding the bit pattern of a non-negative wave speed in the compute type
+// (float bits zero-extended in FP32, double bits in FP64; either way atomicMax
+// on the integer is a max on the values): step k reads slot k%3, writes slot
+// (k+1)%3 and clears slot (k+2)%3.
 struct DevScalars {
     unsigned long long smax[3];
     double t;            // simulated time
@@ -54,7 +55,7 @@ template <typename T> struct StepArgs {
     double *dt_hist;            // ring of the last SWE_DT_HISTORY time steps
     int slot_cur, slot_next, slot_clear;
     int mode;                   // MODE_EULER or MODE_STAGE (first Heun stage or second without averaging)
-    double cfl_rmin;            // cfl * r_min
+    T cfl_rmin;                 // cfl * r_min
     T g, h_eps, r_eps;
     int waf_limiter;
     T qlen[SWE_MAX_GROUPS];     // inflow discharge per unit length [m^2/s]

@@ -147,9 +147,6 @@ __device__ __forceinline__ Flux<T> riemann(T hsL, T uL, T vL, T hsR, T uR, T vR,
     return f;
 }
 
-// Offsets from the centroid to the three edge midpoints, from the scaled
-// outward normals: with e_k = (-ln_k.y, ln_k.x) the edge vectors,
-// m_0 - c = (e_2 - e_1)/6, m_1 - c = (e_0 - e_2)/6, m_2 - c = (e_1 - e_0)/6.
 // Products and sums that the compiler must not fuse, so that an edge's
 // contribution and a cell's sum of contributions have the same bits whether
 // the edge is evaluated by the cell (split kernels) or once per edge (fused).
@@ -162,13 +159,36 @@ __device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(
 __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
 
+// Offsets from the centroid to the three edge midpoints, from the scaled
+// outward normals: with e_k = (-ln_k.y, ln_k.x) the edge vectors,
+// m_0 - c = (e_2 - e_1)/6, m_1 - c = (e_0 - e_2)/6, m_2 - c = (e_1 - e_0)/6.
 template <typename T>
 __device__ __forceinline__ void midpoint_offsets(const Vec2<T> ln[3], T ox[3], T oy[3])
 {
+    // products rounded on their own (mul_rn): the offsets feed differences
+    // that the compiler could otherwise fuse differently in each kernel
     const T s = T(1) / T(6);
-    ox[0] = (-ln[2].y + ln[1].y) * s; oy[0] = (ln[2].x - ln[1].x) * s;
-    ox[1] = (-ln[0].y + ln[2].y) * s; oy[1] = (ln[0].x - ln[2].x) * s;
-    ox[2] = (-ln[1].y + ln[0].y) * s; oy[2] = (ln[1].x - ln[0].x) * s;
+    ox[0] = mul_rn(ln[1].y - ln[2].y, s); oy[0] = mul_rn(ln[2].x - ln[1].x, s);
+    ox[1] = mul_rn(ln[2].y - ln[0].y, s); oy[1] = mul_rn(ln[0].x - ln[2].x, s);
+    ox[2] = mul_rn(ln[0].y - ln[1].y, s); oy[2] = mul_rn(ln[1].x - ln[0].x, s);
+}
+
+// Centroid offset c_j - c_i across edge k of cell i, where j is the
+// neighbour and k_j its local index of the shared edge:
+// c_j - c_i = (m - c_i) - (m - c_j) with m the edge midpoint, the second term
+// the midpoint offset of j's edge k_j from j's scaled normals.  (oxi, oyi) is
+// the midpoint offset of cell i's edge k.  The centroid offsets are thus
+// derived from the normals that the kernels read anyway, not stored.
+template <typename T>
+__device__ __forceinline__ Vec2<T> centroid_offset(const Vec2<T> *ln, T oxi, T oyi, int j, int kj)
+{
+    const T s = T(1) / T(6);
+    const int k1 = kj == 2 ? 0 : kj + 1, k2 = kj == 0 ? 2 : kj - 1;
+    const Vec2<T> a1 = ln[3 * j + k1], a2 = ln[3 * j + k2];
+    Vec2<T> d;
+    d.x = oxi - mul_rn(a1.y - a2.y, s);
+    d.y = oyi - mul_rn(a2.x - a1.x, s);
+    return d;
 }
 
 template <typename T>
@@ -201,6 +221,19 @@ __device__ __forceinline__ T warp_sum(T v)
 // whose values are all zero skips its sum); thread 0 publishes them: the
 // max into the CFL slot (atomicMax on the bits of the non-negative double),
 // the sums into the FP64 diagnostics, scaled by wsum.
+// Wave speeds as ordered integers: the bits of a non-negative float or double
+// compare like the values, so atomicMax on them is a max on the speeds.
+__device__ __forceinline__ unsigned long long speed_bits(float s) { return (unsigned long long)__float_as_uint(s); }
+__device__ __forceinline__ unsigned long long speed_bits(double s)
+{
+    return (unsigned long long)__double_as_longlong(s);
+}
+__device__ __forceinline__ float speed_from_bits(unsigned long long b, float) { return __uint_as_float((unsigned)b); }
+__device__ __forceinline__ double speed_from_bits(unsigned long long b, double)
+{
+    return __longlong_as_double((long long)b);
+}
+
 template <typename T>
 __device__ __forceinline__ void block_publish(T s, T c1, T c2, DevScalars *sc, int slot_next,
                                               bool want_max, double wsum)
@@ -220,37 +253,39 @@ __device__ __forceinline__ void block_publish(T s, T c1, T c2, DevScalars *sc, i
         if (__any_sync(0xffffffffu, c1 != T(0))) c1 = warp_sum(c1);
         if (__any_sync(0xffffffffu, c2 != T(0))) c2 = warp_sum(c2);
         if (lane == 0) {
-            if (want_max && s > T(0))
-                atomicMax(&sc->smax[slot_next], (unsigned long long)__double_as_longlong((double)s));
+            if (want_max && s > T(0)) atomicMax(&sc->smax[slot_next], speed_bits(s));
             if (c1 != T(0)) atomicAdd(&sc->clipped, wsum * (double)c1);
             if (c2 != T(0)) atomicAdd(&sc->bnd_in, wsum * (double)c2);
         }
     }
 }
 
+// The CFL time step of Sec. 6.1 from the current wave-speed slot, or the
+// replayed time step.
 template <typename T>
 __device__ __forceinline__ T step_dt(const StepArgs<T> &a, bool *dry)
 {
     if (a.dtv) { *dry = false; return (T)a.dtv[0]; }
-    double sm = __longlong_as_double((long long)a.sc->smax[a.slot_cur]);
-    *dry = !(sm > 0.0);
+    const T sm = speed_from_bits(a.sc->smax[a.slot_cur], T(0));
+    *dry = !(sm > T(0));
     if (*dry) return T(0);
-    return ddiv((T)a.cfl_rmin, (T)sm);
+    return ddiv(a.cfl_rmin, sm);
 }
 
-// The time step, computed by one thread and shared with the block.
+// The time step for a block.  From the CFL slot every thread evaluates it
+// itself (one broadcast load and a division, no barrier); a replayed time
+// step (FP64 in memory) is converted by one thread and shared.
 template <typename T>
 __device__ __forceinline__ T block_dt(const StepArgs<T> &a, bool *dry)
 {
+    if (!a.dtv) return step_dt(a, dry);
     __shared__ T sh_dt;
-    __shared__ int sh_dry;
     if (threadIdx.x == 0) {
         bool d;
         sh_dt = step_dt(a, &d);
-        sh_dry = d;
     }
     __syncthreads();
-    *dry = sh_dry != 0;
+    *dry = false;
     return sh_dt;
 }
 
@@ -261,12 +296,10 @@ __device__ __forceinline__ T block_dt(const StepArgs<T> &a, bool *dry)
 // (eta, u, v, z) at the midpoint of edge k.
 template <typename T>
 __device__ __forceinline__ void muscl_faces(const T qi[3], T zi, bool ok, int cnt, const T qn[3][3],
-                                            const bool has[3], const Vec2<T> ln[3], const Vec2<T> dd[3],
-                                            Vec4<T> F[3])
+                                            const bool has[3], const T ox[3], const T oy[3],
+                                            const Vec2<T> dd[3], Vec4<T> F[3])
 {
     T gx[3] = {T(0), T(0), T(0)}, gy[3] = {T(0), T(0), T(0)};
-    T ox[3], oy[3];
-    midpoint_offsets(ln, ox, oy);
     // Every product below is either fused explicitly (fma_rn) or rounded on
     // its own (mul_rn), so all kernels that inline this give the same bits.
     if (ok && cnt >= 2) {
@@ -529,7 +562,7 @@ __device__ __forceinline__ CellOut<T> cell_update(const StepArgs<T> &a, T dt, T 
                 sj.hc = p.x; sj.uf = p.y; sj.vf = p.z; sj.z = p.w; sj.ef = p.x + p.w;
                 Ui = src.own_up(k);
                 Uj = src.nbr_up(nb[k]);
-                dlen = dsqrt(dd[k].x * dd[k].x + dd[k].y * dd[k].y);
+                dlen = dsqrt(fma_rn(dd[k].x, dd[k].x, mul_rn(dd[k].y, dd[k].y)));
             } else {
                 const Vec4<T> q = src.nbr_state(nb[k]);
                 sj.hc = q.x; sj.z = q.w; sj.ef = q.x + q.w;

@@ -82,20 +82,20 @@ __device__ __forceinline__ void fused_tile(const StepArgs<T> &a, const FusedArgs
     Nb nb[3];
     Vec2<T> ln[3];
     if (is_cell) {
-        Vec2<T> dd[3];
 #pragma unroll
         for (int k = 0; k < 3; k++) {
             nb[k] = decode_local(f.nbr_local[3 * cell + k]);
             ln[k] = a.m.ln[3 * cell + k];
-            dd[k] = a.m.dd[3 * cell + k];
         }
         const Vec4<T> pi = sm.Ps[t];
         if (SCHEME == SWE_SCHEME_MUSCL) {
             T qi[3] = {pi.x, pi.y, pi.z};
-            T qn[3][3];
+            T qn[3][3], ox[3], oy[3];
+            Vec2<T> dd[3];
             bool has[3];
             bool ok = pi.w > h_eps;
             int cnt = 0;
+            midpoint_offsets(ln, ox, oy);
 #pragma unroll
             for (int k = 0; k < 3; k++) {
                 has[k] = nb[k].interior;
@@ -103,13 +103,17 @@ __device__ __forceinline__ void fused_tile(const StepArgs<T> &a, const FusedArgs
                     const Vec4<T> pj = sm.Ps[nb[k].idx];
                     ok = ok && pj.w > h_eps;
                     qn[k][0] = pj.x; qn[k][1] = pj.y; qn[k][2] = pj.z;
+                    // global index of the neighbour's slot: a tile cell or a halo cell
+                    const int jg = nb[k].idx < nc ? s0 + nb[k].idx : f.halo_ids[hp0 + nb[k].idx - nc];
+                    dd[k] = centroid_offset(a.m.ln, ox[k], oy[k], jg, nb[k].kj);
                     cnt++;
                 } else {
                     qn[k][0] = qi[0]; qn[k][1] = qi[1]; qn[k][2] = qi[2];
+                    dd[k].x = T(0); dd[k].y = T(0);
                 }
             }
             Vec4<T> fv[3];
-            muscl_faces(qi, zi, ok, cnt, qn, has, ln, dd, fv);
+            muscl_faces(qi, zi, ok, cnt, qn, has, ox, oy, dd, fv);
 #pragma unroll
             for (int k = 0; k < 3; k++) sm.Fs[k * B + t] = fv[k];
         } else {
@@ -129,16 +133,17 @@ __device__ __forceinline__ void fused_tile(const StepArgs<T> &a, const FusedArgs
         Vec4<T> out[3];
         if (SCHEME == SWE_SCHEME_MUSCL) {
             T qi[3] = {pg.x, pg.y, pg.z};
-            T qn[3][3];
+            T qn[3][3], ox[3], oy[3];
             bool has[3];
             bool ok = pg.w > h_eps;
             int cnt = 0;
             Vec2<T> lg[3], dg[3];
 #pragma unroll
+            for (int k = 0; k < 3; k++) lg[k] = a.m.ln[3 * cell + k];
+            midpoint_offsets(lg, ox, oy);
+#pragma unroll
             for (int k = 0; k < 3; k++) {
                 const int w = a.m.nbr[3 * cell + k];
-                lg[k] = a.m.ln[3 * cell + k];
-                dg[k] = a.m.dd[3 * cell + k];
                 has[k] = w >= 0;
                 if (has[k]) {
                     const int j = w >> 3;
@@ -146,12 +151,14 @@ __device__ __forceinline__ void fused_tile(const StepArgs<T> &a, const FusedArgs
                     primitives(hj, a.hu[j], a.hv[j], h_eps, uj, vj);
                     ok = ok && hj > h_eps;
                     qn[k][0] = hj + a.m.z[j]; qn[k][1] = uj; qn[k][2] = vj;
+                    dg[k] = centroid_offset(a.m.ln, ox[k], oy[k], j, (w >> 1) & 3);
                     cnt++;
                 } else {
                     qn[k][0] = qi[0]; qn[k][1] = qi[1]; qn[k][2] = qi[2];
+                    dg[k].x = T(0); dg[k].y = T(0);
                 }
             }
-            muscl_faces(qi, zi, ok, cnt, qn, has, lg, dg, out);
+            muscl_faces(qi, zi, ok, cnt, qn, has, ox, oy, dg, out);
         } else {
             T qh[3], qu[3], qv[3];
 #pragma unroll
@@ -188,7 +195,7 @@ __device__ __forceinline__ void fused_tile(const StepArgs<T> &a, const FusedArgs
             Ui = sm.Fs[ki * B + si];
             Uj = sm.Fs[kj * B + sj];
             const Vec2<T> d = a.m.dd[ei];
-            dlen = dsqrt(d.x * d.x + d.y * d.y);
+            dlen = dsqrt(fma_rn(d.x, d.x, mul_rn(d.y, d.y)));
         }
         Contrib<T> ci, cj;
         interior_edge<T, SCHEME>(a, dt, Si, Sj, own_i, l.x, l.y, dlen, Ui, Uj, ci, jin ? &cj : nullptr);

@@ -35,7 +35,7 @@ using namespace swe_dev;
 // Barth-Jespersen limiting at the three edge midpoints.  Zero gradient if the
 // cell or a neighbour is dry or the 2x2 system is singular.
 template <typename T>
-__global__ void k_prep_muscl(StepArgs<T> a, Vec4<T> *F)
+__global__ void __maxnreg__((sizeof(T) == 4 ? 40 : 255)) k_prep_muscl(StepArgs<T> a, Vec4<T> *F)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < a.m.n) prep_muscl_cell(a, i, F);

@@ -66,8 +66,8 @@ int scratch_address(unsigned char **out)
 
 }  // namespace
 
-extern "C" int swe_muscl_step_noalloc(int64_t n_cells, const int32_t *nbr, const float *ln, const float *dd,
-                                      const float *z, const float *manning_n, const float *h, const float *hu,
+extern "C" int swe_muscl_step_noalloc(int64_t n_cells, const int32_t *nbr, const float *ln, const float *z,
+                                      const float *manning_n, const float *h, const float *hu,
                                       const float *hv, float *h_out, float *hu_out, float *hv_out, double dt,
                                       const swe_params *p, const float *inflow_qlen, int n_inflow,
                                       const float *level, int n_level, void *stream)
@@ -77,7 +77,7 @@ extern "C" int swe_muscl_step_noalloc(int64_t n_cells, const int32_t *nbr, const
                       ", got " + std::to_string(n_cells));
         return SWE_ERR_ARG;
     }
-    if (!nbr || !ln || !dd || !z || !h || !hu || !hv || !h_out || !hu_out || !hv_out || !p ||
+    if (!nbr || !ln || !z || !h || !hu || !hv || !h_out || !hu_out || !hv_out || !p ||
         !(dt >= 0.0) || p->precision != SWE_FP32 || p->scheme != SWE_SCHEME_MUSCL || !(p->g > 0) ||
         !(p->h_eps > 0) || n_inflow < 0 || n_inflow > SWE_MAX_GROUPS || n_level < 0 ||
         n_level > SWE_MAX_GROUPS || (n_inflow > 0 && !inflow_qlen) || (n_level > 0 && !level) ||
@@ -103,7 +103,7 @@ extern "C" int swe_muscl_step_noalloc(int64_t n_cells, const int32_t *nbr, const
     a.m.n = n_cells;
     a.m.nbr = nbr;
     a.m.ln = reinterpret_cast<const Vec2<float> *>(ln);
-    a.m.dd = reinterpret_cast<const Vec2<float> *>(dd);
+    a.m.dd = nullptr;   // MUSCL derives the centroid offsets from ln
     a.m.z = z;
     a.m.nman = manning_n;
     a.m.area = nullptr;

@@ -15,15 +15,16 @@ __device__ __forceinline__ void prep_muscl_cell(const StepArgs<T> &a, int i, Vec
     primitives(hi, a.hu[i], a.hv[i], h_eps, ui, vi);
     T qi[3] = {hi + zi, ui, vi};
     Vec2<T> ln[3], dd[3];
-    T qn[3][3];
+    T qn[3][3], ox[3], oy[3];
     bool has[3];
     bool ok = hi > h_eps;
     int cnt = 0;
 #pragma unroll
+    for (int k = 0; k < 3; k++) ln[k] = a.m.ln[3 * i + k];
+    midpoint_offsets(ln, ox, oy);
+#pragma unroll
     for (int k = 0; k < 3; k++) {
         const int w = a.m.nbr[3 * i + k];
-        ln[k] = a.m.ln[3 * i + k];
-        dd[k] = a.m.dd[3 * i + k];
         has[k] = w >= 0;
         if (has[k]) {
             const int j = w >> 3;
@@ -31,13 +32,15 @@ __device__ __forceinline__ void prep_muscl_cell(const StepArgs<T> &a, int i, Vec
             primitives(hj, a.hu[j], a.hv[j], h_eps, uj, vj);
             ok = ok && hj > h_eps;
             qn[k][0] = hj + a.m.z[j]; qn[k][1] = uj; qn[k][2] = vj;
+            dd[k] = centroid_offset(a.m.ln, ox[k], oy[k], j, (w >> 1) & 3);
             cnt++;
         } else {
             qn[k][0] = qi[0]; qn[k][1] = qi[1]; qn[k][2] = qi[2];
+            dd[k].x = T(0); dd[k].y = T(0);
         }
     }
     Vec4<T> f[3];
-    muscl_faces(qi, zi, ok, cnt, qn, has, ln, dd, f);
+    muscl_faces(qi, zi, ok, cnt, qn, has, ox, oy, dd, f);
 #pragma unroll
     for (int k = 0; k < 3; k++) F[3 * i + k] = f[k];
 }

@@ -102,7 +102,7 @@ def load_library(path: str = LIB_PATH, use_torch_allocator: bool = True):
     lib.swe_dt_history.argtypes = [vp, vp, i32]
     lib.swe_autotune.argtypes = [vp, vp, i32, dp, C.POINTER(i32), C.POINTER(i32), C.POINTER(dp)]
     lib.swe_ensemble_autotune.argtypes = [vp, C.POINTER(vp), i32, dp, C.POINTER(i32), C.POINTER(i32), C.POINTER(dp)]
-    lib.swe_muscl_step_noalloc.argtypes = [i64] + [vp] * 11 + [dp, C.POINTER(Params), vp, i32, vp, i32, vp]
+    lib.swe_muscl_step_noalloc.argtypes = [i64] + [vp] * 10 + [dp, C.POINTER(Params), vp, i32, vp, i32, vp]
     if use_torch_allocator:
         import torch
 
@@ -276,13 +276,13 @@ def swe_dt_history(s, n):
     return out
 
 
-def swe_muscl_step_noalloc(n_cells, nbr, ln, dd, z, manning_n, h, hu, hv, h_out, hu_out, hv_out, dt,
+def swe_muscl_step_noalloc(n_cells, nbr, ln, z, manning_n, h, hu, hv, h_out, hu_out, hv_out, dt,
                            params: Params, inflow_qlen=(), level=(), stream=None):
     """Device pointers (ints) in, device pointers out; no allocation inside."""
     qa = np.ascontiguousarray(inflow_qlen, dtype=np.float32).reshape(-1)
     la = np.ascontiguousarray(level, dtype=np.float32).reshape(-1)
     _check(load_library().swe_muscl_step_noalloc(
-        int(n_cells), nbr, ln, dd, z, manning_n, h, hu, hv, h_out, hu_out, hv_out, float(dt), C.byref(params),
+        int(n_cells), nbr, ln, z, manning_n, h, hu, hv, h_out, hu_out, hv_out, float(dt), C.byref(params),
         _p(qa) if len(qa) else None, len(qa), _p(la) if len(la) else None, len(la),
         stream if stream is not None else _current_stream()))
 

@@ -33,14 +33,13 @@ def _device_layout(mesh, w):
     owner[inner] = (perm[np.repeat(np.arange(mesh.n), 3).reshape(-1, 3)][inner] < perm[nbr[inner]]).astype(np.int32)
     packed = np.where(inner, (nbr << 3) | (ne << 1) | owner, -1 - bt).astype(np.int32)
     ln = np.stack([a["lnx"], a["lny"]], axis=-1).astype(np.float32)
-    dd = np.stack([a["dx"], a["dy"]], axis=-1).astype(np.float32)
     lens = np.hypot(a["lnx"], a["lny"])
     qlen = []
     for g, q in enumerate(w.q_in):
         sel = (~inner) & ((bt & 3) == W.INFLOW) & ((bt >> 2) == g)
         qlen.append(q / lens[sel].sum())
     cells = {k: getattr(w, k)[perm].astype(np.float32) for k in ("z", "nman", "h", "hu", "hv")}
-    return perm, packed, ln, dd, cells, np.array(qlen, np.float32), np.asarray(w.level, np.float32)
+    return perm, packed, ln, cells, np.array(qlen, np.float32), np.asarray(w.level, np.float32)
 
 
 def test_noalloc_step_matches_regular_entry_point_twice():
@@ -66,9 +65,9 @@ def test_noalloc_step_matches_regular_entry_point_twice():
         expected.append(ref.get_state())
     ref.close()
 
-    perm, packed, ln, dd, cells, qlen, level = _device_layout(mesh, w)
+    perm, packed, ln, cells, qlen, level = _device_layout(mesh, w)
     dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
-    t_nbr, t_ln, t_dd = dev(packed), dev(ln), dev(dd)
+    t_nbr, t_ln = dev(packed), dev(ln)
     t_z, t_n = dev(cells["z"]), dev(cells["nman"])
     bufs = [[dev(cells["h"]), dev(cells["hu"]), dev(cells["hv"])],
             [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3)]]
@@ -76,7 +75,7 @@ def test_noalloc_step_matches_regular_entry_point_twice():
     stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
     for call, dt in enumerate(dts):
         src, dst = bufs[call % 2], bufs[(call + 1) % 2]
-        swe.swe_muscl_step_noalloc(n, t_nbr.data_ptr(), t_ln.data_ptr(), t_dd.data_ptr(), t_z.data_ptr(),
+        swe.swe_muscl_step_noalloc(n, t_nbr.data_ptr(), t_ln.data_ptr(), t_z.data_ptr(),
                                    t_n.data_ptr(), *[b.data_ptr() for b in src], *[b.data_ptr() for b in dst],
                                    float(dt), p, qlen, level, stream)
         torch.cuda.synchronize()
@@ -95,5 +94,5 @@ def test_noalloc_rejects_meshes_above_its_limit():
     swe.load_library()
     p = swe.swe_params_default("muscl", "fp32")
     with pytest.raises(swe.SweError) as e:
-        swe.swe_muscl_step_noalloc(swe.NOALLOC_MAX_CELLS + 1, *([1] * 11), 0.1, p, stream=C.c_void_p(None))
+        swe.swe_muscl_step_noalloc(swe.NOALLOC_MAX_CELLS + 1, *([1] * 10), 0.1, p, stream=C.c_void_p(None))
     assert e.value.code == -1

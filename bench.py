@@ -86,15 +86,34 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def ncu_traffic(kernel_key: str, cells: int):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current kernels."""
+def ncu_counters(kernel_key: str):
+    """Per-cell counters of a kernel from the committed ncu summary, if taken on the current kernels."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
         return None
     d = json.load(open(path)).get(kernel_key)
     if not d or d.get("source_sha") != kernel_source_sha():
         return None
-    return float(d["dram_bytes_per_cell"]) * cells
+    return d
+
+
+def ncu_traffic(kernel_key: str, cells: int):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current kernels."""
+    d = ncu_counters(kernel_key)
+    return float(d["dram_bytes_per_cell"]) * cells if d else None
+
+
+def issue_roofline(kernel_key: str, cells: int, kernel_ms: float, sm_mhz: float, n_sm: int):
+    """The kernel against the SMs' instruction-issue rate (one warp instruction per scheduler and
+    clock, four schedulers per SM), with the warp instructions per cell that ncu counted."""
+    d = ncu_counters(kernel_key)
+    if not d or "warp_inst_per_cell" not in d or not sm_mhz:
+        return None
+    peak = 4.0 * n_sm * sm_mhz * 1e6 / 1e9                     # G warp instructions / s
+    achieved = float(d["warp_inst_per_cell"]) * cells / (kernel_ms / 1e3) / 1e9
+    return {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "G warp-inst/s",
+            "frac": achieved / peak, "warp_inst_per_cell": d["warp_inst_per_cell"],
+            "peak_source": f"4 schedulers x {n_sm} SMs x {sm_mhz:.0f} MHz (median SM clock under load)"}
 
 
 class ClockSampler:
@@ -199,8 +218,11 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / len(t_steps),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "river-13M MUSCL-HLLC (oracle on a bounded sample)", "cells": om.n,
-                   "scheme": "muscl", "precision": "fp64"},
+        "config": {"workload": f"river {RIVER_GRID[0]}x{RIVER_GRID[1]} jittered grid, "
+                               f"{2 * RIVER_GRID[0] * RIVER_GRID[1]} triangles, MUSCL-HLLC, Euler, CFL 0.9, "
+                               "Morton order (the FP64 oracle on a bounded sample of the same generator)",
+                   "cells": 2 * RIVER_GRID[0] * RIVER_GRID[1], "sample_cells": om.n, "scheme": "muscl",
+                   "precision": "fp64"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -324,6 +346,11 @@ def run_gpu(args):
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
+    iss = {k: issue_roofline(f"{kname}:{k}:muscl:fp32", n, v[0] / v[1], clocks.get("sm_mhz") or 0.0,
+                             torch.cuda.get_device_properties(local).multi_processor_count)
+           for k, v in prof.items()}
+    if any(iss.values()):
+        out["issue_roofline"] = {k: v for k, v in iss.items() if v}
 
     if rank == 0 and not args.quick:
         out.update(fp64_comparison(args, mesh, w, swe, torch))
@@ -395,17 +422,24 @@ def fp64_comparison(args, mesh, w, swe, torch):
 
 
 def cpu_baseline(w, n):
-    """The FP64 oracle as it stands, on the host cores, 2 steps of the full mesh (bounded sample)."""
+    """The FP64 oracle as it stands, on the host cores: 10 steps of the full mesh on all cores and
+    one step on one core (bounded samples)."""
     import oracle
+    import platform
     oracle.build()
     om = oracle.Mesh(w.nodes, w.tris, w.bnd_edges, w.bnd_tag)
     cores = os.cpu_count() or 1
-    o = oracle.opts("muscl", threads=cores)
     steps = 10
     t0 = time.perf_counter()
-    oracle.run(om, o, w.z, w.nman, w.h, w.hu, w.hv, steps, q_in=w.q_in, level=w.level)
+    oracle.run(om, oracle.opts("muscl", threads=cores), w.z, w.nman, w.h, w.hu, w.hv, steps, q_in=w.q_in,
+               level=w.level)
     el = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.run(om, oracle.opts("muscl", threads=1), w.z, w.nman, w.h, w.hu, w.hv, 1, q_in=w.q_in, level=w.level)
+    el1 = time.perf_counter() - t0
     return {"value": n * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "one_core": {"value": n / el1, "unit": UNIT, "sample": "1 step of the full mesh, 1 thread"},
+            "cpu": platform.processor() or platform.machine(),
             "sample": f"{steps} FP64 MUSCL-HLLC Euler steps of the full {n}-cell river mesh "
                       f"(mesh build excluded), OpenMP over cells"}
 

@@ -11,6 +11,16 @@ __device__ __forceinline__ void prep_muscl_cell(const StepArgs<T> &a, int i, Vec
 {
     const T h_eps = a.h_eps;
     T hi = a.h[i], zi = a.m.z[i];
+    if (hi <= h_eps) {
+        // a dry cell has a zero gradient and zero velocity: its three face
+        // values are its centre values (eta, 0, 0), as muscl_faces gives them;
+        // the neighbours and the geometry are not needed
+        Vec4<T> f;
+        f.x = hi + zi; f.y = T(0); f.z = T(0); f.w = zi;
+#pragma unroll
+        for (int k = 0; k < 3; k++) F[3 * i + k] = f;
+        return;
+    }
     T ui, vi;
     primitives(hi, a.hu[i], a.hv[i], h_eps, ui, vi);
     T qi[3] = {hi + zi, ui, vi};

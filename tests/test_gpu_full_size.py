@@ -75,3 +75,56 @@ def test_fp32_bench_configuration_at_full_size(river13m):
     sf.step(49, 0.9)
     assert np.array_equal(sf.get_state()[0], hs)
     sf.close()
+
+
+# ---- the 4M river (2310 x 866 grid): WAF and MUSCL in FP32 against the FP64 path ----
+
+@pytest.fixture(scope="module")
+def river4m():
+    B.build()
+    swe.load_library()
+    w = W.river(2310, 866)                          # 4,000,920 cells, same recipe as the 13M mesh
+    assert w.n_cells == 4_000_920
+    mesh = swe.Mesh.from_workload(w, "morton")
+    yield w, mesh
+    mesh.close()
+
+
+def _wetting_front(w, h, thresh=1e-3):
+    """Largest along-valley x of the cells that were dry at t = 0 and now hold more than 1 mm."""
+    cx, _ = w.centroids()
+    new = (h > thresh) & (w.h <= 0.0)
+    return float(cx[new].max()) if new.any() else float("nan")
+
+
+@pytest.mark.parametrize("scheme", ["muscl", "waf"])
+def test_river_4m_fp32_error_mass_and_front_against_fp64(river4m, scheme):
+    """FP32 bulk arithmetic after 1000 steps, at matched time (the FP64 run's dt replayed), with the
+    same h_eps (each precision keeps its own round-off guard r_eps of the WAF ratios): relative
+    L1(h) <= 1e-4 and mass drift <= 1e-6; the wetting front agrees to two cells."""
+    w, mesh = river4m
+    steps = 1000
+    p64 = swe.swe_params_default(scheme, "fp64")
+    s64 = swe.State.from_workload(mesh, p64, w)
+    m0 = s64.mass()[0]
+    s64.step(steps, 0.9)
+    dts = s64.dt_history(steps)
+    h64, hu64, hv64 = s64.get_state()
+    mass64, clip64, bin64 = s64.mass()
+    s64.close()
+    p32 = swe.swe_params_default(scheme, "fp32")
+    p32.h_eps = p64.h_eps
+    s32 = swe.State.from_workload(mesh, p32, w)
+    s32.step_dt(dts)
+    h32, hu32, hv32 = s32.get_state()
+    mass32, clip32, bin32 = s32.mass()
+    s32.close()
+    l1 = np.abs(h32 - h64).sum() / np.abs(h64).sum()
+    assert l1 <= 1e-4, l1
+    changed = h64 != w.h
+    assert changed.sum() > 1000                     # the inflow has moved water
+    assert np.abs(h32 - h64)[changed].sum() / np.abs(h64 - w.h)[changed].sum() <= 1e-3
+    assert abs(mass32 - m0 - clip32 - bin32) <= 1e-6 * m0
+    assert abs(mass64 - m0 - clip64 - bin64) <= 1e-12 * m0
+    f64, f32 = _wetting_front(w, h64), _wetting_front(w, h32)
+    assert np.isfinite(f64) and abs(f32 - f64) <= 2 * 40000.0 / 2310

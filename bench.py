@@ -176,6 +176,34 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """The largest x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """The sum of x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_throughput(cells: int, steps: int, ms_local: float, dist=None, device="cpu"):
+    """Whole-job cell-updates/s: every rank's cells x steps over the slowest rank's time (replicas,
+    no data-path collective).  Returns (value, max ms)."""
+    ms = max_over_ranks(ms_local, dist, device)
+    total = sum_over_ranks(cells, dist, device)
+    return total * steps / (ms / 1e3), ms
+
+
 def river_workload(rank: int, scale: float):
     from paper_2307_16758_gb300 import workloads as W
     nx, ny = RIVER_GRID
@@ -289,11 +317,7 @@ def run_gpu(args):
     clocks = sampler.stop(tw0, tw1)
     ms = e0.elapsed_time(e1)
     st.sync()
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * n * args.steps / (ms / 1e3)
+    value, ms = job_throughput(n, args.steps, ms, dist, "cuda")
 
     # per-kernel device time over a second timed region of the same length
     st.profile_begin()
@@ -320,7 +344,7 @@ def run_gpu(args):
     st.get_state(hout)
     mass = st.mass()
     t1 = time.perf_counter()
-    e2e = ws * n * args.steps / (t1 - t0)
+    e2e, _ = job_throughput(n, args.steps, (t1 - t0) * 1e3, dist, "cuda")
     h2d = 3 * 8 * n / args.steps
     d2h = (3 * 8 * n + 8 * 3) / args.steps
 

@@ -472,12 +472,58 @@ template <typename T> struct EnsembleT {
     int *d_begin = nullptr;
     size_t tab_cap = 0;
     int grid = 0;
+    // CUDA graphs of kGraphSteps batched steps, keyed by the starting step
+    // phase (steps taken mod 6); captured on a private stream, dropped when
+    // the table is rebuilt
+    static constexpr int kGraphSteps = 24;
+    std::map<int, cudaGraphExec_t> graphs;
+    cudaStream_t cap_stream = nullptr;
 
     ~EnsembleT()
     {
         if (stream) cudaStreamSynchronize(stream);
+        clear_graphs();
+        if (cap_stream) cudaStreamDestroy(cap_stream);
         dev_free(d_tab, stream);
         dev_free(d_begin, stream);
+    }
+
+    void clear_graphs()
+    {
+        for (auto &g : graphs) cudaGraphExecDestroy(g.second);
+        graphs.clear();
+    }
+
+    cudaError_t launch_one(int phase, cudaStream_t s)
+    {
+        return launch_ensemble<T>(scheme, built_fused, d_tab, d_begin, (int)mem.size(), phase, grid, built_block, s);
+    }
+
+    // kGraphSteps batched steps through a cached CUDA graph.
+    int graph_steps()
+    {
+        const int ph0 = (int)(mem[0]->k % 6);
+        auto it = graphs.find(ph0);
+        if (it == graphs.end()) {
+            if (!cap_stream) CK(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
+            cudaError_t e = cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal);
+            for (int q = 0; q < kGraphSteps && e == cudaSuccess; q++) e = launch_one((ph0 + q) % 6, cap_stream);
+            cudaGraph_t g = nullptr;
+            cudaError_t e2 = cudaStreamEndCapture(cap_stream, &g);
+            if (e != cudaSuccess || e2 != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                swe_set_error("CUDA graph capture failed");
+                return SWE_ERR_CUDA;
+            }
+            cudaGraphExec_t ex = nullptr;
+            e = cudaGraphInstantiate(&ex, g, 0);
+            cudaGraphDestroy(g);
+            CK(e);
+            it = graphs.emplace(ph0, ex).first;
+        }
+        CK(cudaGraphLaunch(it->second, stream));
+        for (StateT<T> *s : mem) { s->k += kGraphSteps; s->cur = (s->cur + kGraphSteps) & 1; }
+        return SWE_OK;
     }
 
     int check_uniform()
@@ -524,6 +570,7 @@ template <typename T> struct EnsembleT {
         CK(cudaMemcpyAsync(d_begin, begin.data(), sizeof(int) * (nm + 1), cudaMemcpyHostToDevice, stream));
         CK(cudaStreamSynchronize(stream));
         CK(ensemble_prepare<T>(mem[0]->p.scheme, fused, block));
+        clear_graphs();
         grid = begin[nm];
         cfl = cfl_;
         built_fused = fused;
@@ -534,15 +581,23 @@ template <typename T> struct EnsembleT {
     int step(int n, double cfl_)
     {
         if (n < 0 || !(cfl_ > 0.0)) { swe_set_error("swe_ensemble_step: bad argument"); return SWE_ERR_ARG; }
+        // members stepped on their own in between must still share the step phase
+        int rc = check_uniform();
+        if (rc) return rc;
         if (cfl_ != cfl || built_fused != mem[0]->fused || built_block != mem[0]->block()) {
-            int rc = build(cfl_);
+            rc = build(cfl_);
             if (rc) return rc;
         }
         for (StateT<T> *s : mem)
-            if (!s->smax_valid) { int rc = s->init_smax(); if (rc) return rc; }
-        for (int q = 0; q < n; q++) {
-            const int phase = (int)(mem[0]->k % 6);
-            CK(launch_ensemble<T>(scheme, built_fused, d_tab, d_begin, (int)mem.size(), phase, grid, built_block, stream));
+            if (!s->smax_valid) { rc = s->init_smax(); if (rc) return rc; }
+        int left = n;
+        while (left >= kGraphSteps) {
+            rc = graph_steps();
+            if (rc) return rc;
+            left -= kGraphSteps;
+        }
+        for (; left > 0; left--) {
+            CK(launch_one((int)(mem[0]->k % 6), stream));
             for (StateT<T> *s : mem) { s->k++; s->cur ^= 1; }
         }
         return SWE_OK;

@@ -73,38 +73,21 @@ cudaError_t launch_ensemble(int scheme, bool fused, const EnsEntry<T> *tab, cons
         kern<<<grid, block, smem, s>>>(tab, begin, n_mem, phase);
         return cudaGetLastError();
     }
-    const int nw = block / 32;
     if (scheme == SWE_SCHEME_MUSCL) {
         k_prep_ens<T, SWE_SCHEME_MUSCL><<<grid, block, 0, s>>>(tab, begin, n_mem, phase);
-        k_flux_ens<T, SWE_SCHEME_MUSCL>
-            <<<grid, block, nw * flux_smem_per_warp<T, SWE_SCHEME_MUSCL>(), s>>>(tab, begin, n_mem, phase);
+        k_flux_ens<T, SWE_SCHEME_MUSCL><<<grid, block, 0, s>>>(tab, begin, n_mem, phase);
     } else if (scheme == SWE_SCHEME_WAF) {
         k_prep_ens<T, SWE_SCHEME_WAF><<<grid, block, 0, s>>>(tab, begin, n_mem, phase);
-        k_flux_ens<T, SWE_SCHEME_WAF>
-            <<<grid, block, nw * flux_smem_per_warp<T, SWE_SCHEME_WAF>(), s>>>(tab, begin, n_mem, phase);
+        k_flux_ens<T, SWE_SCHEME_WAF><<<grid, block, 0, s>>>(tab, begin, n_mem, phase);
     } else {
-        k_flux_ens<T, SWE_SCHEME_HLLC>
-            <<<grid, block, nw * flux_smem_per_warp<T, SWE_SCHEME_HLLC>(), s>>>(tab, begin, n_mem, phase);
+        k_flux_ens<T, SWE_SCHEME_HLLC><<<grid, block, 0, s>>>(tab, begin, n_mem, phase);
     }
     return cudaGetLastError();
 }
 
 template <typename T> cudaError_t ensemble_prepare(int scheme, bool fused, int block)
 {
-    if (!fused) {
-        const int nw = block / 32;
-        cudaError_t e = cudaSuccess;
-        if (scheme == SWE_SCHEME_MUSCL)
-            e = cudaFuncSetAttribute(k_flux_ens<T, SWE_SCHEME_MUSCL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(nw * flux_smem_per_warp<T, SWE_SCHEME_MUSCL>()));
-        else if (scheme == SWE_SCHEME_WAF)
-            e = cudaFuncSetAttribute(k_flux_ens<T, SWE_SCHEME_WAF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(nw * flux_smem_per_warp<T, SWE_SCHEME_WAF>()));
-        else
-            e = cudaFuncSetAttribute(k_flux_ens<T, SWE_SCHEME_HLLC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(nw * flux_smem_per_warp<T, SWE_SCHEME_HLLC>()));
-        return e;
-    }
+    if (!fused) return cudaSuccess;
     const int smem = (int)fused_smem_bytes<T>(scheme, block);
     auto kern = scheme == SWE_SCHEME_WAF ? k_fused_ens<T, SWE_SCHEME_WAF> : k_fused_ens<T, SWE_SCHEME_MUSCL>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

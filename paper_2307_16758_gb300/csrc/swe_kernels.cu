@@ -175,20 +175,10 @@ template <typename T> int split_max_threads(int scheme)
 {
     cudaFuncAttributes fa{};
     cudaError_t e;
-    size_t per_warp;
-    if (scheme == SWE_SCHEME_MUSCL) {
-        e = cudaFuncGetAttributes(&fa, k_flux<T, SWE_SCHEME_MUSCL>);
-        per_warp = flux_smem_per_warp<T, SWE_SCHEME_MUSCL>();
-    } else if (scheme == SWE_SCHEME_WAF) {
-        e = cudaFuncGetAttributes(&fa, k_flux<T, SWE_SCHEME_WAF>);
-        per_warp = flux_smem_per_warp<T, SWE_SCHEME_WAF>();
-    } else {
-        e = cudaFuncGetAttributes(&fa, k_flux<T, SWE_SCHEME_HLLC>);
-        per_warp = flux_smem_per_warp<T, SWE_SCHEME_HLLC>();
-    }
-    if (e != cudaSuccess) return 0;
-    const int by_smem = per_warp ? (int)((227 * 1024) / per_warp) * 32 : 1024;
-    return std::min(fa.maxThreadsPerBlock, by_smem);
+    if (scheme == SWE_SCHEME_MUSCL) e = cudaFuncGetAttributes(&fa, k_flux<T, SWE_SCHEME_MUSCL>);
+    else if (scheme == SWE_SCHEME_WAF) e = cudaFuncGetAttributes(&fa, k_flux<T, SWE_SCHEME_WAF>);
+    else e = cudaFuncGetAttributes(&fa, k_flux<T, SWE_SCHEME_HLLC>);
+    return e == cudaSuccess ? fa.maxThreadsPerBlock : 0;
 }
 template int split_max_threads<float>(int);
 template int split_max_threads<double>(int);
@@ -205,12 +195,7 @@ cudaError_t launch_prep(int scheme, const StepArgs<T> &a, Vec4<T> *F, Vec4<T> *U
 
 template <typename T, int SCHEME> cudaError_t launch_flux_s(const StepArgs<T> &a, int block, cudaStream_t s)
 {
-    const size_t smem = (size_t)(block / 32) * flux_smem_per_warp<T, SCHEME>();
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_flux<T, SCHEME>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    k_flux<T, SCHEME><<<grid_for(a.m.n, block), block, smem, s>>>(a);
+    k_flux<T, SCHEME><<<grid_for(a.m.n, block), block, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -109,11 +109,6 @@ template <typename T> struct GlobalSrc {
     }
 };
 
-// Per-warp dynamic shared memory of the flux kernel: none (the cell-centric
-// flux kernel evaluates every edge from both of its cells; a warp-level
-// queue that solved in-warp edges once measured slower on GB300).
-template <typename T, int SCHEME> __host__ __device__ constexpr size_t flux_smem_per_warp() { return 0; }
-
 // Flux kernel body for one block of cells: each cell evaluates its three
 // edges (hydrostatic reconstruction, canonical Riemann flux), adds the
 // contributions in edge order and updates.

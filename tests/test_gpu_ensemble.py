@@ -61,9 +61,13 @@ def test_ensemble_members_match_stepping_alone(kernel, scheme, precision):
         assert np.array_equal(gh, h) and np.array_equal(ghu, hu) and np.array_equal(ghv, hv)
         gt, gk = st.time()
         assert gt == t and gk == k == 53
-    # the members still work on their own afterwards
+    # the members still work on their own afterwards; the ensemble then refuses to run members
+    # that are out of step with one another
     states[1].step(7, 0.9)
     assert states[1].time()[1] == 60
+    with pytest.raises(swe.SweError) as e:
+        ens.step(1, 0.9)
+    assert e.value.code == -1
 
 
 def test_ensemble_fp64_matches_the_oracle():

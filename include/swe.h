@@ -56,6 +56,9 @@ enum { SWE_FP64 = 0, SWE_FP32 = 1 };
 enum { SWE_EULER = 0, SWE_HEUN = 1 };
 enum { SWE_WAF_SUPERBEE = 0, SWE_WAF_PHI1 = 1, SWE_WAF_PHI0 = 2 };
 enum { SWE_KERNEL_AUTO = 0, SWE_KERNEL_SPLIT = 1, SWE_KERNEL_FUSED = 2 };
+/* CFL rule (Sec. 6.1, d = inscribed radius r): GLOBAL dt = CFL min_i r_i /
+ * max_wet s_i as printed; LOCAL dt = CFL min over wet cells of r_i / s_i. */
+enum { SWE_CFL_GLOBAL = 0, SWE_CFL_LOCAL = 1 };
 #define SWE_MAX_GROUPS 16
 
 typedef struct swe_mesh swe_mesh;
@@ -73,6 +76,7 @@ typedef struct {
     double r_eps;     /* WAF: relative size of a local change treated as zero */
     int kernel;       /* SWE_KERNEL_*: split (face values in scratch) or fused tile kernel */
     int block;        /* threads per block (0: default) */
+    int cfl_mode;     /* SWE_CFL_GLOBAL (default) or SWE_CFL_LOCAL */
 } swe_params;
 
 /* Values of the boundary groups (copied at init). */

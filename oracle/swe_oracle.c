@@ -45,7 +45,8 @@
  *      (hu,hv) <- (hu,hv) / (1 + dt g n^2 |u| h^(-4/3)) after the flux update.
  *  R10 Explicit Euler (Sec. 6.1) is the time scheme; Heun is offered only for
  *      the convergence-order study.
- *  R11 CFL (Sec. 6.1): dt = CFL * min_i r_i / max_wet(sqrt(g h)+|u|).
+ *  R11 CFL (Sec. 6.1): dt = CFL * min_i r_i / max_wet(sqrt(g h)+|u|); as an
+ *      option, per cell: dt = CFL * min over wet cells of r_i / s_i.
  *  R12 Each interior edge is evaluated in one canonical orientation (L = the
  *      cell with the lower original id), so both cells see the same flux.
  *  R13 MUSCL: unweighted least-squares gradients of (eta,u,v) over the face
@@ -783,16 +784,18 @@ int om_run(const om_mesh *m, const om_opts *o,
         if (dt_given) {
             dt = dt_given[s];
         } else {
-            /* CFL rule of Sec. 6.1 with d = inscribed radius (R11) */
-            double smax = 0.0;
+            /* CFL rule of Sec. 6.1 with d = inscribed radius (R11): the global
+             * form min_i r_i / max_i s_i, or per cell min_i (r_i / s_i) */
+            double smax = 0.0, rs_min = INFINITY;
             for (int64_t i = 0; i < n; i++) {
                 if (h[i] <= o->h_eps) continue;
                 double u = hu[i] / h[i], v = hv[i] / h[i];
                 double sp = sqrt(o->g * h[i]) + sqrt(u * u + v * v);
                 if (sp > smax) smax = sp;
+                if (sp > 0.0 && m->rin[i] / sp < rs_min) rs_min = m->rin[i] / sp;
             }
             if (!(smax > 0.0)) { rc = -4; break; }
-            dt = o->cfl * rmin / smax;
+            dt = o->cfl_local ? o->cfl * rs_min : o->cfl * rmin / smax;
         }
         if (dt_used) dt_used[s] = dt;
         euler_stage(m, o, &w, z, nman, qlen, level, h, hu, hv, h1, hu1, hv1, dt);

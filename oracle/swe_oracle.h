@@ -58,6 +58,8 @@ typedef struct {
     double h_eps;      /* velocity desingularisation / dry threshold [m] */
     double r_eps;      /* WAF: |local change| below r_eps*max(1,|q|) gives r = 0 */
     double cfl;
+    int cfl_local;     /* 0: dt = CFL min_i r_i / max_wet s_i (Sec. 6.1, global form);
+                          1: dt = CFL min over wet cells of r_i / s_i (per-cell form) */
 } om_opts;
 
 /* Advance n_steps.  h,hu,hv are updated in place.  dt_given (length n_steps)

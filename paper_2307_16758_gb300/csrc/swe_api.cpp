@@ -265,7 +265,7 @@ template <typename T> struct StateT {
         k = ph;
         StepArgs<T> a = args(ph & 1, (ph & 1) ^ 1);
         k = k0;
-        a.cfl_rmin = (T)(cfl * r_min);
+        a.cfl_rmin = cfl_factor(cfl);
         return a;
     }
 
@@ -275,6 +275,10 @@ template <typename T> struct StateT {
         m.n = n; m.nbr = nbr; m.ln = ln; m.dd = dd; m.z = z; m.nman = nman; m.area = area;
         return m;
     }
+
+    // Numerator of the CFL time step: cfl * r_min in the global form (the
+    // published speed is max s_i), cfl in the local form (max s_i / r_i).
+    T cfl_factor(double cfl) const { return (T)(p.cfl_mode == SWE_CFL_LOCAL ? cfl : cfl * r_min); }
 
     StepArgs<T> args(int in, int out) const
     {
@@ -287,6 +291,7 @@ template <typename T> struct StateT {
         a.dt_hist = dt_hist;
         a.slot_cur = (int)(k % 3); a.slot_next = (int)((k + 1) % 3); a.slot_clear = (int)((k + 2) % 3);
         a.mode = MODE_EULER;
+        a.cfl_local = p.cfl_mode == SWE_CFL_LOCAL;
         a.g = (T)p.g; a.h_eps = (T)p.h_eps; a.r_eps = (T)p.r_eps;
         a.waf_limiter = p.waf_limiter;
         for (int q = 0; q < SWE_MAX_GROUPS; q++) { a.qlen[q] = qlen[q]; a.level[q] = level[q]; }
@@ -319,7 +324,7 @@ template <typename T> struct StateT {
     {
         const int nxt = cur ^ 1;
         StepArgs<T> a = args(cur, nxt);
-        a.cfl_rmin = (T)(cfl * r_min);
+        a.cfl_rmin = cfl_factor(cfl);
         a.dtv = dt_dev;
         const int bl = block();
         if (p.time_scheme == SWE_EULER) {
@@ -671,7 +676,8 @@ bool valid_params(const swe_params *p)
     return p && p->scheme >= 0 && p->scheme <= 2 && (p->precision == SWE_FP64 || p->precision == SWE_FP32) &&
            (p->time_scheme == SWE_EULER || p->time_scheme == SWE_HEUN) && p->waf_limiter >= 0 &&
            p->waf_limiter <= 2 && p->g > 0 && p->h_eps > 0 && p->r_eps >= 0 && p->kernel >= 0 &&
-           p->kernel <= 2 && p->block >= 0 && p->block <= 1024 && (p->block % 32) == 0;
+           p->kernel <= 2 && p->block >= 0 && p->block <= 1024 && (p->block % 32) == 0 &&
+           (p->cfl_mode == SWE_CFL_GLOBAL || p->cfl_mode == SWE_CFL_LOCAL);
 }
 
 template <typename T>
@@ -777,6 +783,7 @@ int swe_params_default(swe_params *p, int scheme, int precision)
     p->r_eps = precision == SWE_FP64 ? 1e-12 : 1e-6;
     p->kernel = SWE_KERNEL_AUTO;
     p->block = 0;
+    p->cfl_mode = SWE_CFL_GLOBAL;
     return SWE_OK;
 }
 

@@ -55,7 +55,8 @@ template <typename T> struct StepArgs {
     double *dt_hist;            // ring of the last SWE_DT_HISTORY time steps
     int slot_cur, slot_next, slot_clear;
     int mode;                   // MODE_EULER or MODE_STAGE (first Heun stage or second without averaging)
-    T cfl_rmin;                 // cfl * r_min
+    T cfl_rmin;                 // cfl * r_min (global CFL form) or cfl (local form)
+    int cfl_local;              // 1: the published wave speed is s_i / r_i (local CFL form)
     T g, h_eps, r_eps;
     int waf_limiter;
     T qlen[SWE_MAX_GROUPS];     // inflow discharge per unit length [m^2/s]

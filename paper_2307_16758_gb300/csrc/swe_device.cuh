@@ -392,6 +392,14 @@ __device__ __forceinline__ void unit_normal(double lx, double ly, double &L, dou
     nx = lx / L; ny = ly / L;
 }
 
+// The edge length alone (the same bits as unit_normal's L in FP32).
+__device__ __forceinline__ float edge_length(float lx, float ly)
+{
+    const float l2 = fma_rn(lx, lx, mul_rn(ly, ly));
+    return l2 * rsqrtf(l2);
+}
+__device__ __forceinline__ double edge_length(double lx, double ly) { return sqrt(fma_rn(lx, lx, mul_rn(ly, ly))); }
+
 // Contribution of one edge to its cell's flux sum: L * (M, P n - Tt t) with t = (-n_y, n_x).
 template <typename T> struct Contrib { T c0, c1, c2; };
 
@@ -487,6 +495,27 @@ __device__ __forceinline__ Contrib<T> boundary_edge(const StepArgs<T> &a, const 
     return contribution(L, M, P, Tt, nx, ny);
 }
 
+// 1 / r of a triangle from its scaled normals: the perimeter over twice the
+// area (r = 2A / P, the CFL length of Sec. 6.1).
+template <typename T>
+__device__ __forceinline__ T inv_inradius(const Vec2<T> ln[3])
+{
+    const T per = edge_length(ln[0].x, ln[0].y) + edge_length(ln[1].x, ln[1].y) + edge_length(ln[2].x, ln[2].y);
+    return ddiv(per, ln[0].x * ln[1].y - ln[0].y * ln[1].x);
+}
+
+// The CFL quantity that cell i publishes for its wave speed s: s itself in the
+// global form, s / r_i in the local form (normals read here).
+template <typename T>
+__device__ __forceinline__ T cfl_speed(const StepArgs<T> &a, int64_t i, T s)
+{
+    if (!a.cfl_local || !(s > T(0))) return s;
+    Vec2<T> ln[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) ln[k] = a.m.ln[3 * i + k];
+    return mul_rn(s, inv_inradius(ln));
+}
+
 // Add contribution k (k = 0, 1, 2 in this order) to the cell's sum.
 template <typename T>
 __device__ __forceinline__ void accumulate(int k, const Contrib<T> &c, T &R0, T &R1, T &R2)
@@ -520,6 +549,7 @@ __device__ __forceinline__ CellOut<T> cell_finish(const StepArgs<T> &a, T dt, T 
     if (hn > h_eps) {
         const T u = ddiv(hun, hn), v = ddiv(hvn, hn);
         o.smax = dsqrt(g * hn) + dsqrt(u * u + v * v);
+        if (a.cfl_local) o.smax = mul_rn(o.smax, inv_inradius(ln));
     }
     o.bsum = bs * dt;
     return o;

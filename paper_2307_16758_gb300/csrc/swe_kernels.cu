@@ -72,7 +72,7 @@ __global__ void k_smax(StepArgs<T> a, int slot)
         T h = a.h[i];
         if (h > a.h_eps) {
             T u = a.hu[i] / h, v = a.hv[i] / h;
-            s = dsqrt(a.g * h) + dsqrt(u * u + v * v);
+            s = cfl_speed(a, i, dsqrt(a.g * h) + dsqrt(u * u + v * v));
         }
     }
     block_publish<T>(s, T(0), T(0), a.sc, slot, true, 1.0);
@@ -89,7 +89,7 @@ __global__ void k_heun_avg(StepArgs<T> a, const T *h0, const T *hu0, const T *hv
         a.ho[i] = h; a.huo[i] = hu; a.hvo[i] = hv;
         if (h > a.h_eps) {
             T u = hu / h, v = hv / h;
-            s = dsqrt(a.g * h) + dsqrt(u * u + v * v);
+            s = cfl_speed(a, i, dsqrt(a.g * h) + dsqrt(u * u + v * v));
         }
     }
     block_publish<T>(s, T(0), T(0), a.sc, a.slot_next, true, 1.0);

@@ -28,6 +28,7 @@ PRECISION = {"fp64": 0, "fp32": 1}
 TIME_SCHEME = {"euler": 0, "heun": 1}
 WAF_LIMITER = {"superbee": 0, "phi1": 1, "phi0": 2}
 KERNEL = {"auto": 0, "split": 1, "fused": 2}
+CFL_MODE = {"global": 0, "local": 1}
 MAX_GROUPS = 16
 
 EXPORTED = [
@@ -51,7 +52,7 @@ class SweError(RuntimeError):
 class Params(C.Structure):
     _fields_ = [("scheme", C.c_int), ("precision", C.c_int), ("time_scheme", C.c_int),
                 ("waf_limiter", C.c_int), ("g", C.c_double), ("h_eps", C.c_double),
-                ("r_eps", C.c_double), ("kernel", C.c_int), ("block", C.c_int)]
+                ("r_eps", C.c_double), ("kernel", C.c_int), ("block", C.c_int), ("cfl_mode", C.c_int)]
 
 
 class BcValues(C.Structure):
@@ -157,6 +158,8 @@ def swe_params_default(scheme="muscl", precision="fp32", **over) -> Params:
             v = WAF_LIMITER.get(v, v)
         elif k == "kernel":
             v = KERNEL.get(v, v)
+        elif k == "cfl_mode":
+            v = CFL_MODE.get(v, v)
         setattr(p, k, v)
     return p
 

@@ -45,7 +45,8 @@ def test_params_default(lib):
     p = swe.swe_params_default("muscl", "fp32")
     assert p.scheme == 1 and p.precision == 1 and p.g == 9.81 and p.h_eps == 1e-4
     p = swe.swe_params_default("hllc", "fp64")
-    assert p.h_eps == 1e-6 and p.r_eps == 1e-12 and p.time_scheme == 0
+    assert p.h_eps == 1e-6 and p.r_eps == 1e-12 and p.time_scheme == 0 and p.cfl_mode == 0
+    assert swe.swe_params_default("muscl", "fp64", cfl_mode="local").cfl_mode == 1
     with pytest.raises(swe.SweError) as e:
         swe.swe_params_default(7, "fp64")
     assert e.value.code == -1

@@ -235,3 +235,38 @@ def test_set_state_round_trip_and_resume():
     end_b = b.get_state()
     for x, y in zip(end_a, end_b):
         assert np.array_equal(x, y)
+
+
+# ---- CFL forms (R11: the printed global form, and the local form as an option) ----
+
+@pytest.mark.parametrize("kernel,time_scheme", [("split", "euler"), ("fused", "euler"), ("split", "heun")])
+def test_fp64_local_cfl_steps_match_the_oracle(kernel, time_scheme):
+    """CFL-driven steps (not replayed) on a jittered mesh with a breach: the GPU's time steps and
+    state follow the oracle's under the per-cell form, which differs from the global one there."""
+    w = _pdb()
+    o = run_oracle(w, "muscl", steps=40, cfl_mode="local", time_scheme=time_scheme)
+    og = run_oracle(w, "muscl", steps=1, time_scheme=time_scheme)
+    assert o["dts"][0] > og["dts"][0] * (1 + 1e-9)        # the local form takes a longer first step
+    p = swe.swe_params_default("muscl", "fp64", kernel=kernel, cfl_mode="local", time_scheme=time_scheme)
+    m = swe.Mesh.from_workload(w, "morton")
+    s = swe.State.from_workload(m, p, w)
+    s.step(40, 0.9)
+    dts = s.dt_history(40)
+    h, hu, hv = s.get_state()
+    s.close()
+    m.close()
+    assert np.allclose(dts, o["dts"], rtol=1e-12, atol=0)
+    assert max(state_errors(dict(h=h, hu=hu, hv=hv), o)) <= 1e-9
+
+
+def test_fp32_local_cfl_takes_the_oracle_first_step():
+    w = _pdb()
+    o = run_oracle(w, "muscl", steps=1, cfl_mode="local", h_eps=1e-4, r_eps=1e-6)
+    g = swe.swe_params_default("muscl", "fp32", cfl_mode="local")
+    m = swe.Mesh.from_workload(w, "morton")
+    s = swe.State.from_workload(m, g, w)
+    s.step(1, 0.9)
+    dt = s.dt_history(1)[0]
+    s.close()
+    m.close()
+    assert math.isclose(dt, o["dts"][0], rel_tol=1e-6)

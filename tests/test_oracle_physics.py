@@ -452,6 +452,58 @@ def test_first_time_step_closed_form():
     assert math.isclose(dts[0], 0.9 * r / math.sqrt(G * 1.0), rel_tol=1e-14)
 
 
+def _graded_strip():
+    """Right triangles of legs 1 x 1 (x < 4) and 0.5 x 1 (4 < x < 6), two rows, walls;
+    h = 1, u = 3 m/s on the coarse cells and 0 on the fine ones."""
+    xs = np.array([0.0, 1.0, 2.0, 3.0, 4.0, 4.5, 5.0, 5.5, 6.0])
+    ys = np.array([0.0, 1.0, 2.0])
+    nodes = np.array([[x, y] for y in ys for x in xs])
+    nx = len(xs)
+    tris = []
+    for j in range(len(ys) - 1):
+        for i in range(nx - 1):
+            p = j * nx + i
+            tris += [[p, p + 1, p + nx + 1], [p, p + nx + 1, p + nx]]
+    tris = np.array(tris, np.int32)
+    n = len(tris)
+    cx = nodes[tris, 0].mean(axis=1)
+    coarse = cx < 4.0
+    w = W.Workload("graded", nodes, tris, np.zeros((0, 2), np.int32), np.zeros(0, np.int32),
+                   np.zeros((0, 2), np.int32), np.zeros(n), np.zeros(n), np.ones(n),
+                   np.where(coarse, 3.0, 0.0), np.zeros(n))
+    return w, coarse
+
+
+def _inradius_right(a, b):
+    """Inscribed radius of a right triangle with legs a, b: area / semi-perimeter."""
+    return a * b / (a + b + math.hypot(a, b))
+
+
+@pytest.mark.parametrize("mode", ["global", "local"])
+def test_first_time_step_per_cell_cfl_closed_form(mode):
+    """Both CFL forms on cells of two sizes (the option of R11): the global form takes the
+    smallest cell and the fastest cell, min r / max s; the local form the smallest r_i / s_i."""
+    w, coarse = _graded_strip()
+    m = _mesh(w)
+    _, _, _, dts, _ = oracle.run(m, oracle.opts("hllc", cfl=0.9, cfl_mode=mode), w.z, w.nman, w.h, w.hu,
+                                 w.hv, 1)
+    r_c, r_f = _inradius_right(1.0, 1.0), _inradius_right(0.5, 1.0)
+    s_c, s_f = math.sqrt(G) + 3.0, math.sqrt(G)
+    want = 0.9 * r_f / s_c if mode == "global" else 0.9 * min(r_c / s_c, r_f / s_f)
+    assert math.isclose(dts[0], want, rel_tol=1e-14)
+
+
+def test_per_cell_cfl_equals_global_on_equal_cells_and_is_never_smaller():
+    w = W.dam_break_1d()
+    m = _mesh(w)
+    run = lambda mode, ww: oracle.run(m if ww is w else _mesh(ww), oracle.opts("hllc", cfl=0.9, cfl_mode=mode),
+                                      ww.z, ww.nman, ww.h, ww.hu, ww.hv, 20)[3]
+    dg, dl = run("global", w), run("local", w)
+    assert np.allclose(dg, dl, rtol=1e-14, atol=0)          # equal cells: the same condition
+    w2, _ = _graded_strip()
+    assert (run("local", w2)[0] >= run("global", w2)[0])
+
+
 def test_fixed_level_boundary_fills_to_its_level():
     """A fixed-level boundary above a lake at rest lets water in until the lake
     stands at that level (the steady state of the boundary condition)."""

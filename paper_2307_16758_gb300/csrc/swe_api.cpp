@@ -721,7 +721,7 @@ int state_init(StateT<T> &s, const swe_mesh *m, const double *h, const double *h
     }
     s.sc = s.template alloc<DevScalars>(1);
     s.n_part = mass_partials_needed(n);
-    s.mass_part = s.template alloc<double>(s.n_part);
+    s.mass_part = s.template alloc<double>(2 * s.n_part);   // (sum, compensation) per block
     s.mass_out = s.template alloc<double>(1);
     s.staging = s.template alloc<double>(3 * n);
     s.dt_hist = s.template alloc<double>(SWE_DT_HISTORY);

@@ -33,8 +33,11 @@ __device__ __forceinline__ int block_member(const int *begin, int n_mem)
     return sh_m;
 }
 
+// Register caps as for the single-mesh kernels (swe_kernels.cu): FP32 MUSCL
+// prep at 40 and flux at 48 registers.
 template <typename T, int SCHEME>
-__global__ void k_prep_ens(const EnsEntry<T> *tab, const int *begin, int n_mem, int phase)
+__global__ void __maxnreg__((sizeof(T) == 4 && SCHEME == SWE_SCHEME_MUSCL ? 40 : 255))
+    k_prep_ens(const EnsEntry<T> *tab, const int *begin, int n_mem, int phase)
 {
     const int m = block_member(begin, n_mem);
     const EnsEntry<T> &e = tab[m];
@@ -46,7 +49,8 @@ __global__ void k_prep_ens(const EnsEntry<T> *tab, const int *begin, int n_mem, 
 }
 
 template <typename T, int SCHEME>
-__global__ void k_flux_ens(const EnsEntry<T> *tab, const int *begin, int n_mem, int phase)
+__global__ void __maxnreg__((sizeof(T) == 4 && SCHEME == SWE_SCHEME_MUSCL ? 48 : 255))
+    k_flux_ens(const EnsEntry<T> *tab, const int *begin, int n_mem, int phase)
 {
     const int m = block_member(begin, n_mem);
     flux_block<T, SCHEME>(tab[m].a[phase], (int)blockIdx.x - begin[m]);

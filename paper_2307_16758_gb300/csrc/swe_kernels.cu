@@ -103,42 +103,65 @@ __global__ void k_heun_avg(StepArgs<T> a, const T *h0, const T *hu0, const T *hv
     }
 }
 
-// Mass: per-block FP64 partial sums in a fixed tree order, then one block
-// adds the partials in a fixed order (deterministic).
+// Mass: per-block FP64 compensated partial sums (value and lost low-order
+// part) in a fixed tree order, then one block merges the partials in a fixed
+// order (deterministic; the total is within a few ulp of the exact sum).
 constexpr int MASS_BLOCK = 256;
 constexpr int MASS_ITEMS = 8;
+
+// Compensated (Neumaier) summation: (s, c) holds the sum s and the lost
+// low-order part c; the total is s + c.
+struct Comp { double s, c; };
+
+__device__ __forceinline__ void comp_add(Comp &a, double x)
+{
+    const double t = __dadd_rn(a.s, x);
+    a.c += fabs(a.s) >= fabs(x) ? __dadd_rn(__dsub_rn(a.s, t), x) : __dadd_rn(__dsub_rn(x, t), a.s);
+    a.s = t;
+}
+
+__device__ __forceinline__ void comp_merge(Comp &a, const Comp &b)
+{
+    comp_add(a, b.s);
+    a.c += b.c;
+}
+
+// Fixed-order tree over the block's (s, c) pairs; thread 0 ends with the total.
+__device__ __forceinline__ Comp block_comp_sum(Comp v)
+{
+    __shared__ double ss[MASS_BLOCK], sc[MASS_BLOCK];
+    ss[threadIdx.x] = v.s; sc[threadIdx.x] = v.c;
+    __syncthreads();
+    for (int o = MASS_BLOCK / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            Comp a{ss[threadIdx.x], sc[threadIdx.x]};
+            comp_merge(a, Comp{ss[threadIdx.x + o], sc[threadIdx.x + o]});
+            ss[threadIdx.x] = a.s; sc[threadIdx.x] = a.c;
+        }
+        __syncthreads();
+    }
+    return Comp{ss[0], sc[0]};
+}
 
 template <typename T>
 __global__ void __launch_bounds__(MASS_BLOCK) k_mass_partial(DevMesh<T> m, const T *h, double *partials)
 {
-    __shared__ double sh[MASS_BLOCK];
     const int64_t base = (int64_t)blockIdx.x * MASS_BLOCK * MASS_ITEMS;
-    double s = 0.0;
+    Comp v{0.0, 0.0};
     for (int q = 0; q < MASS_ITEMS; q++) {
         int64_t i = base + (int64_t)q * MASS_BLOCK + threadIdx.x;
-        if (i < m.n) s += m.area[i] * (double)h[i];
+        if (i < m.n) comp_add(v, __dmul_rn(m.area[i], (double)h[i]));
     }
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = MASS_BLOCK / 2; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
+    const Comp t = block_comp_sum(v);
+    if (threadIdx.x == 0) { partials[2 * blockIdx.x] = t.s; partials[2 * blockIdx.x + 1] = t.c; }
 }
 
 __global__ void __launch_bounds__(MASS_BLOCK) k_mass_final(const double *partials, int n, double *out)
 {
-    __shared__ double sh[MASS_BLOCK];
-    double s = 0.0;
-    for (int q = threadIdx.x; q < n; q += MASS_BLOCK) s += partials[q];
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = MASS_BLOCK / 2; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) out[0] = sh[0];
+    Comp v{0.0, 0.0};
+    for (int q = threadIdx.x; q < n; q += MASS_BLOCK) comp_merge(v, Comp{partials[2 * q], partials[2 * q + 1]});
+    const Comp t = block_comp_sum(v);
+    if (threadIdx.x == 0) out[0] = t.s + t.c;
 }
 
 // Original-order FP64 host layout <-> renumbered device state.

@@ -270,3 +270,19 @@ def test_fp32_local_cfl_takes_the_oracle_first_step():
     s.close()
     m.close()
     assert math.isclose(dt, o["dts"][0], rel_tol=1e-6)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_mass_is_the_correctly_rounded_sum(precision):
+    """swe_mass sums area_i * h_i with compensation: within a few ulp of the exactly rounded sum."""
+    w = _river(160, 60)
+    m = swe.Mesh.from_workload(w, "morton")
+    a = m.export()
+    s = swe.State.from_workload(m, swe.swe_params_default("muscl", precision), w)
+    s.step(30, 0.9)
+    h = s.get_state()[0]
+    mass = s.mass()[0]
+    s.close()
+    m.close()
+    exact = math.fsum((a["area"] * h[a["perm"]]).tolist())
+    assert abs(mass - exact) <= 4 * np.spacing(exact), (mass, exact)

@@ -51,9 +51,9 @@ SEED = 20230733
 def algo_bytes(kind: str, scheme: str, precision: str) -> int:
     f = 4 if precision == "fp32" else 8
     nbr = 12
-    if scheme == "muscl" and kind == "prep":
+    if scheme in ("muscl", "muscl_edge") and kind == "prep":
         return 3 * f + f + nbr + 6 * f + 12 * f
-    if scheme == "muscl" and kind == "flux":
+    if scheme in ("muscl", "muscl_edge") and kind == "flux":
         return 3 * f + f + nbr + 6 * f + 12 * f + f + 3 * f
     if kind == "fused":
         return 3 * f + f + nbr + 6 * f + f + 3 * f
@@ -290,7 +290,7 @@ def run_gpu(args):
     w, grid = river_workload(rank, args.scale)
     mesh = swe.Mesh.from_workload(w, "morton")
     n = mesh.n
-    p32 = swe.swe_params_default("muscl", "fp32", kernel=args.kernel)
+    p32 = swe.swe_params_default(args.scheme, "fp32", kernel=args.kernel)
     st = swe.State.from_workload(mesh, p32, w)
     dev_bytes, kernel_used, block = st.info()
     kname = {1: "split", 2: "fused"}.get(kernel_used, str(kernel_used))
@@ -326,12 +326,12 @@ def run_gpu(args):
     launches = sum(c for _, c in prof.values())
     dom = max(prof, key=lambda k: prof[k][0])
     dom_ms = prof[dom][0] / prof[dom][1]
-    bytes_launch = algo_bytes(dom, "muscl", "fp32") * n
+    bytes_launch = algo_bytes(dom, args.scheme, "fp32") * n
     peak, peak_src = measured_peaks()
     achieved = bytes_launch / (dom_ms / 1e3) / 1e9
-    traffic = ncu_traffic(f"{kname}:{dom}:muscl:fp32", n)
+    traffic = ncu_traffic(f"{kname}:{dom}:{args.scheme}:fp32", n)
     step_ms = ms / args.steps
-    step_ideal = step_bytes_ideal("muscl", "fp32") * n / (step_ms / 1e3) / 1e9
+    step_ideal = step_bytes_ideal(args.scheme, "fp32") * n / (step_ms / 1e3) / 1e9
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).pin_memory().numpy()
@@ -353,24 +353,25 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {
-            "workload": f"river {grid[0]}x{grid[1]} jittered grid, {n} triangles, MUSCL-HLLC FP32 bulk "
+            "workload": f"river {grid[0]}x{grid[1]} jittered grid, {n} triangles, "
+                        f"{'MUSCL-HLLC' if args.scheme == 'muscl' else 'edge-upwind MUSCL-HLLC'} FP32 bulk "
                         "(FP64 mass/time), Euler, CFL 0.9, Morton order",
-            "cells": n, "scheme": "muscl", "precision": "fp32", "time_scheme": "euler", "kernel": kname,
+            "cells": n, "scheme": args.scheme, "precision": "fp32", "time_scheme": "euler", "kernel": kname,
             "block": block, "device_bytes": dev_bytes,
             "l2": f"inputs larger than L2: {dev_bytes / 1e9:.2f} GB resident per state, no flush needed",
             "parallelism": "replicas" if ws > 1 else "single GPU", "seed": SEED,
         },
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
-                     "algo_bytes_per_cell": algo_bytes(dom, "muscl", "fp32"),
+                     "algo_bytes_per_cell": algo_bytes(dom, args.scheme, "fp32"),
                      "kernel_ms": dom_ms, "per_kernel_ms": {k: v[0] / v[1] for k, v in prof.items()},
-                     "step_ideal_bytes_per_cell": step_bytes_ideal("muscl", "fp32"),
+                     "step_ideal_bytes_per_cell": step_bytes_ideal(args.scheme, "fp32"),
                      "step_frac_of_ideal": step_ideal / peak},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
-    iss = {k: issue_roofline(f"{kname}:{k}:muscl:fp32", n, v[0] / v[1], clocks.get("sm_mhz") or 0.0,
+    iss = {k: issue_roofline(f"{kname}:{k}:{args.scheme}:fp32", n, v[0] / v[1], clocks.get("sm_mhz") or 0.0,
                              torch.cuda.get_device_properties(local).multi_processor_count)
            for k, v in prof.items()}
     if any(iss.values()):
@@ -394,7 +395,7 @@ def fp64_comparison(args, mesh, w, swe, torch):
     """FP64 GPU path: its throughput, and the FP32 error against it at matched time."""
     n = mesh.n
     m_steps = args.fp64_steps
-    p64 = swe.swe_params_default("muscl", "fp64", kernel=args.kernel)
+    p64 = swe.swe_params_default(args.scheme, "fp64", kernel=args.kernel)
     s64 = swe.State.from_workload(mesh, p64, w)
     s64.step(3, args.cfl)
     s64.sync()
@@ -410,7 +411,7 @@ def fp64_comparison(args, mesh, w, swe, torch):
     dts = s64.dt_history(m_steps)
     h64, hu64, hv64 = s64.get_state()
     mass64 = s64.mass()
-    p32 = swe.swe_params_default("muscl", "fp32", kernel=args.kernel)
+    p32 = swe.swe_params_default(args.scheme, "fp32", kernel=args.kernel)
     p32.h_eps = p64.h_eps         # same algorithm, precision differs only
     p32.r_eps = p64.r_eps
     s32 = swe.State.from_workload(mesh, p32, w)
@@ -543,6 +544,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cfl", type=float, default=0.9)
     ap.add_argument("--kernel", default="auto", choices=["auto", "split", "fused"])
+    ap.add_argument("--scheme", default="muscl", choices=["muscl", "muscl_edge"],
+                    help="MUSCL-HLLC with least-squares gradients (default) or the paper's edge-upwind MUSCL")
     ap.add_argument("--fp64-steps", type=int, default=1000)
     ap.add_argument("--scale", type=float, default=1.0, help="fraction of the 13M-cell mesh (testing only)")
     ap.add_argument("--quick", action="store_true", help="skip the FP64 comparison and the CPU baseline")

@@ -51,7 +51,11 @@ enum {
 
 enum { SWE_WALL = 0, SWE_OPEN = 1, SWE_INFLOW = 2, SWE_LEVEL = 3 };
 enum { SWE_REORDER_NONE = 0, SWE_REORDER_MORTON = 1, SWE_REORDER_RCM = 2 };
-enum { SWE_SCHEME_HLLC = 0, SWE_SCHEME_MUSCL = 1, SWE_SCHEME_WAF = 2 };
+/* HLLC first order (Sec. 6.2.1); MUSCL-HLLC with least-squares gradients and
+ * a Barth-Jespersen limiter; WAF-HLLC (Sec. 6.2.2); MUSCL_EDGE: the paper's
+ * MUSCL (Sec. 6.2.3), slopes along each edge from the upwind means of the
+ * two other neighbours, limited with parameter beta (split kernels only). */
+enum { SWE_SCHEME_HLLC = 0, SWE_SCHEME_MUSCL = 1, SWE_SCHEME_WAF = 2, SWE_SCHEME_MUSCL_EDGE = 3 };
 enum { SWE_FP64 = 0, SWE_FP32 = 1 };
 enum { SWE_EULER = 0, SWE_HEUN = 1 };
 enum { SWE_WAF_SUPERBEE = 0, SWE_WAF_PHI1 = 1, SWE_WAF_PHI0 = 2 };
@@ -77,6 +81,7 @@ typedef struct {
     int kernel;       /* SWE_KERNEL_*: split (face values in scratch) or fused tile kernel */
     int block;        /* threads per block (0: default) */
     int cfl_mode;     /* SWE_CFL_GLOBAL (default) or SWE_CFL_LOCAL */
+    double muscl_beta; /* SWE_SCHEME_MUSCL_EDGE limiter, 1 (MINBEE) .. 2 (SUPERBEE, default) */
 } swe_params;
 
 /* Values of the boundary groups (copied at init). */
@@ -90,7 +95,8 @@ typedef struct {
 const char *swe_last_error(void);
 
 /* Defaults: g = 9.81, h_eps = 1e-6 (FP64) or 1e-4 (FP32),
- * r_eps = 1e-12 (FP64) or 1e-6 (FP32), Euler, SUPERBEE, automatic kernel. */
+ * r_eps = 1e-12 (FP64) or 1e-6 (FP32), Euler, SUPERBEE, automatic kernel,
+ * global CFL form, muscl_beta = 2. */
 int swe_params_default(swe_params *p, int scheme, int precision);
 
 /* Device memory: by default cudaMalloc/cudaFree.  A host program (for example

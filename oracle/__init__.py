@@ -19,7 +19,7 @@ _SRC = os.path.join(_HERE, "swe_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
-SCHEMES = {"hllc": 0, "muscl": 1, "waf": 2}
+SCHEMES = {"hllc": 0, "muscl": 1, "waf": 2, "muscl_edge": 3}
 BC_WALL, BC_OPEN, BC_INFLOW, BC_LEVEL = 0, 1, 2, 3
 
 
@@ -37,7 +37,8 @@ def build(force: bool = False) -> str:
 class _Opts(C.Structure):
     _fields_ = [("scheme", C.c_int), ("time_scheme", C.c_int), ("waf_limiter", C.c_int),
                 ("threads", C.c_int), ("g", C.c_double), ("h_eps", C.c_double),
-                ("r_eps", C.c_double), ("cfl", C.c_double), ("cfl_local", C.c_int)]
+                ("r_eps", C.c_double), ("cfl", C.c_double), ("cfl_local", C.c_int),
+                ("beta", C.c_double)]
 
 
 def _load():
@@ -58,6 +59,8 @@ def _load():
         lib.om_edge_flux.argtypes = [C.POINTER(_Opts), vp, vp, vp]
         lib.om_mass.argtypes = [vp, vp]
         lib.om_mass.restype = C.c_double
+        lib.om_beta_limit.argtypes = [C.c_double, C.c_double, C.c_double]
+        lib.om_beta_limit.restype = C.c_double
         _lib = lib
     return _lib
 
@@ -67,10 +70,10 @@ def _p(a):
 
 
 def opts(scheme="hllc", time_scheme="euler", waf_limiter="superbee", g=9.81, h_eps=1e-6,
-         r_eps=1e-12, cfl=0.9, threads=0, cfl_mode="global") -> _Opts:
+         r_eps=1e-12, cfl=0.9, threads=0, cfl_mode="global", beta=2.0) -> _Opts:
     return _Opts(SCHEMES[scheme], {"euler": 0, "heun": 1}[time_scheme],
                  {"superbee": 0, "phi1": 1, "phi0": 2}[waf_limiter], threads,
-                 g, h_eps, r_eps, cfl, {"global": 0, "local": 1}[cfl_mode])
+                 g, h_eps, r_eps, cfl, {"global": 0, "local": 1}[cfl_mode], beta)
 
 
 class Mesh:
@@ -164,3 +167,8 @@ def edge_flux(o: _Opts, state, waf=None):
     out = np.empty(4)
     lib.om_edge_flux(C.byref(o), _p(a), _p(w), _p(out))
     return out
+
+
+def beta_limit(beta, up, dn):
+    """The limited slope of the paper's MUSCL (Sec. 6.2.3); see om_beta_limit."""
+    return float(_load().om_beta_limit(float(beta), float(up), float(dn)))

@@ -55,6 +55,16 @@
  *      singular.  u = hu/h if h > h_eps else 0.  Depth below 0 after the
  *      update is set to 0 and the mass that adds is recorded; momentum is
  *      zeroed where h <= h_eps.
+ *  R15 The paper's own MUSCL (Sec. 6.2.3, scheme 3): the reconstructed
+ *      variables are (eta, u, v), as in R13; x_RL is the edge midpoint and
+ *      distances are Euclidean; the upwind value of a side is the mean over
+ *      its cell's two other neighbours and sits at the mean of their
+ *      centroids (a missing neighbour stands in with the cell, as in R4); an
+ *      upwind distance of 0 (no other neighbour) gives an upwind slope of 0;
+ *      the limited slope is 0 when its condition difference is 0, and when
+ *      the side's cell, the other cell or one of its upwind cells is dry;
+ *      boundary edges use the cell-centre values.  HR, Riemann flux and
+ *      update are those of the other schemes.
  */
 #include "swe_oracle.h"
 
@@ -616,6 +626,67 @@ static void upwind_means(const om_mesh *m, const work_t *w, const double *h, int
     *hm = sh / 2.0; *um = su / 2.0; *vm = sv / 2.0;
 }
 
+/* Sec. 6.2.3: the limited slope of the paper's MUSCL (see om_beta_limit). */
+double om_beta_limit(double beta, double up, double dn)
+{
+    if (dn > 0.0) {
+        double p = fmin(beta * up, dn), q = fmin(up, beta * dn);
+        return fmax(0.0, fmax(p, q));
+    }
+    if (dn < 0.0) {
+        double p = fmax(beta * up, dn), q = fmax(up, beta * dn);
+        return fmin(0.0, fmin(p, q));
+    }
+    return 0.0;
+}
+
+/* upwind data of cell c for its edge e: mean of (eta, u, v) over its two
+ * other neighbours, the position of that mean (mean of their centroids), and
+ * whether those cells are wet; a missing neighbour stands in with c (R15) */
+static void paper_upwind(const om_mesh *m, const om_opts *o, const work_t *w, const double *h, int64_t c, int e,
+                         double *q, double *px, double *py, int *wet)
+{
+    q[0] = q[1] = q[2] = 0.0;
+    *px = *py = 0.0;
+    *wet = 1;
+    for (int d = 1; d <= 2; d++) {
+        int32_t j = m->nbr[3 * c + (e + d) % 3];
+        int64_t s = j >= 0 ? j : c;
+        q[0] += w->eta[s] / 2.0; q[1] += w->u[s] / 2.0; q[2] += w->v[s] / 2.0;
+        *px += m->cx[s] / 2.0; *py += m->cy[s] / 2.0;
+        if (h[s] <= o->h_eps) *wet = 0;
+    }
+}
+
+/* Reconstructed states of the paper's MUSCL (Sec. 6.2.3) at the edge between
+ * L (cell l, its local edge kl) and R (cell r, edge kr), as printed:
+ *   U~_L = U_L + |x_RL - x_L| dU_L,   U~_R = U_R - |x_R - x_RL| dU_R,
+ *   dU_L = lim((U_L - U_Lupw)/|x_L - x_Lupw|, (U_R - U_L)/|x_R - x_L|),
+ *   dU_R = lim((U_R - U_L)/|x_R - x_L|, (U_Rupw - U_R)/|x_Rupw - x_R|),
+ * componentwise for (eta, u, v), with the readings of R15. */
+static void paper_edge_states(const om_mesh *m, const om_opts *o, const work_t *w, const double *h,
+                              int64_t l, int kl, int64_t r, int kr, double *fl, double *fr)
+{
+    const double ql[3] = {w->eta[l], w->u[l], w->v[l]}, qr[3] = {w->eta[r], w->u[r], w->v[r]};
+    double ul[3], ur[3], lx, ly, rx, ry;
+    int wl, wr;
+    paper_upwind(m, o, w, h, l, kl, ul, &lx, &ly, &wl);
+    paper_upwind(m, o, w, h, r, kr, ur, &rx, &ry, &wr);
+    const double d_lr = hypot(m->cx[r] - m->cx[l], m->cy[r] - m->cy[l]);
+    const double d_lu = hypot(m->cx[l] - lx, m->cy[l] - ly), d_ru = hypot(rx - m->cx[r], ry - m->cy[r]);
+    const double m_l = hypot(m->mx[3 * l + kl], m->my[3 * l + kl]);   /* |x_RL - x_L| */
+    const double m_r = hypot(m->mx[3 * r + kr], m->my[3 * r + kr]);   /* |x_R - x_RL| */
+    const int wet_lr = h[l] > o->h_eps && h[r] > o->h_eps;
+    for (int s = 0; s < 3; s++) {
+        const double s_lr = (qr[s] - ql[s]) / d_lr;
+        double dl = 0.0, dr = 0.0;
+        if (wet_lr && wl) dl = om_beta_limit(o->beta, d_lu > 0.0 ? (ql[s] - ul[s]) / d_lu : 0.0, s_lr);
+        if (wet_lr && wr) dr = om_beta_limit(o->beta, s_lr, d_ru > 0.0 ? (ur[s] - qr[s]) / d_ru : 0.0);
+        fl[s] = ql[s] + m_l * dl;
+        fr[s] = qr[s] - m_r * dr;
+    }
+}
+
 static void euler_stage(const om_mesh *m, const om_opts *o, work_t *w,
                         const double *z, const double *nman, const double *qlen, const double *level,
                         const double *h, const double *hu, const double *hv,
@@ -649,8 +720,12 @@ static void euler_stage(const om_mesh *m, const om_opts *o, work_t *w,
                 int ka = i < j ? k : kj, kb = i < j ? kj : k;
                 double cnx = i < j ? nx : -nx, cny = i < j ? ny : -ny;
                 double fa[3], fb[3];
-                face_values(m, w, scheme, a, ka, fa);
-                face_values(m, w, scheme, b, kb, fb);
+                if (scheme == 3) {
+                    paper_edge_states(m, o, w, h, a, ka, b, kb, fa, fb);
+                } else {
+                    face_values(m, w, scheme, a, ka, fa);
+                    face_values(m, w, scheme, b, kb, fb);
+                }
                 double hfa = fa[0] - z[a]; if (hfa < 0.0) hfa = 0.0;
                 double hfb = fb[0] - z[b]; if (hfb < 0.0) hfb = 0.0;
                 double zf = z[a] > z[b] ? z[a] : z[b];            /* R6 */

@@ -50,7 +50,8 @@ int om_rcm_order(const om_mesh *m, int32_t *perm);
 
 /* Options of one run. */
 typedef struct {
-    int scheme;        /* 0 first-order HLLC, 1 MUSCL (LSQ + Barth-Jespersen) + HLLC, 2 WAF */
+    int scheme;        /* 0 first-order HLLC, 1 MUSCL (LSQ + Barth-Jespersen) + HLLC, 2 WAF,
+                          3 the paper's MUSCL (edge-upwind slopes, beta-limiter) + HLLC */
     int time_scheme;   /* 0 explicit Euler, 1 Heun (SSP-RK2, order studies only) */
     int waf_limiter;   /* 0 SUPERBEE, 1 phi = 1 (no limiting), 2 phi = 0 */
     int threads;       /* OpenMP threads (0 = default); results do not depend on it */
@@ -60,6 +61,7 @@ typedef struct {
     double cfl;
     int cfl_local;     /* 0: dt = CFL min_i r_i / max_wet s_i (Sec. 6.1, global form);
                           1: dt = CFL min over wet cells of r_i / s_i (per-cell form) */
+    double beta;       /* scheme 3: limiter parameter (1 MINBEE, 2 SUPERBEE) */
 } om_opts;
 
 /* Advance n_steps.  h,hu,hv are updated in place.  dt_given (length n_steps)
@@ -89,6 +91,12 @@ int om_gradients(const om_mesh *m, const om_opts *o, const double *z,
  * side (hydrostatic-reconstruction form, cell-centre pressure removed) and
  * the tangential momentum flux. */
 int om_edge_flux(const om_opts *o, const double *in, const double *waf, double *out);
+
+/* The limited slope of the paper's MUSCL (Sec. 6.2.3) from the slope "up"
+ * behind the cell and the slope "dn" towards the other side of the edge:
+ * dn > 0: max(0, min(beta up, dn), min(up, beta dn));
+ * dn < 0: min(0, max(beta up, dn), max(up, beta dn)); dn = 0: 0. */
+double om_beta_limit(double beta, double up, double dn);
 
 /* Sum of area*h in FP64 with Neumaier compensation, in cell order. */
 double om_mass(const om_mesh *m, const double *h);

@@ -201,7 +201,7 @@ template <typename T> struct StateT {
             CK(up(fa.nbr_local, tl.nbr_local.data(), sizeof(uint16_t) * 3 * n));
             p.kernel = SWE_KERNEL_FUSED;
         } else {
-            if (p.scheme == SWE_SCHEME_MUSCL && !F) F = alloc<Vec4<T>>(3 * n);
+            if ((p.scheme == SWE_SCHEME_MUSCL || p.scheme == SWE_SCHEME_MUSCL_EDGE) && !F) F = alloc<Vec4<T>>(3 * n);
             if (p.scheme == SWE_SCHEME_WAF && !F) { F = alloc<Vec4<T>>(n); U = alloc<Vec4<T>>(3 * n); }
             if (p.scheme != SWE_SCHEME_HLLC && (!F || (p.scheme == SWE_SCHEME_WAF && !U))) {
                 swe_set_error("device allocation failed");
@@ -293,6 +293,7 @@ template <typename T> struct StateT {
         a.mode = MODE_EULER;
         a.cfl_local = p.cfl_mode == SWE_CFL_LOCAL;
         a.g = (T)p.g; a.h_eps = (T)p.h_eps; a.r_eps = (T)p.r_eps;
+        a.beta = (T)p.muscl_beta;
         a.waf_limiter = p.waf_limiter;
         for (int q = 0; q < SWE_MAX_GROUPS; q++) { a.qlen[q] = qlen[q]; a.level[q] = level[q]; }
         return a;
@@ -410,7 +411,7 @@ template <typename T> std::vector<Candidate> candidates(const StateT<T> &S, cons
     const int ls = split_max_threads<T>(S.p.scheme);
     for (int b : {128, 256, 512})
         if (b <= ls) c.push_back({false, b});
-    if (S.p.scheme != SWE_SCHEME_HLLC && m) {
+    if ((S.p.scheme == SWE_SCHEME_MUSCL || S.p.scheme == SWE_SCHEME_WAF) && m) {
         const int lf = fused_max_threads<T>(S.p.scheme);
         for (int b : {128, 256})
             if (b <= lf) c.push_back({true, b});
@@ -673,11 +674,13 @@ template <typename T> struct EnsembleT {
 
 bool valid_params(const swe_params *p)
 {
-    return p && p->scheme >= 0 && p->scheme <= 2 && (p->precision == SWE_FP64 || p->precision == SWE_FP32) &&
+    return p && p->scheme >= 0 && p->scheme <= 3 && (p->precision == SWE_FP64 || p->precision == SWE_FP32) &&
            (p->time_scheme == SWE_EULER || p->time_scheme == SWE_HEUN) && p->waf_limiter >= 0 &&
            p->waf_limiter <= 2 && p->g > 0 && p->h_eps > 0 && p->r_eps >= 0 && p->kernel >= 0 &&
            p->kernel <= 2 && p->block >= 0 && p->block <= 1024 && (p->block % 32) == 0 &&
-           (p->cfl_mode == SWE_CFL_GLOBAL || p->cfl_mode == SWE_CFL_LOCAL);
+           (p->cfl_mode == SWE_CFL_GLOBAL || p->cfl_mode == SWE_CFL_LOCAL) &&
+           (p->scheme != SWE_SCHEME_MUSCL_EDGE || (p->muscl_beta >= 1.0 && p->muscl_beta <= 2.0)) &&
+           (p->scheme != SWE_SCHEME_MUSCL_EDGE || p->kernel != SWE_KERNEL_FUSED);
 }
 
 template <typename T>
@@ -769,7 +772,7 @@ const char *swe_last_error(void) { return g_err.c_str(); }
 
 int swe_params_default(swe_params *p, int scheme, int precision)
 {
-    if (!p || scheme < 0 || scheme > 2 || (precision != SWE_FP64 && precision != SWE_FP32)) {
+    if (!p || scheme < 0 || scheme > 3 || (precision != SWE_FP64 && precision != SWE_FP32)) {
         swe_set_error("swe_params_default: bad argument");
         return SWE_ERR_ARG;
     }
@@ -784,6 +787,7 @@ int swe_params_default(swe_params *p, int scheme, int precision)
     p->kernel = SWE_KERNEL_AUTO;
     p->block = 0;
     p->cfl_mode = SWE_CFL_GLOBAL;
+    p->muscl_beta = 2.0;
     return SWE_OK;
 }
 

@@ -58,6 +58,7 @@ template <typename T> struct StepArgs {
     T cfl_rmin;                 // cfl * r_min (global CFL form) or cfl (local form)
     int cfl_local;              // 1: the published wave speed is s_i / r_i (local CFL form)
     T g, h_eps, r_eps;
+    T beta;                     // MUSCL_EDGE slope-limiter parameter
     int waf_limiter;
     T qlen[SWE_MAX_GROUPS];     // inflow discharge per unit length [m^2/s]
     T level[SWE_MAX_GROUPS];    // fixed free-surface levels [m]

@@ -45,6 +45,7 @@ __global__ void __maxnreg__((sizeof(T) == 4 && SCHEME == SWE_SCHEME_MUSCL ? 40 :
     const int i = ((int)blockIdx.x - begin[m]) * blockDim.x + threadIdx.x;
     if (i >= a.m.n) return;
     if (SCHEME == SWE_SCHEME_MUSCL) prep_muscl_cell(a, i, e.F);
+    else if (SCHEME == SWE_SCHEME_MUSCL_EDGE) prep_muscl_edge_cell(a, i, e.F);
     else prep_waf_cell(a, i, e.F, e.U);
 }
 
@@ -79,6 +80,9 @@ cudaError_t launch_ensemble(int scheme, bool fused, const EnsEntry<T> *tab, cons
     }
     if (scheme == SWE_SCHEME_MUSCL) {
         k_prep_ens<T, SWE_SCHEME_MUSCL><<<grid, block, 0, s>>>(tab, begin, n_mem, phase);
+        k_flux_ens<T, SWE_SCHEME_MUSCL><<<grid, block, 0, s>>>(tab, begin, n_mem, phase);
+    } else if (scheme == SWE_SCHEME_MUSCL_EDGE) {
+        k_prep_ens<T, SWE_SCHEME_MUSCL_EDGE><<<grid, block, 0, s>>>(tab, begin, n_mem, phase);
         k_flux_ens<T, SWE_SCHEME_MUSCL><<<grid, block, 0, s>>>(tab, begin, n_mem, phase);
     } else if (scheme == SWE_SCHEME_WAF) {
         k_prep_ens<T, SWE_SCHEME_WAF><<<grid, block, 0, s>>>(tab, begin, n_mem, phase);

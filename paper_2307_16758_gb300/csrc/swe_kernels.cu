@@ -41,6 +41,14 @@ __global__ void __maxnreg__((sizeof(T) == 4 ? 40 : 255)) k_prep_muscl(StepArgs<T
     if (i < a.m.n) prep_muscl_cell(a, i, F);
 }
 
+// The paper's MUSCL (Sec. 6.2.3): edge-upwind slopes, beta-limited.
+template <typename T>
+__global__ void k_prep_muscl_edge(StepArgs<T> a, Vec4<T> *F)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < a.m.n) prep_muscl_edge_cell(a, i, F);
+}
+
 template <typename T>
 __global__ void k_prep_waf(StepArgs<T> a, Vec4<T> *P, Vec4<T> *U)
 {
@@ -198,7 +206,7 @@ template <typename T> int split_max_threads(int scheme)
 {
     cudaFuncAttributes fa{};
     cudaError_t e;
-    if (scheme == SWE_SCHEME_MUSCL) e = cudaFuncGetAttributes(&fa, k_flux<T, SWE_SCHEME_MUSCL>);
+    if (scheme == SWE_SCHEME_MUSCL || scheme == SWE_SCHEME_MUSCL_EDGE) e = cudaFuncGetAttributes(&fa, k_flux<T, SWE_SCHEME_MUSCL>);
     else if (scheme == SWE_SCHEME_WAF) e = cudaFuncGetAttributes(&fa, k_flux<T, SWE_SCHEME_WAF>);
     else e = cudaFuncGetAttributes(&fa, k_flux<T, SWE_SCHEME_HLLC>);
     return e == cudaSuccess ? fa.maxThreadsPerBlock : 0;
@@ -212,6 +220,7 @@ template <typename T>
 cudaError_t launch_prep(int scheme, const StepArgs<T> &a, Vec4<T> *F, Vec4<T> *U, int block, cudaStream_t s)
 {
     if (scheme == SWE_SCHEME_MUSCL) k_prep_muscl<T><<<grid_for(a.m.n, block), block, 0, s>>>(a, F);
+    else if (scheme == SWE_SCHEME_MUSCL_EDGE) k_prep_muscl_edge<T><<<grid_for(a.m.n, block), block, 0, s>>>(a, F);
     else if (scheme == SWE_SCHEME_WAF) k_prep_waf<T><<<grid_for(a.m.n, block), block, 0, s>>>(a, F, U);
     return cudaGetLastError();
 }
@@ -225,7 +234,8 @@ template <typename T, int SCHEME> cudaError_t launch_flux_s(const StepArgs<T> &a
 template <typename T>
 cudaError_t launch_flux(int scheme, const StepArgs<T> &a, int block, cudaStream_t s)
 {
-    if (scheme == SWE_SCHEME_MUSCL) return launch_flux_s<T, SWE_SCHEME_MUSCL>(a, block, s);
+    // the paper's MUSCL differs only in prep: its flux kernel is the MUSCL one
+    if (scheme == SWE_SCHEME_MUSCL || scheme == SWE_SCHEME_MUSCL_EDGE) return launch_flux_s<T, SWE_SCHEME_MUSCL>(a, block, s);
     if (scheme == SWE_SCHEME_WAF) return launch_flux_s<T, SWE_SCHEME_WAF>(a, block, s);
     return launch_flux_s<T, SWE_SCHEME_HLLC>(a, block, s);
 }

@@ -23,7 +23,7 @@ ERRORS = {-1: "SWE_ERR_ARG", -2: "SWE_ERR_MESH", -3: "SWE_ERR_CUDA", -4: "SWE_ER
           -5: "SWE_ERR_NONFINITE", -6: "SWE_ERR_TIMEOUT", -7: "SWE_ERR_NOMEM"}
 SWE_WALL, SWE_OPEN, SWE_INFLOW, SWE_LEVEL = 0, 1, 2, 3
 REORDER = {"none": 0, "morton": 1, "rcm": 2}
-SCHEME = {"hllc": 0, "muscl": 1, "waf": 2}
+SCHEME = {"hllc": 0, "muscl": 1, "waf": 2, "muscl_edge": 3}
 PRECISION = {"fp64": 0, "fp32": 1}
 TIME_SCHEME = {"euler": 0, "heun": 1}
 WAF_LIMITER = {"superbee": 0, "phi1": 1, "phi0": 2}
@@ -52,7 +52,8 @@ class SweError(RuntimeError):
 class Params(C.Structure):
     _fields_ = [("scheme", C.c_int), ("precision", C.c_int), ("time_scheme", C.c_int),
                 ("waf_limiter", C.c_int), ("g", C.c_double), ("h_eps", C.c_double),
-                ("r_eps", C.c_double), ("kernel", C.c_int), ("block", C.c_int), ("cfl_mode", C.c_int)]
+                ("r_eps", C.c_double), ("kernel", C.c_int), ("block", C.c_int), ("cfl_mode", C.c_int),
+                ("muscl_beta", C.c_double)]
 
 
 class BcValues(C.Structure):

@@ -25,6 +25,7 @@ import argparse
 import glob
 import hashlib
 import json
+import math
 import os
 import subprocess
 import sys
@@ -536,6 +537,69 @@ def run_ensemble(args):
     }))
 
 
+def run_time_error(args):
+    """Time against L2 error on the paper's wet-bed dam break (Sec. 6.3: [0,10] x [0,1], h = 1 | 0.5,
+    t = 1 s) for 20k-600k cells, every scheme, FP32 and FP64: GPU time of the CFL steps that reach
+    t = 1 (CUDA events, after an untimed run that counts them) and the area-weighted relative L2
+    error of h against the closed form (Stoker) at the time reached.  The MUSCL schemes also run
+    with Heun steps and with Euler at CFL 0.45 (Euler at 0.9 does not converge for them)."""
+    import torch
+
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from exact import stoker
+    from paper_2307_16758_gb300 import swe
+    from paper_2307_16758_gb300 import workloads as W
+    import __graft_entry__
+
+    __graft_entry__.build()
+    swe.load_library()
+    stream = torch.cuda.current_stream()
+    rows = []
+    for cells in (20_000, 50_000, 100_000, 200_000, 400_000, 600_000):
+        ny = max(2, int(round(math.sqrt(cells / 20.0))))
+        nx = int(round(cells / (2.0 * ny)))
+        w = W.dam_break_1d(nx, ny, 10.0, 1.0, 1.0, 0.5, x_dam=5.0)
+        mesh = swe.Mesh.from_workload(w, "morton")
+        area = mesh.export()["area"][np.argsort(mesh.export()["perm"])]
+        cx, _ = w.centroids()
+        runs = [("hllc", "euler", 0.9), ("waf", "euler", 0.9)]
+        for s in ("muscl", "muscl_edge"):
+            runs += [(s, "euler", 0.9), (s, "heun", 0.9), (s, "euler", 0.45)]
+        for precision in ("fp32", "fp64"):
+            for scheme, ts, cfl in runs:
+                p = swe.swe_params_default(scheme, precision, time_scheme=ts)
+                st = swe.State.from_workload(mesh, p, w)
+                steps = 0
+                while st.time()[0] < 1.0:                      # count the CFL steps to t = 1
+                    st.step(1, cfl)
+                    steps += 1
+                st.close()
+                st = swe.State.from_workload(mesh, p, w)
+                st.step(min(steps, 3), cfl)                   # graphs and caches warm, then restart
+                st.close()
+                st = swe.State.from_workload(mesh, p, w)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                st.step(steps, cfl)
+                e1.record(stream)
+                e1.synchronize()
+                ms = e0.elapsed_time(e1)
+                t = st.time()[0]
+                h = st.get_state()[0]
+                st.close()
+                hex_, _ = stoker(cx, t, 5.0, 1.0, 0.5)
+                l2 = float(np.sqrt(np.sum(area * (h - hex_) ** 2) / np.sum(area * hex_ ** 2)))
+                rows.append({"cells": w.n_cells, "precision": precision, "scheme": scheme, "time_scheme": ts,
+                             "cfl": cfl, "steps": steps, "t": t, "ms": ms, "l2_h": l2})
+                print(f"{w.n_cells:8d} {precision} {scheme:10s} {ts:5s} cfl {cfl:.2f} steps {steps:5d} "
+                      f"t {t:.4f} {ms:8.2f} ms  L2(h) {l2:.3e}", file=sys.stderr)
+        mesh.close()
+    print(json.dumps({"study": "GPU time against L2 error, wet-bed dam break (Sec. 6.3)",
+                      "unit": {"ms": "GPU ms to t = 1 s", "l2_h": "relative L2 of h against Stoker"},
+                      "rows": rows}))
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -551,6 +615,8 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the FP64 comparison and the CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ensemble", action="store_true", help="the 64-scenario batched ensemble instead")
+    ap.add_argument("--time-error", action="store_true",
+                    help="GPU time against L2 error on the paper's dam break, 20k-600k cells, all schemes")
     ap.add_argument("--members", type=int, default=64)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -559,6 +625,8 @@ def main():
         run_reference(args)
     elif args.ensemble:
         run_ensemble(args)
+    elif args.time_error:
+        run_time_error(args)
     else:
         run_gpu(args)
 

@@ -68,6 +68,7 @@ enum { SWE_CFL_GLOBAL = 0, SWE_CFL_LOCAL = 1 };
 typedef struct swe_mesh swe_mesh;
 typedef struct swe_state swe_state;
 typedef struct swe_ensemble swe_ensemble;
+typedef struct swe_partition swe_partition;
 
 /* Solver options.  Fill with swe_params_default, then override. */
 typedef struct {
@@ -234,6 +235,37 @@ int swe_muscl_step_noalloc(int64_t n_cells, const int32_t *nbr, const float *ln,
  * kernels).  Outputs (may be NULL): SWE_KERNEL_*, threads per block, ms per step. */
 int swe_autotune(swe_state *s, const swe_mesh *m, int trial_steps, double cfl, int *kernel, int *block,
                  double *ms_per_step);
+
+/* ---- Partitions and the boundary-first schedule --------------------------- */
+
+/* Not a multi-GPU path (one GPU here): the single-GPU rehearsal of the
+ * paper's sub-domain schedule (Sec. 6.4).  A partition cuts a mesh into
+ * n_parts contiguous ranges of its (Morton) cell order, of equal size to
+ * within one cell, and records per part two halo layers (halo1: cells of
+ * other parts next to the part; halo2: cells of other parts next to halo1,
+ * which the second-order reconstructions of halo1 cells read), its boundary
+ * cells (owned cells that another part holds in a halo) and the rest, its
+ * interior.  Cell ids are in the library's (new) order, see swe_mesh_export.
+ * Errors: SWE_ERR_ARG (n_parts outside 1 .. min(1024, cells)). */
+int swe_partition_create(const swe_mesh *m, int n_parts, swe_partition **out);
+int swe_partition_destroy(swe_partition *p);
+/* Part `part`: owned cells [owned_begin, owned_end) and the list sizes. */
+int swe_partition_info(const swe_partition *p, int part, int64_t *owned_begin, int64_t *owned_end,
+                       int64_t *n_halo1, int64_t *n_halo2, int64_t *n_boundary);
+/* The sorted cell lists of part `part` (caller-allocated, sized by
+ * swe_partition_info; any pointer may be NULL). */
+int swe_partition_export(const swe_partition *p, int part, int32_t *halo1, int32_t *halo2, int32_t *boundary);
+/* Step the state with the boundary-first schedule of a partition of its mesh
+ * (NULL: the plain schedule): every step updates all parts' boundary cells
+ * first, then packs every part's halo (halo1 then halo2, from the new state)
+ * into exchange buffers on a second stream while it updates the interior
+ * cells.  The results are those of the plain schedule, bit for bit.  Needs
+ * the split kernels and Euler steps (SWE_ERR_ARG otherwise); the partition
+ * may be destroyed afterwards. */
+int swe_set_partition(swe_state *s, const swe_partition *p);
+/* The exchange buffer of part `part` after the last step: the state of its
+ * halo1 then halo2 cells, as FP64 host arrays (synchronises). */
+int swe_halo_get(swe_state *s, int part, double *h, double *hu, double *hv);
 
 /* ---- Ensemble ---------------------------------------------------------- */
 

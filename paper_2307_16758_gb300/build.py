@@ -26,6 +26,7 @@ SOURCES = [
     ("swe_ensemble.cu", ["-Xptxas", "-v"] if os.environ.get("SWE_PTXAS_VERBOSE") else []),
     ("swe_api.cpp", []),
     ("swe_tiles.cpp", []),
+    ("swe_partition.cpp", []),
     ("swe_mesh.cpp", ["-Xcompiler", "-ffp-contract=off"]),
 ]
 

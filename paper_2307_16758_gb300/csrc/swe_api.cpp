@@ -14,6 +14,7 @@
 
 #include "swe_dev.h"
 #include "swe_mesh.h"
+#include "swe_partition.h"
 #include "swe_tiles.h"
 
 int swe_mesh_build_host(const double *xy, int64_t n_nodes, const int32_t *tri, int64_t n,
@@ -89,6 +90,14 @@ template <typename T> struct StateT {
     // fused tile kernel
     bool fused = false;
     FusedArgs fa{};
+    // boundary-first schedule (swe_set_partition)
+    bool sched = false;
+    int32_t *d_bnd = nullptr, *d_int = nullptr, *d_recv = nullptr;
+    int64_t n_bnd = 0, n_int = 0, n_recv = 0;
+    std::vector<int64_t> recv_ptr;
+    T *halo_buf = nullptr;
+    cudaStream_t halo_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // CUDA graphs of kGraphSteps CFL steps, keyed by (steps launched mod 6, cfl):
     // the launch pattern (ping-pong buffer, CFL slot ring) repeats every 6 steps
     static constexpr int kGraphSteps = 24;
@@ -110,6 +119,9 @@ template <typename T> struct StateT {
     {
         for (auto &g : graphs) cudaGraphExecDestroy(g.second);
         if (cap_stream) cudaStreamDestroy(cap_stream);
+        if (halo_stream) { cudaStreamSynchronize(halo_stream); cudaStreamDestroy(halo_stream); }
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
         for (auto &e : ev_used) { cudaEventDestroy(std::get<1>(e)); cudaEventDestroy(std::get<2>(e)); }
         for (auto e : ev_pool) cudaEventDestroy(e);
         for (auto &b : mem.blocks) dev_free(b.first, stream);
@@ -157,6 +169,10 @@ template <typename T> struct StateT {
     // (building the tiling from the mesh); allocates what that kernel needs.
     int configure(bool want_fused, int block, const swe_mesh *m)
     {
+        if (want_fused && sched) {
+            swe_set_error("the boundary-first schedule runs the split kernels (clear the partition first)");
+            return SWE_ERR_ARG;
+        }
         const int lim = want_fused ? fused_max_threads<T>(p.scheme) : split_max_threads<T>(p.scheme);
         if (lim <= 0) { swe_set_error("cannot query the kernels (no usable GPU?)"); return SWE_ERR_CUDA; }
         if (block <= 0 || block % 32 || block > lim) {
@@ -308,7 +324,74 @@ template <typename T> struct StateT {
             cudaError_t e = traced(SWE_K_PREP, [&] { return launch_prep<T>(p.scheme, a, F, U, bl, stream); });
             if (e != cudaSuccess) return e;
         }
-        return traced(SWE_K_FLUX, [&] { return launch_flux<T>(p.scheme, a, bl, stream); });
+        if (!sched) return traced(SWE_K_FLUX, [&] { return launch_flux<T>(p.scheme, a, bl, stream); });
+        // boundary-first schedule (Sec. 6.4): first the cells that other parts
+        // hold in their halos, then, while their new state is packed into the
+        // halo buffers on a second stream, the interior
+        StepArgs<T> b = a;
+        b.cells = d_bnd; b.n_list = (int)n_bnd; b.no_advance = n_int > 0;
+        cudaError_t e = traced(SWE_K_FLUX, [&] { return launch_flux_list<T>(p.scheme, b, bl, stream); });
+        if (e == cudaSuccess) e = cudaEventRecord(ev_fork, stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(halo_stream, ev_fork, 0);
+        if (e == cudaSuccess) e = launch_pack_halo<T>(n_recv, d_recv, a.ho, a.huo, a.hvo, halo_buf, halo_stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_join, halo_stream);
+        StepArgs<T> c = a;
+        c.cells = d_int; c.n_list = (int)n_int; c.no_advance = 0;
+        if (e == cudaSuccess) e = traced(SWE_K_FLUX, [&] { return launch_flux_list<T>(p.scheme, c, bl, stream); });
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, ev_join, 0);
+        return e;
+    }
+
+    // Boundary-first schedule over a partition of the mesh (NULL: plain).
+    int set_partition(const swe_partition *part)
+    {
+        CK(cudaStreamSynchronize(stream));
+        clear_graphs();
+        for (void *q : {(void *)d_bnd, (void *)d_int, (void *)d_recv, (void *)halo_buf}) release(q);
+        d_bnd = d_int = d_recv = nullptr;
+        halo_buf = nullptr;
+        sched = false;
+        recv_ptr.clear();
+        if (!part) return SWE_OK;
+        if (part->n != n) { swe_set_error("swe_set_partition: the partition is of another mesh"); return SWE_ERR_ARG; }
+        if (fused || p.time_scheme != SWE_EULER) {
+            swe_set_error("swe_set_partition: the boundary-first schedule runs the split kernels with Euler steps");
+            return SWE_ERR_ARG;
+        }
+        n_bnd = (int64_t)part->boundary_all.size();
+        n_int = (int64_t)part->interior_all.size();
+        n_recv = (int64_t)part->recv_cell.size();
+        d_bnd = alloc<int32_t>(std::max<int64_t>(n_bnd, 1));
+        d_int = alloc<int32_t>(std::max<int64_t>(n_int, 1));
+        d_recv = alloc<int32_t>(std::max<int64_t>(n_recv, 1));
+        halo_buf = alloc<T>(std::max<int64_t>(3 * n_recv, 1));
+        if (!d_bnd || !d_int || !d_recv || !halo_buf) { swe_set_error("device allocation failed"); return SWE_ERR_NOMEM; }
+        CK(cudaMemcpy(d_bnd, part->boundary_all.data(), sizeof(int32_t) * n_bnd, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(d_int, part->interior_all.data(), sizeof(int32_t) * n_int, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(d_recv, part->recv_cell.data(), sizeof(int32_t) * n_recv, cudaMemcpyHostToDevice));
+        CK(cudaMemset(halo_buf, 0, sizeof(T) * std::max<int64_t>(3 * n_recv, 1)));
+        if (!halo_stream) CK(cudaStreamCreateWithFlags(&halo_stream, cudaStreamNonBlocking));
+        if (!ev_fork) CK(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+        if (!ev_join) CK(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
+        recv_ptr = part->recv_ptr;
+        sched = true;
+        return SWE_OK;
+    }
+
+    // The packed halo of part q after the last step, as FP64 host arrays.
+    int halo_get(int q, double *ho, double *huo, double *hvo)
+    {
+        if (!sched || q < 0 || q + 1 >= (int)recv_ptr.size()) { swe_set_error("swe_halo_get: no such part"); return SWE_ERR_ARG; }
+        CK(cudaStreamSynchronize(stream));
+        const int64_t a = recv_ptr[q], len = recv_ptr[q + 1] - a;
+        std::vector<T> tmp((size_t)std::max<int64_t>(len, 1));
+        double *dst[3] = {ho, huo, hvo};
+        for (int f = 0; f < 3; f++) {
+            if (!dst[f] || len == 0) continue;
+            CK(cudaMemcpy(tmp.data(), halo_buf + f * n_recv + a, sizeof(T) * len, cudaMemcpyDeviceToHost));
+            for (int64_t s = 0; s < len; s++) dst[f][s] = (double)tmp[s];
+        }
+        return SWE_OK;
     }
 
     int init_smax()
@@ -411,7 +494,7 @@ template <typename T> std::vector<Candidate> candidates(const StateT<T> &S, cons
     const int ls = split_max_threads<T>(S.p.scheme);
     for (int b : {128, 256, 512})
         if (b <= ls) c.push_back({false, b});
-    if ((S.p.scheme == SWE_SCHEME_MUSCL || S.p.scheme == SWE_SCHEME_WAF) && m) {
+    if ((S.p.scheme == SWE_SCHEME_MUSCL || S.p.scheme == SWE_SCHEME_WAF) && m && !S.sched) {
         const int lf = fused_max_threads<T>(S.p.scheme);
         for (int b : {128, 256})
             if (b <= lf) c.push_back({true, b});
@@ -536,6 +619,10 @@ template <typename T> struct EnsembleT {
     {
         StateT<T> &s0 = *mem[0];
         for (StateT<T> *s : mem) {
+            if (s->sched) {
+                swe_set_error("ensemble members run without a boundary-first schedule");
+                return SWE_ERR_ARG;
+            }
             if (s->p.scheme != s0.p.scheme || s->p.time_scheme != SWE_EULER || s->fused != s0.fused ||
                 s->block() != s0.block() || s->stream != s0.stream || (s->k % 6) != (s0.k % 6)) {
                 swe_set_error("ensemble members need the same scheme, Euler steps, kernel, block, stream and step phase");
@@ -1153,6 +1240,65 @@ int swe_autotune(swe_state *s, const swe_mesh *m, int trial_steps, double cfl, i
         if (ms_per_step) *ms_per_step = ms;
     }
     return rc;
+}
+
+// ---- partitions and the boundary-first schedule ---------------------------
+
+int swe_partition_create(const swe_mesh *m, int n_parts, swe_partition **out)
+{
+    if (out) *out = nullptr;
+    if (!m || !out || n_parts < 1) {
+        swe_set_error("swe_partition_create: bad argument");
+        return SWE_ERR_ARG;
+    }
+    auto *p = new (std::nothrow) swe_partition();
+    if (!p) { swe_set_error("host allocation failed"); return SWE_ERR_NOMEM; }
+    if (swe_partition_build(*m, n_parts, *p) != 0) {
+        delete p;
+        swe_set_error("swe_partition_create: the part count must be within 1 .. min(1024, cells)");
+        return SWE_ERR_ARG;
+    }
+    *out = p;
+    return SWE_OK;
+}
+
+int swe_partition_destroy(swe_partition *p)
+{
+    delete p;
+    return SWE_OK;
+}
+
+int swe_partition_info(const swe_partition *p, int part, int64_t *owned_begin, int64_t *owned_end,
+                       int64_t *n_halo1, int64_t *n_halo2, int64_t *n_boundary)
+{
+    if (!p || part < 0 || part >= p->n_parts) { swe_set_error("swe_partition_info: bad argument"); return SWE_ERR_ARG; }
+    if (owned_begin) *owned_begin = p->start[part];
+    if (owned_end) *owned_end = p->start[part + 1];
+    if (n_halo1) *n_halo1 = (int64_t)p->halo1[part].size();
+    if (n_halo2) *n_halo2 = (int64_t)p->halo2[part].size();
+    if (n_boundary) *n_boundary = (int64_t)p->boundary[part].size();
+    return SWE_OK;
+}
+
+int swe_partition_export(const swe_partition *p, int part, int32_t *halo1, int32_t *halo2, int32_t *boundary)
+{
+    if (!p || part < 0 || part >= p->n_parts) { swe_set_error("swe_partition_export: bad argument"); return SWE_ERR_ARG; }
+    if (halo1) std::copy(p->halo1[part].begin(), p->halo1[part].end(), halo1);
+    if (halo2) std::copy(p->halo2[part].begin(), p->halo2[part].end(), halo2);
+    if (boundary) std::copy(p->boundary[part].begin(), p->boundary[part].end(), boundary);
+    return SWE_OK;
+}
+
+int swe_set_partition(swe_state *s, const swe_partition *part)
+{
+    if (!s) { swe_set_error("swe_set_partition: bad argument"); return SWE_ERR_ARG; }
+    return DISPATCH(s, S.set_partition(part));
+}
+
+int swe_halo_get(swe_state *s, int part, double *h, double *hu, double *hv)
+{
+    if (!s) { swe_set_error("swe_halo_get: bad argument"); return SWE_ERR_ARG; }
+    return DISPATCH(s, S.halo_get(part, h, hu, hv));
 }
 
 }  // extern "C"

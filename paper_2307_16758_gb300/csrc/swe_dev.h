@@ -59,6 +59,9 @@ template <typename T> struct StepArgs {
     int cfl_local;              // 1: the published wave speed is s_i / r_i (local CFL form)
     T g, h_eps, r_eps;
     T beta;                     // MUSCL_EDGE slope-limiter parameter
+    const int32_t *cells;       // boundary-first schedule: the flux launch covers these cells
+    int n_list;                 //   (n_list of them) instead of 0..n-1
+    int no_advance;             // 1: not the step's last flux launch (time is advanced by the last)
     int waf_limiter;
     T qlen[SWE_MAX_GROUPS];     // inflow discharge per unit length [m^2/s]
     T level[SWE_MAX_GROUPS];    // fixed free-surface levels [m]
@@ -118,6 +121,13 @@ cudaError_t launch_fused(int scheme, const StepArgs<T> &a, const FusedArgs &f, c
 template <typename T> size_t fused_smem_bytes(int scheme, int block);
 template <typename T> int fused_max_threads(int scheme);     // launch limit of the fused kernel (registers)
 template <typename T> cudaError_t fused_prepare(int scheme, int block);   // shared-memory attribute, once
+
+// Boundary-first schedule: flux over a list of cells (a.cells, a.n_list), and
+// the halo of every part packed (SoA, [3][n]) from the new state.
+template <typename T> cudaError_t launch_flux_list(int scheme, const StepArgs<T> &a, int block, cudaStream_t s);
+template <typename T>
+cudaError_t launch_pack_halo(int64_t n, const int32_t *cells, const T *h, const T *hu, const T *hv, T *buf,
+                             cudaStream_t s);
 template <typename T> int split_max_threads(int scheme);     // launch limit of the split kernels
 
 template <typename T>

@@ -70,6 +70,24 @@ __global__ void __maxnreg__((flux_maxnreg<T, SCHEME>())) k_flux(StepArgs<T> a)
     flux_block<T, SCHEME>(a, blockIdx.x);
 }
 
+template <typename T, int SCHEME>
+__global__ void __maxnreg__((flux_maxnreg<T, SCHEME>())) k_flux_list(StepArgs<T> a)
+{
+    flux_block<T, SCHEME, true>(a, blockIdx.x);
+}
+
+// Halo of the boundary-first schedule: the new state of the listed cells,
+// packed as [h..., hu..., hv...] (what each part would receive).
+template <typename T>
+__global__ void k_pack_halo(int64_t n, const int32_t *cells, const T *h, const T *hu, const T *hv, T *buf)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < n) {
+        const int32_t c = cells[s];
+        buf[s] = h[c]; buf[n + s] = hu[c]; buf[2 * n + s] = hv[c];
+    }
+}
+
 // Wave speed of the current state into slot `slot` (CFL rule of Sec. 6.1).
 template <typename T>
 __global__ void k_smax(StepArgs<T> a, int slot)
@@ -241,6 +259,29 @@ cudaError_t launch_flux(int scheme, const StepArgs<T> &a, int block, cudaStream_
 }
 
 template <typename T>
+cudaError_t launch_flux_list(int scheme, const StepArgs<T> &a, int block, cudaStream_t s)
+{
+    if (a.n_list <= 0) return cudaSuccess;
+    const unsigned grid = grid_for(a.n_list, block);
+    if (scheme == SWE_SCHEME_MUSCL || scheme == SWE_SCHEME_MUSCL_EDGE)
+        k_flux_list<T, SWE_SCHEME_MUSCL><<<grid, block, 0, s>>>(a);
+    else if (scheme == SWE_SCHEME_WAF)
+        k_flux_list<T, SWE_SCHEME_WAF><<<grid, block, 0, s>>>(a);
+    else
+        k_flux_list<T, SWE_SCHEME_HLLC><<<grid, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_pack_halo(int64_t n, const int32_t *cells, const T *h, const T *hu, const T *hv, T *buf,
+                             cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_pack_halo<T><<<grid_for(n, 256), 256, 0, s>>>(n, cells, h, hu, hv, buf);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_smax(const StepArgs<T> &a, int slot, int block, cudaStream_t s)
 {
     k_smax<T><<<grid_for(a.m.n, block), block, 0, s>>>(a, slot);
@@ -290,6 +331,9 @@ cudaError_t launch_convert(int64_t n, const double *src, T *dst, cudaStream_t s)
 #define SWE_INSTANTIATE(T)                                                                                 \
     template cudaError_t launch_prep<T>(int, const StepArgs<T> &, Vec4<T> *, Vec4<T> *, int, cudaStream_t); \
     template cudaError_t launch_flux<T>(int, const StepArgs<T> &, int, cudaStream_t);                      \
+    template cudaError_t launch_flux_list<T>(int, const StepArgs<T> &, int, cudaStream_t);                 \
+    template cudaError_t launch_pack_halo<T>(int64_t, const int32_t *, const T *, const T *, const T *, T *, \
+                                             cudaStream_t);                                                \
     template cudaError_t launch_smax<T>(const StepArgs<T> &, int, int, cudaStream_t);                      \
     template cudaError_t launch_heun_avg<T>(const StepArgs<T> &, const T *, const T *, const T *, int,     \
                                             cudaStream_t);                                                 \

@@ -198,15 +198,18 @@ template <typename T> struct GlobalSrc {
 // Flux kernel body for one block of cells: each cell evaluates its three
 // edges (hydrostatic reconstruction, canonical Riemann flux), adds the
 // contributions in edge order and updates.
-template <typename T, int SCHEME>
+// With LIST, thread t of the launch updates cell a.cells[t] (boundary-first
+// schedule); otherwise cell t.
+template <typename T, int SCHEME, bool LIST = false>
 __device__ __forceinline__ void flux_block(const StepArgs<T> &a, int block_index)
 {
-    const int i = block_index * blockDim.x + threadIdx.x;
+    const int t = block_index * blockDim.x + threadIdx.x;
+    const int i = LIST ? (t < a.n_list ? a.cells[t] : -1) : t;
     bool dry;
     const T dt = block_dt(a, &dry);
     CellOut<T> o;
     o.smax = T(0); o.clip = T(0); o.bsum = T(0);
-    if (i < a.m.n) {
+    if (LIST ? i >= 0 : i < a.m.n) {
         Nb nb[3];
         Vec2<T> ln[3], dd[3];
 #pragma unroll
@@ -221,7 +224,7 @@ __device__ __forceinline__ void flux_block(const StepArgs<T> &a, int block_index
         a.ho[i] = o.h; a.huo[i] = o.hu; a.hvo[i] = o.hv;
         if (!(dfinite(o.h) && dfinite(o.hu) && dfinite(o.hv))) atomicOr(&a.sc->status, ST_NONFINITE);
     }
-    step_epilogue<T>(a, dt, dry, o.smax, o.clip, o.bsum, block_index == 0);
+    step_epilogue<T>(a, dt, dry, o.smax, o.clip, o.bsum, block_index == 0 && !(LIST && a.no_advance));
 }
 
 }  // namespace swe_dev

@@ -38,6 +38,8 @@ EXPORTED = [
     "swe_state_info", "swe_ensemble_create", "swe_ensemble_destroy", "swe_ensemble_step",
     "swe_ensemble_sync", "swe_profile_begin", "swe_profile_end", "swe_dt_history",
     "swe_muscl_step_noalloc", "swe_autotune", "swe_ensemble_autotune",
+    "swe_partition_create", "swe_partition_destroy", "swe_partition_info", "swe_partition_export",
+    "swe_set_partition", "swe_halo_get",
 ]
 NOALLOC_MAX_CELLS = 262144
 KERNEL_KINDS = ["prep", "flux", "heun_avg", "smax", "fused", "ensemble", "k6", "k7"]
@@ -105,6 +107,12 @@ def load_library(path: str = LIB_PATH, use_torch_allocator: bool = True):
     lib.swe_autotune.argtypes = [vp, vp, i32, dp, C.POINTER(i32), C.POINTER(i32), C.POINTER(dp)]
     lib.swe_ensemble_autotune.argtypes = [vp, C.POINTER(vp), i32, dp, C.POINTER(i32), C.POINTER(i32), C.POINTER(dp)]
     lib.swe_muscl_step_noalloc.argtypes = [i64] + [vp] * 10 + [dp, C.POINTER(Params), vp, i32, vp, i32, vp]
+    lib.swe_partition_create.argtypes = [vp, i32, C.POINTER(vp)]
+    lib.swe_partition_destroy.argtypes = [vp]
+    lib.swe_partition_info.argtypes = [vp, i32] + [C.POINTER(i64)] * 5
+    lib.swe_partition_export.argtypes = [vp, i32, vp, vp, vp]
+    lib.swe_set_partition.argtypes = [vp, vp]
+    lib.swe_halo_get.argtypes = [vp, i32, vp, vp, vp]
     if use_torch_allocator:
         import torch
 
@@ -329,6 +337,39 @@ def swe_ensemble_sync(e):
 
 # ---- convenience wrappers ---------------------------------------------------
 
+def swe_partition_create(mesh, n_parts):
+    out = C.c_void_p()
+    _check(load_library().swe_partition_create(mesh, int(n_parts), C.byref(out)))
+    return out
+
+
+def swe_partition_destroy(p):
+    load_library().swe_partition_destroy(p)
+
+
+def swe_partition_info(p, part):
+    v = [C.c_int64() for _ in range(5)]
+    _check(load_library().swe_partition_info(p, int(part), *[C.byref(x) for x in v]))
+    return tuple(x.value for x in v)        # owned_begin, owned_end, n_halo1, n_halo2, n_boundary
+
+
+def swe_partition_export(p, part):
+    _, _, n1, n2, nb = swe_partition_info(p, part)
+    h1, h2, b = (np.empty(max(k, 1), np.int32) for k in (n1, n2, nb))
+    _check(load_library().swe_partition_export(p, int(part), _p(h1), _p(h2), _p(b)))
+    return h1[:n1], h2[:n2], b[:nb]
+
+
+def swe_set_partition(s, p):
+    _check(load_library().swe_set_partition(s, p))
+
+
+def swe_halo_get(s, part, n):
+    h, hu, hv = np.empty(max(n, 1)), np.empty(max(n, 1)), np.empty(max(n, 1))
+    _check(load_library().swe_halo_get(s, int(part), _p(h), _p(hu), _p(hv)))
+    return h[:n], hu[:n], hv[:n]
+
+
 class Mesh:
     """Owning wrapper of a swe_mesh handle."""
 
@@ -399,12 +440,44 @@ class State:
     def profile_end(self):
         return swe_profile_end(self.handle)
 
+    def set_partition(self, partition):
+        swe_set_partition(self.handle, partition.handle if partition is not None else None)
+
+    def halo(self, partition, part):
+        _, _, n1, n2, _ = partition.info(part)
+        return swe_halo_get(self.handle, part, n1 + n2)
+
     def autotune(self, mesh=None, trial_steps=8, cfl=0.9):
         return swe_autotune(self.handle, mesh.handle if mesh is not None else None, trial_steps, cfl)
 
     def close(self):
         if self.handle:
             swe_state_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Partition:
+    """Owning wrapper of a swe_partition handle (sub-domains with two halo layers)."""
+
+    def __init__(self, mesh: "Mesh", n_parts: int):
+        self.n_parts = int(n_parts)
+        self.handle = swe_partition_create(mesh.handle, n_parts)
+
+    def info(self, part):
+        return swe_partition_info(self.handle, part)
+
+    def export(self, part):
+        return swe_partition_export(self.handle, part)
+
+    def close(self):
+        if self.handle:
+            swe_partition_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -55,6 +55,14 @@
  *      singular.  u = hu/h if h > h_eps else 0.  Depth below 0 after the
  *      update is set to 0 and the mass that adds is recorded; momentum is
  *      zeroed where h <= h_eps.
+ *  R16 Second-order hydrostatic reconstruction (the paper's future work,
+ *      Sec. 7; scheme 1 with hr_order 2): h is reconstructed like eta (LSQ +
+ *      Barth-Jespersen, zero gradient next to a dry cell), the bed at a face
+ *      is z_f = z_i + (grad eta - grad h).(m_k - c_i) (a linear bed in the
+ *      cell), the Riemann problem takes z_f* = max of the two face beds, and
+ *      the cell's own pressure term of a face is g/2 (h_f + h_i)(eta_f - eta_i)
+ *      (wet face) -- the first-order correction of R6 plus the centred bed
+ *      source g (h_f + h_i)/2 (z_f - z_i) L n of that face.
  *  R15 The paper's own MUSCL (Sec. 6.2.3, scheme 3): the reconstructed
  *      variables are (eta, u, v), as in R13; x_RL is the edge midpoint and
  *      distances are Euclidean; the upwind value of a side is the mean over
@@ -518,15 +526,18 @@ int om_edge_flux(const om_opts *o, const double *in, const double *waf, double *
 /* Gradients: least squares + Barth-Jespersen (R13)                         */
 /* ------------------------------------------------------------------------ */
 
+/* Limited gradients of (eta, u, v) and, when hq is given (R16), of h as a
+ * fourth quantity: gl[2 s], gl[2 s + 1] for quantity s. */
 static void cell_gradient(const om_mesh *m, const om_opts *o, int64_t i,
                           const double *eta, const double *u, const double *v, const double *h,
-                          double *gl, double *gu)
+                          double *gl, double *gu, const double *hq)
 {
-    for (int q = 0; q < 6; q++) { gl[q] = 0.0; if (gu) gu[q] = 0.0; }
+    const int nq = hq ? 4 : 3;
+    for (int q = 0; q < 2 * nq; q++) { gl[q] = 0.0; if (gu) gu[q] = 0.0; }
     if (h[i] <= o->h_eps) return;
     double Mxx = 0, Mxy = 0, Myy = 0;
-    double b[3][2] = {{0, 0}, {0, 0}, {0, 0}};
-    const double *q[3] = {eta, u, v};
+    double b[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    const double *q[4] = {eta, u, v, hq};
     int cnt = 0;
     for (int k = 0; k < 3; k++) {
         int32_t j = m->nbr[3 * i + k];
@@ -534,7 +545,7 @@ static void cell_gradient(const om_mesh *m, const om_opts *o, int64_t i,
         if (h[j] <= o->h_eps) return;            /* dry neighbour: first order */
         double dx = m->cx[j] - m->cx[i], dy = m->cy[j] - m->cy[i];
         Mxx += dx * dx; Mxy += dx * dy; Myy += dy * dy;
-        for (int s = 0; s < 3; s++) {
+        for (int s = 0; s < nq; s++) {
             double dq = q[s][j] - q[s][i];
             b[s][0] += dx * dq; b[s][1] += dy * dq;
         }
@@ -542,7 +553,7 @@ static void cell_gradient(const om_mesh *m, const om_opts *o, int64_t i,
     }
     double det = Mxx * Myy - Mxy * Mxy, tr = Mxx + Myy;
     if (cnt < 2 || det <= 1e-12 * tr * tr) return;  /* singular: first order */
-    for (int s = 0; s < 3; s++) {
+    for (int s = 0; s < nq; s++) {
         /* Cramer's rule for the 2x2 normal equations */
         double gx = (Myy * b[s][0] - Mxy * b[s][1]) / det;
         double gy = (Mxx * b[s][1] - Mxy * b[s][0]) / det;
@@ -586,7 +597,7 @@ int om_gradients(const om_mesh *m, const om_opts *o, const double *z,
     int64_t n = m->n;
     double *eta = malloc(sizeof(double) * n), *u = malloc(sizeof(double) * n), *v = malloc(sizeof(double) * n);
     primitives(m, o, z, h, hu, hv, eta, u, v);
-    for (int64_t i = 0; i < n; i++) cell_gradient(m, o, i, eta, u, v, h, gl + 6 * i, gu ? gu + 6 * i : NULL);
+    for (int64_t i = 0; i < n; i++) cell_gradient(m, o, i, eta, u, v, h, gl + 6 * i, gu ? gu + 6 * i : NULL, NULL);
     free(eta); free(u); free(v);
     return 0;
 }
@@ -599,16 +610,21 @@ typedef struct {
     double *eta, *u, *v, *grad, *clip, *bflux;
 } work_t;
 
-/* face values (eta, u, v) of cell i at the midpoint of its local edge k */
-static void face_values(const om_mesh *m, const work_t *w, int scheme, int64_t i, int k, double *f)
+/* face values (eta, u, v) of cell i at the midpoint of its local edge k, and
+ * f[3] the bed there: z_i, or with the second-order reconstruction (R16)
+ * z_i + (grad eta - grad h) . (m_k - c_i), the bed that the reconstructed
+ * eta and h imply */
+static void face_values(const om_mesh *m, const om_opts *o, const work_t *w, const double *z, int scheme,
+                        int64_t i, int k, double *f)
 {
-    f[0] = w->eta[i]; f[1] = w->u[i]; f[2] = w->v[i];
+    f[0] = w->eta[i]; f[1] = w->u[i]; f[2] = w->v[i]; f[3] = z[i];
     if (scheme == 1) {
-        const double *gr = w->grad + 6 * i;
+        const double *gr = w->grad + 8 * i;
         double ox = m->mx[3 * i + k], oy = m->my[3 * i + k];
         f[0] += gr[0] * ox + gr[1] * oy;
         f[1] += gr[2] * ox + gr[3] * oy;
         f[2] += gr[4] * ox + gr[5] * oy;
+        if (o->hr_order == 2) f[3] += (gr[0] - gr[6]) * ox + (gr[1] - gr[7]) * oy;
     }
 }
 
@@ -687,6 +703,16 @@ static void paper_edge_states(const om_mesh *m, const om_opts *o, const work_t *
     }
 }
 
+/* R16: the own-side pressure term of a face with the linear bed, g/2 (h_f^2 -
+ * h_i^2) + g (h_f + h_i)/2 (z_f - z_i): the first-order correction plus the
+ * centred bed source of the face, written as g/2 (h_f + h_i)(eta_f - eta_i)
+ * on a wet face (h_f = eta_f - z_f) and g/2 (h_f + h_i)(z_f - eta_i) on a dry
+ * one, so that a lake at rest gives an exact zero.  f = (eta_f, u, v, z_f). */
+static double hyd2(double g, double hf, double hc, const double *f, double eta_c)
+{
+    return 0.5 * g * (hf + hc) * ((hf > 0.0 ? f[0] : f[3]) - eta_c);
+}
+
 static void euler_stage(const om_mesh *m, const om_opts *o, work_t *w,
                         const double *z, const double *nman, const double *qlen, const double *level,
                         const double *h, const double *hu, const double *hv,
@@ -698,7 +724,8 @@ static void euler_stage(const om_mesh *m, const om_opts *o, work_t *w,
     primitives(m, o, z, h, hu, hv, w->eta, w->u, w->v);
     if (scheme == 1) {
 #pragma omp parallel for schedule(static)
-        for (int64_t i = 0; i < n; i++) cell_gradient(m, o, i, w->eta, w->u, w->v, h, w->grad + 6 * i, NULL);
+        for (int64_t i = 0; i < n; i++)
+            cell_gradient(m, o, i, w->eta, w->u, w->v, h, w->grad + 8 * i, NULL, o->hr_order == 2 ? h : NULL);
     }
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; i++) {
@@ -708,9 +735,9 @@ static void euler_stage(const om_mesh *m, const om_opts *o, work_t *w,
             double L = m->len[3 * i + k];
             double nx = m->lnx[3 * i + k] / L, ny = m->lny[3 * i + k] / L;
             int32_t j = m->nbr[3 * i + k];
-            double fi[3];
-            face_values(m, w, scheme, i, k, fi);
-            double hfi = fi[0] - z[i];
+            double fi[4];
+            face_values(m, o, w, z, scheme, i, k, fi);
+            double hfi = fi[0] - fi[3];
             if (hfi < 0.0) hfi = 0.0;
             double M, P, T, sgn;
             if (j >= 0) {
@@ -719,20 +746,24 @@ static void euler_stage(const om_mesh *m, const om_opts *o, work_t *w,
                 int64_t a = i < j ? i : j, b = i < j ? j : i;
                 int ka = i < j ? k : kj, kb = i < j ? kj : k;
                 double cnx = i < j ? nx : -nx, cny = i < j ? ny : -ny;
-                double fa[3], fb[3];
+                double fa[4], fb[4];
                 if (scheme == 3) {
                     paper_edge_states(m, o, w, h, a, ka, b, kb, fa, fb);
+                    fa[3] = z[a]; fb[3] = z[b];
                 } else {
-                    face_values(m, w, scheme, a, ka, fa);
-                    face_values(m, w, scheme, b, kb, fb);
+                    face_values(m, o, w, z, scheme, a, ka, fa);
+                    face_values(m, o, w, z, scheme, b, kb, fb);
                 }
-                double hfa = fa[0] - z[a]; if (hfa < 0.0) hfa = 0.0;
-                double hfb = fb[0] - z[b]; if (hfb < 0.0) hfb = 0.0;
-                double zf = z[a] > z[b] ? z[a] : z[b];            /* R6 */
+                double hfa = fa[0] - fa[3]; if (hfa < 0.0) hfa = 0.0;
+                double hfb = fb[0] - fb[3]; if (hfb < 0.0) hfb = 0.0;
+                double zf = fa[3] > fb[3] ? fa[3] : fb[3];        /* R6 (face beds: R16) */
                 double hsa = fa[0] - zf; if (hsa < 0.0) hsa = 0.0;
                 double hsb = fb[0] - zf; if (hsb < 0.0) hsb = 0.0;
-                double in[10] = {hfa, hsa, h[a], fa[1] * cnx + fa[2] * cny, -fa[1] * cny + fa[2] * cnx,
-                                 hfb, hsb, h[b], fb[1] * cnx + fb[2] * cny, -fb[1] * cny + fb[2] * cnx};
+                /* R16: the cell-centre pressure term is replaced by hyd2 below (so
+                 * edge_flux gets hcell = hface and adds nothing) */
+                const int hr2 = scheme == 1 && o->hr_order == 2;
+                double in[10] = {hfa, hsa, hr2 ? hfa : h[a], fa[1] * cnx + fa[2] * cny, -fa[1] * cny + fa[2] * cnx,
+                                 hfb, hsb, hr2 ? hfb : h[b], fb[1] * cnx + fb[2] * cny, -fb[1] * cny + fb[2] * cnx};
                 double out[4];
                 if (scheme == 2) {
                     double hma, uma, vma, hmb, umb, vmb;
@@ -747,6 +778,7 @@ static void euler_stage(const om_mesh *m, const om_opts *o, work_t *w,
                 }
                 M = out[0]; T = out[3];
                 P = i < j ? out[1] : out[2];
+                if (hr2) P += hyd2(g, hfi, h[i], fi, w->eta[i]);
                 sgn = i < j ? 1.0 : -1.0;
                 /* sgn * (M, P n_c + T t_c) with n_c = sgn * n  ==  (sgn M, P n + T t) */
                 R[0] += L * sgn * M;
@@ -757,7 +789,8 @@ static void euler_stage(const om_mesh *m, const om_opts *o, work_t *w,
             /* boundary edge: cell i is the left state, normal outward (Sec. 6.1) */
             int tag = m->btag[3 * i + k], type = tag & 3, grp = tag >> 2;
             double un = fi[1] * nx + fi[2] * ny, vt = -fi[1] * ny + fi[2] * nx;
-            double hyd = 0.5 * g * (hfi - h[i]) * (hfi + h[i]);
+            double hyd = (scheme == 1 && o->hr_order == 2) ? hyd2(g, hfi, h[i], fi, w->eta[i])
+                                                           : 0.5 * g * (hfi - h[i]) * (hfi + h[i]);
             if (type == BC_WALL) {
                 M = 0.0; P = hyd; T = 0.0;
             } else if (type == BC_OPEN) {
@@ -766,12 +799,13 @@ static void euler_stage(const om_mesh *m, const om_opts *o, work_t *w,
                 double q = qlen[grp];
                 M = -q; P = (hfi > o->h_eps ? q * q / hfi : 0.0) + hyd; T = 0.0;
             } else {
-                double hg = level[grp] - z[i];
+                double hg = level[grp] - fi[3];
                 if (hg < 0.0) hg = 0.0;
-                double in[10] = {hfi, hfi, h[i], un, vt, hg, hg, hg, un, vt};
+                const int hr2 = scheme == 1 && o->hr_order == 2;
+                double in[10] = {hfi, hfi, hr2 ? hfi : h[i], un, vt, hg, hg, hg, un, vt};
                 double out[4];
                 edge_flux(o, 0, in, NULL, out);
-                M = out[0]; P = out[1]; T = out[3];
+                M = out[0]; P = out[1] + (hr2 ? hyd : 0.0); T = out[3];
             }
             R[0] += L * M;
             R[1] += L * (P * nx - T * ny);
@@ -846,7 +880,7 @@ int om_run(const om_mesh *m, const om_opts *o,
 
     work_t w;
     w.eta = malloc(sizeof(double) * n); w.u = malloc(sizeof(double) * n); w.v = malloc(sizeof(double) * n);
-    w.grad = malloc(sizeof(double) * 6 * n);
+    w.grad = malloc(sizeof(double) * 8 * n);
     w.clip = malloc(sizeof(double) * n); w.bflux = malloc(sizeof(double) * n);
     double *h1 = malloc(sizeof(double) * n), *hu1 = malloc(sizeof(double) * n), *hv1 = malloc(sizeof(double) * n);
     double *h2 = NULL, *hu2 = NULL, *hv2 = NULL;

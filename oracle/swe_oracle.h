@@ -62,6 +62,8 @@ typedef struct {
     int cfl_local;     /* 0: dt = CFL min_i r_i / max_wet s_i (Sec. 6.1, global form);
                           1: dt = CFL min over wet cells of r_i / s_i (per-cell form) */
     double beta;       /* scheme 3: limiter parameter (1 MINBEE, 2 SUPERBEE) */
+    int hr_order;      /* scheme 1: 1 hydrostatic reconstruction on the cell bed (R6),
+                          2 second order with a linear bed in each cell (R16) */
 } om_opts;
 
 /* Advance n_steps.  h,hu,hv are updated in place.  dt_given (length n_steps)

@@ -434,6 +434,71 @@ def test_paper_muscl_is_first_order_next_to_dry_cells_and_at_rest():
     assert np.array_equal(h, w.h) and not hu.any() and not hv.any()
 
 
+def _bump_over_bed(n, amp_z=0.6, sig_z=1.5):
+    """Smooth free-surface hump over a smooth (unquantised) Gaussian bed, at rest."""
+    w = W.gaussian_hump(n, l=10.0, amp=0.05, sigma=1.2)
+    m = _mesh(w)
+    cx, cy = m.arrays["cx"], m.arrays["cy"]
+    z = amp_z * np.exp(-((cx - 5) ** 2 + (cy - 5) ** 2) / (2 * sig_z ** 2))
+    eta = 1.0 + 0.05 * np.exp(-((cx - 5) ** 2 + (cy - 5) ** 2) / (2 * 1.2 ** 2))
+    return w, m, z, eta - z
+
+
+def test_second_order_hydrostatic_reconstruction_restores_the_order_over_a_bed():
+    """R16: over a steep smooth bed the cell-bed reconstruction (R6) leaves MUSCL first order;
+    with the linear bed of the second-order reconstruction it is second order again."""
+    order = {}
+    for hr in (1, 2):
+        sols = {}
+        for n in (16, 32, 64, 128):
+            w, m, z, h = _bump_over_bed(n)
+            steps = n // 2
+            out = oracle.run(m, oracle.opts("muscl", time_scheme="heun", hr_order=hr), z, np.zeros(m.n), h,
+                             0 * h, 0 * h, steps, dt=np.full(steps, 0.4 / steps))
+            sols[n] = out[0] + z
+        d2 = np.abs(sols[32] - _restrict(sols[64], 32)).mean()
+        d3 = np.abs(sols[64] - _restrict(sols[128], 64)).mean()
+        order[hr] = math.log2(d2 / d3)
+    assert order[1] < 1.2 and order[2] > 1.8, order
+
+
+@pytest.mark.parametrize("bc", ["wall", "level"])
+def test_second_order_hydrostatic_reconstruction_keeps_a_lake_at_rest(bc):
+    w = W.partial_dam_break(nx=40, ny=20, spacing=1.0, n_gauss=20, breach=False, seed=8)
+    if bc == "level":
+        w.bnd_tag = np.full(len(w.bnd_edges), W.tag(W.LEVEL), np.int32)
+        w.level = np.array([2.0])
+    m = _mesh(w)
+    h, hu, hv, *_ = oracle.run(m, oracle.opts("muscl", hr_order=2), w.z, w.nman, w.h, w.hu, w.hv, 300,
+                               level=w.level)
+    assert np.array_equal(h, w.h) and not hu.any() and not hv.any()
+
+
+def test_second_order_hydrostatic_reconstruction_conserves_mass_and_is_the_first_on_a_flat_bed():
+    w = W.partial_dam_break(nx=30, ny=14, spacing=1.0, n_gauss=8, seed=5)
+    m = _mesh(w)
+    h, *_ = oracle.run(m, oracle.opts("muscl", hr_order=2), w.z, w.nman, w.h, w.hu, w.hv, 150)
+    assert abs(m.mass(h) - m.mass(w.h)) <= 1e-13 * m.mass(w.h)      # walls, wet everywhere at the break
+    wf = W.dam_break_1d(60, 6, 10.0, 1.0, 1.0, 0.5, x_dam=5.0)      # flat bed: no bed to reconstruct
+    mf = _mesh(wf)
+    a = oracle.run(mf, oracle.opts("muscl", hr_order=1), wf.z, wf.nman, wf.h, wf.hu, wf.hv, 100)
+    b = oracle.run(mf, oracle.opts("muscl", hr_order=2), wf.z, wf.nman, wf.h, wf.hu, wf.hv, 100)
+    assert np.abs(a[0] - b[0]).max() < 1e-12 and np.abs(a[1] - b[1]).max() < 1e-12
+
+
+def test_second_order_hydrostatic_reconstruction_rotates():
+    w = W.partial_dam_break(nx=24, ny=12, spacing=1.0, n_gauss=8, seed=5)
+    w.hu = 0.1 * w.h
+    m = _mesh(w)
+    rot = np.stack([-w.nodes[:, 1], w.nodes[:, 0]], axis=1)
+    mr = oracle.Mesh(rot, w.tris, w.bnd_edges, w.bnd_tag, w.cut_edges)
+    o = oracle.opts("muscl", hr_order=2)
+    a = oracle.run(m, o, w.z, w.nman, w.h, w.hu, w.hv, 80)
+    b = oracle.run(mr, o, w.z, w.nman, w.h, -w.hv, w.hu, 80)
+    assert np.abs(a[0] - b[0]).max() < 1e-13
+    assert np.abs(a[1] - b[2]).max() < 1e-13 and np.abs(a[2] + b[1]).max() < 1e-13
+
+
 def test_lsq_gradient_exact_for_linear_fields():
     w = W.partial_dam_break(nx=12, ny=8, spacing=1.0, n_gauss=0, seed=3, breach=False)
     m = _mesh(w, cut=False)

@@ -291,7 +291,7 @@ def run_gpu(args):
     w, grid = river_workload(rank, args.scale)
     mesh = swe.Mesh.from_workload(w, "morton")
     n = mesh.n
-    p32 = swe.swe_params_default(args.scheme, "fp32", kernel=args.kernel)
+    p32 = swe.swe_params_default(args.scheme, "fp32", kernel=args.kernel, hr_order=args.hr_order)
     st = swe.State.from_workload(mesh, p32, w)
     part = None
     if args.parts > 1:                       # boundary-first schedule over Morton sub-domains
@@ -334,7 +334,8 @@ def run_gpu(args):
     bytes_launch = algo_bytes(dom, args.scheme, "fp32") * n
     peak, peak_src = measured_peaks()
     achieved = bytes_launch / (dom_ms / 1e3) / 1e9
-    traffic = ncu_traffic(f"{kname}:{dom}:{args.scheme}:fp32", n)
+    skey = args.scheme + (":hr2" if args.hr_order == 2 else "")      # counters key of the kernels
+    traffic = ncu_traffic(f"{kname}:{dom}:{skey}:fp32", n)
     step_ms = ms / args.steps
     step_ideal = step_bytes_ideal(args.scheme, "fp32") * n / (step_ms / 1e3) / 1e9
 
@@ -360,8 +361,9 @@ def run_gpu(args):
         "config": {
             "workload": f"river {grid[0]}x{grid[1]} jittered grid, {n} triangles, "
                         f"{'MUSCL-HLLC' if args.scheme == 'muscl' else 'edge-upwind MUSCL-HLLC'} FP32 bulk "
-                        "(FP64 mass/time), Euler, CFL 0.9, Morton order",
-            "cells": n, "scheme": args.scheme, "precision": "fp32", "time_scheme": "euler", "kernel": kname,
+                        "(FP64 mass/time), Euler, CFL 0.9, Morton order"
+                        + (", second-order hydrostatic reconstruction" if args.hr_order == 2 else ""),
+            "cells": n, "scheme": args.scheme, "hr_order": args.hr_order, "precision": "fp32", "time_scheme": "euler", "kernel": kname,
             "block": block, "device_bytes": dev_bytes,
             "l2": f"inputs larger than L2: {dev_bytes / 1e9:.2f} GB resident per state, no flush needed",
             "parallelism": "replicas" if ws > 1 else "single GPU", "seed": SEED,
@@ -377,7 +379,7 @@ def run_gpu(args):
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
-    iss = {k: issue_roofline(f"{kname}:{k}:{args.scheme}:fp32", n, v[0] / v[1], clocks.get("sm_mhz") or 0.0,
+    iss = {k: issue_roofline(f"{kname}:{k}:{skey}:fp32", n, v[0] / v[1], clocks.get("sm_mhz") or 0.0,
                              torch.cuda.get_device_properties(local).multi_processor_count)
            for k, v in prof.items()}
     if any(iss.values()):
@@ -403,7 +405,7 @@ def fp64_comparison(args, mesh, w, swe, torch):
     """FP64 GPU path: its throughput, and the FP32 error against it at matched time."""
     n = mesh.n
     m_steps = args.fp64_steps
-    p64 = swe.swe_params_default(args.scheme, "fp64", kernel=args.kernel)
+    p64 = swe.swe_params_default(args.scheme, "fp64", kernel=args.kernel, hr_order=args.hr_order)
     s64 = swe.State.from_workload(mesh, p64, w)
     s64.step(3, args.cfl)
     s64.sync()
@@ -419,7 +421,7 @@ def fp64_comparison(args, mesh, w, swe, torch):
     dts = s64.dt_history(m_steps)
     h64, hu64, hv64 = s64.get_state()
     mass64 = s64.mass()
-    p32 = swe.swe_params_default(args.scheme, "fp32", kernel=args.kernel)
+    p32 = swe.swe_params_default(args.scheme, "fp32", kernel=args.kernel, hr_order=args.hr_order)
     p32.h_eps = p64.h_eps         # same algorithm, precision differs only
     p32.r_eps = p64.r_eps
     s32 = swe.State.from_workload(mesh, p32, w)
@@ -617,6 +619,8 @@ def main():
     ap.add_argument("--kernel", default="auto", choices=["auto", "split", "fused"])
     ap.add_argument("--scheme", default="muscl", choices=["muscl", "muscl_edge"],
                     help="MUSCL-HLLC with least-squares gradients (default) or the paper's edge-upwind MUSCL")
+    ap.add_argument("--hr-order", type=int, default=1, choices=[1, 2],
+                    help="hydrostatic reconstruction: 1 (cell bed) or 2 (linear bed; LSQ MUSCL only)")
     ap.add_argument("--fp64-steps", type=int, default=1000)
     ap.add_argument("--scale", type=float, default=1.0, help="fraction of the 13M-cell mesh (testing only)")
     ap.add_argument("--quick", action="store_true", help="skip the FP64 comparison and the CPU baseline")

@@ -83,6 +83,9 @@ typedef struct {
     int block;        /* threads per block (0: default) */
     int cfl_mode;     /* SWE_CFL_GLOBAL (default) or SWE_CFL_LOCAL */
     double muscl_beta; /* SWE_SCHEME_MUSCL_EDGE limiter, 1 (MINBEE) .. 2 (SUPERBEE, default) */
+    int hr_order;     /* hydrostatic reconstruction: 1 on the cell bed (default); 2 (SWE_SCHEME_MUSCL,
+                         split kernels) second order, with the linear bed that the reconstructed
+                         eta and h imply in each cell -- the paper's future work (Sec. 7) */
 } swe_params;
 
 /* Values of the boundary groups (copied at init). */
@@ -97,7 +100,7 @@ const char *swe_last_error(void);
 
 /* Defaults: g = 9.81, h_eps = 1e-6 (FP64) or 1e-4 (FP32),
  * r_eps = 1e-12 (FP64) or 1e-6 (FP32), Euler, SUPERBEE, automatic kernel,
- * global CFL form, muscl_beta = 2. */
+ * global CFL form, muscl_beta = 2, hr_order = 1. */
 int swe_params_default(swe_params *p, int scheme, int precision);
 
 /* Device memory: by default cudaMalloc/cudaFree.  A host program (for example
@@ -273,7 +276,7 @@ int swe_halo_get(swe_state *s, int part, double *h, double *hu, double *hv);
  * split kernels) advances all of them, each with its own CFL time step, its
  * own boundary values and its own time (the batched form of running many
  * scenarios; cf. the paper's one-sub-domain-per-GPU layout, Sec. 6.4).
- * Members must share precision, scheme, Euler time stepping, kernel, block,
+ * Members must share precision, scheme, hr_order, Euler time stepping, kernel, block,
  * stream and step phase (steps taken mod 6; freshly initialised states do).
  * Members stay owned by the caller, must outlive the ensemble, and can be
  * queried (swe_get_state, swe_mass, swe_time) as usual. */

@@ -310,6 +310,7 @@ template <typename T> struct StateT {
         a.cfl_local = p.cfl_mode == SWE_CFL_LOCAL;
         a.g = (T)p.g; a.h_eps = (T)p.h_eps; a.r_eps = (T)p.r_eps;
         a.beta = (T)p.muscl_beta;
+        a.hr2 = p.hr_order == 2;
         a.waf_limiter = p.waf_limiter;
         for (int q = 0; q < SWE_MAX_GROUPS; q++) { a.qlen[q] = qlen[q]; a.level[q] = level[q]; }
         return a;
@@ -494,7 +495,7 @@ template <typename T> std::vector<Candidate> candidates(const StateT<T> &S, cons
     const int ls = split_max_threads<T>(S.p.scheme);
     for (int b : {128, 256, 512})
         if (b <= ls) c.push_back({false, b});
-    if ((S.p.scheme == SWE_SCHEME_MUSCL || S.p.scheme == SWE_SCHEME_WAF) && m && !S.sched) {
+    if ((S.p.scheme == SWE_SCHEME_MUSCL || S.p.scheme == SWE_SCHEME_WAF) && m && !S.sched && S.p.hr_order == 1) {
         const int lf = fused_max_threads<T>(S.p.scheme);
         for (int b : {128, 256})
             if (b <= lf) c.push_back({true, b});
@@ -585,7 +586,7 @@ template <typename T> struct EnsembleT {
 
     cudaError_t launch_one(int phase, cudaStream_t s)
     {
-        return launch_ensemble<T>(scheme, built_fused, d_tab, d_begin, (int)mem.size(), phase, grid, built_block, s);
+        return launch_ensemble<T>(scheme, mem[0]->p.hr_order == 2, built_fused, d_tab, d_begin, (int)mem.size(), phase, grid, built_block, s);
     }
 
     // kGraphSteps batched steps through a cached CUDA graph.
@@ -623,9 +624,10 @@ template <typename T> struct EnsembleT {
                 swe_set_error("ensemble members run without a boundary-first schedule");
                 return SWE_ERR_ARG;
             }
-            if (s->p.scheme != s0.p.scheme || s->p.time_scheme != SWE_EULER || s->fused != s0.fused ||
+            if (s->p.scheme != s0.p.scheme || s->p.hr_order != s0.p.hr_order || s->p.time_scheme != SWE_EULER ||
+                s->fused != s0.fused ||
                 s->block() != s0.block() || s->stream != s0.stream || (s->k % 6) != (s0.k % 6)) {
-                swe_set_error("ensemble members need the same scheme, Euler steps, kernel, block, stream and step phase");
+                swe_set_error("ensemble members need the same scheme and reconstruction order, Euler steps, kernel, block, stream and step phase");
                 return SWE_ERR_ARG;
             }
         }
@@ -767,7 +769,8 @@ bool valid_params(const swe_params *p)
            p->kernel <= 2 && p->block >= 0 && p->block <= 1024 && (p->block % 32) == 0 &&
            (p->cfl_mode == SWE_CFL_GLOBAL || p->cfl_mode == SWE_CFL_LOCAL) &&
            (p->scheme != SWE_SCHEME_MUSCL_EDGE || (p->muscl_beta >= 1.0 && p->muscl_beta <= 2.0)) &&
-           (p->scheme != SWE_SCHEME_MUSCL_EDGE || p->kernel != SWE_KERNEL_FUSED);
+           (p->scheme != SWE_SCHEME_MUSCL_EDGE || p->kernel != SWE_KERNEL_FUSED) &&
+           (p->hr_order == 1 || (p->hr_order == 2 && p->scheme == SWE_SCHEME_MUSCL && p->kernel != SWE_KERNEL_FUSED));
 }
 
 template <typename T>
@@ -875,6 +878,7 @@ int swe_params_default(swe_params *p, int scheme, int precision)
     p->block = 0;
     p->cfl_mode = SWE_CFL_GLOBAL;
     p->muscl_beta = 2.0;
+    p->hr_order = 1;
     return SWE_OK;
 }
 

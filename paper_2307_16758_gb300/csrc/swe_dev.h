@@ -62,6 +62,7 @@ template <typename T> struct StepArgs {
     const int32_t *cells;       // boundary-first schedule: the flux launch covers these cells
     int n_list;                 //   (n_list of them) instead of 0..n-1
     int no_advance;             // 1: not the step's last flux launch (time is advanced by the last)
+    int hr2;                    // 1: second-order hydrostatic reconstruction (linear bed, MUSCL)
     int waf_limiter;
     T qlen[SWE_MAX_GROUPS];     // inflow discharge per unit length [m^2/s]
     T level[SWE_MAX_GROUPS];    // fixed free-surface levels [m]
@@ -131,7 +132,7 @@ cudaError_t launch_pack_halo(int64_t n, const int32_t *cells, const T *h, const 
 template <typename T> int split_max_threads(int scheme);     // launch limit of the split kernels
 
 template <typename T>
-cudaError_t launch_ensemble(int scheme, bool fused, const EnsEntry<T> *tab, const int *begin, int n_mem, int phase,
+cudaError_t launch_ensemble(int scheme, bool hr2, bool fused, const EnsEntry<T> *tab, const int *begin, int n_mem, int phase,
                             int grid, int block, cudaStream_t s);
 template <typename T> cudaError_t ensemble_prepare(int scheme, bool fused, int block);
 

@@ -294,24 +294,30 @@ __device__ __forceinline__ T block_dt(const StepArgs<T> &a, bool *dry)
 // (eta, u, v); qn[k] = neighbour k's (eta, u, v) where has[k]; ok = the cell
 // and all its neighbours are wet; cnt = number of neighbours.  F[k] =
 // (eta, u, v, z) at the midpoint of edge k.
-template <typename T>
-__device__ __forceinline__ void muscl_faces(const T qi[3], T zi, bool ok, int cnt, const T qn[3][3],
+template <typename T, int NQ = 3>
+__device__ __forceinline__ void muscl_faces(const T qi[NQ], T zi, bool ok, int cnt, const T qn[3][NQ],
                                             const bool has[3], const T ox[3], const T oy[3],
                                             const Vec2<T> dd[3], Vec4<T> F[3])
 {
-    T gx[3] = {T(0), T(0), T(0)}, gy[3] = {T(0), T(0), T(0)};
+    // NQ = 3: (eta, u, v).  NQ = 4 adds h (second-order hydrostatic
+    // reconstruction, R16): the face bed is then z_i + (grad eta - grad h).(m_k - c_i).
+    T gx[NQ], gy[NQ];
+#pragma unroll
+    for (int s = 0; s < NQ; s++) { gx[s] = T(0); gy[s] = T(0); }
     // Every product below is either fused explicitly (fma_rn) or rounded on
     // its own (mul_rn), so all kernels that inline this give the same bits.
     if (ok && cnt >= 2) {
         T Mxx = T(0), Mxy = T(0), Myy = T(0);
-        T bx[3] = {T(0), T(0), T(0)}, by[3] = {T(0), T(0), T(0)};
+        T bx[NQ], by[NQ];
+#pragma unroll
+        for (int s = 0; s < NQ; s++) { bx[s] = T(0); by[s] = T(0); }
 #pragma unroll
         for (int k = 0; k < 3; k++) {
             if (!has[k]) continue;
             T dx = dd[k].x, dy = dd[k].y;
             Mxx = fma_rn(dx, dx, Mxx); Mxy = fma_rn(dx, dy, Mxy); Myy = fma_rn(dy, dy, Myy);
 #pragma unroll
-            for (int s = 0; s < 3; s++) {
+            for (int s = 0; s < NQ; s++) {
                 T dq = qn[k][s] - qi[s];
                 bx[s] = fma_rn(dx, dq, bx[s]); by[s] = fma_rn(dy, dq, by[s]);
             }
@@ -319,7 +325,7 @@ __device__ __forceinline__ void muscl_faces(const T qi[3], T zi, bool ok, int cn
         T det = fma_rn(Mxx, Myy, -mul_rn(Mxy, Mxy)), tr = Mxx + Myy;
         if (det > mul_rn(mul_rn(T(1e-12), tr), tr)) {
 #pragma unroll
-            for (int s = 0; s < 3; s++) {
+            for (int s = 0; s < NQ; s++) {
                 T px = ddiv(fma_rn(Myy, bx[s], -mul_rn(Mxy, by[s])), det);
                 T py = ddiv(fma_rn(Mxx, by[s], -mul_rn(Mxy, bx[s])), det);
                 T qmin = qi[s], qmax = qi[s];
@@ -347,7 +353,7 @@ __device__ __forceinline__ void muscl_faces(const T qi[3], T zi, bool ok, int cn
         F[k].x = qi[0] + fma_rn(gx[0], ox[k], mul_rn(gy[0], oy[k]));
         F[k].y = qi[1] + fma_rn(gx[1], ox[k], mul_rn(gy[1], oy[k]));
         F[k].z = qi[2] + fma_rn(gx[2], ox[k], mul_rn(gy[2], oy[k]));
-        F[k].w = zi;
+        F[k].w = NQ == 4 ? zi + fma_rn(gx[0] - gx[NQ - 1], ox[k], mul_rn(gy[0] - gy[NQ - 1], oy[k])) : zi;
     }
 }
 
@@ -415,7 +421,30 @@ __device__ __forceinline__ Contrib<T> contribution(T L, T sM, T P, T Tt, T nx, T
 
 // One side of an edge: the free surface and velocities at the edge midpoint,
 // the cell's bed and its cell-centre depth.
-template <typename T> struct Side { T ef, uf, vf, z, hc; };
+// z is the bed at the face (the cell bed, or with the second-order
+// reconstruction the linear bed at the midpoint); zc is the cell bed.
+template <typename T> struct Side { T ef, uf, vf, z, hc, zc; };
+
+// Flux-template id of the LSQ MUSCL scheme with the second-order hydrostatic
+// reconstruction (R16).  It is not a public scheme value: the flux kernels
+// are instantiated for it so that the first-order path carries no test.
+constexpr int FLUX_MUSCL_HR2 = 0x10 | SWE_SCHEME_MUSCL;
+
+// Schemes whose flux kernel reads reconstructed face values.
+__host__ __device__ constexpr bool face_scheme(int s) { return s == SWE_SCHEME_MUSCL || s == FLUX_MUSCL_HR2; }
+
+// The cell's own pressure term of a face (the hydrostatic correction).  First
+// order (Sec. 6.2.3 HR, R6): g/2 (h_f^2 - h_c^2).  Second-order
+// reconstruction (R16): that plus the centred bed source of the face,
+// g/2 (h_f + h_c)(eta_f - eta_c) on a wet face and g/2 (h_f + h_c)(z_f - eta_c)
+// on a dry one, so that a lake at rest gives an exact zero.
+template <typename T, bool HR2>
+__device__ __forceinline__ T own_pressure(const StepArgs<T> &a, T hf, const Side<T> &s)
+{
+    const T half = T(0.5);
+    if (!HR2) return half * a.g * (hf - s.hc) * (hf + s.hc);
+    return mul_rn(mul_rn(mul_rn(half, a.g), hf + s.hc), (hf > T(0) ? s.ef : s.z) - (s.hc + s.zc));
+}
 
 // Interior edge seen from side i (scaled outward normal (lx, ly) of i):
 // hydrostatic reconstruction, canonical-orientation Riemann flux, and the
@@ -453,12 +482,12 @@ __device__ __forceinline__ void interior_edge(const StepArgs<T> &a, T dt, const 
     }
     const T PA = hsA * unA * unA + fl.DL2, PB = hsB * unB * unB + fl.DR2;
     const T hfi = dmax(si.ef - si.z, T(0));
-    const T Pi = (own_i ? PA : PB) + half * g * (hfi - si.hc) * (hfi + si.hc);
+    const T Pi = (own_i ? PA : PB) + own_pressure<T, SCHEME == FLUX_MUSCL_HR2>(a, hfi, si);
     const T sMi = own_i ? fl.M : -fl.M;
     ci = contribution(L, sMi, Pi, fl.Tt, nx, ny);
     if (cj) {
         const T hfj = dmax(sj.ef - sj.z, T(0));
-        const T Pj = (own_i ? PB : PA) + half * g * (hfj - sj.hc) * (hfj + sj.hc);
+        const T Pj = (own_i ? PB : PA) + own_pressure<T, SCHEME == FLUX_MUSCL_HR2>(a, hfj, sj);
         const T sMj = own_i ? -fl.M : fl.M;
         *cj = contribution(L, sMj, Pj, fl.Tt, -nx, -ny);
     }
@@ -466,7 +495,7 @@ __device__ __forceinline__ void interior_edge(const StepArgs<T> &a, T dt, const 
 
 // Boundary edge of cell i (outward normal, Sec. 6.1): wall, open, inflow,
 // fixed level.  bs receives the mass that leaves, -L*M.
-template <typename T>
+template <typename T, bool HR2 = false>
 __device__ __forceinline__ Contrib<T> boundary_edge(const StepArgs<T> &a, const Side<T> &si, int tag, T lx, T ly,
                                                     T &bs)
 {
@@ -474,7 +503,7 @@ __device__ __forceinline__ Contrib<T> boundary_edge(const StepArgs<T> &a, const 
     T L, nx, ny;
     unit_normal(lx, ly, L, nx, ny);
     const T hf = dmax(si.ef - si.z, T(0));
-    const T hyd = half * g * (hf - si.hc) * (hf + si.hc);
+    const T hyd = own_pressure<T, HR2>(a, hf, si);
     const int kind = tag & 3, grp = tag >> 2;
     const T un = si.uf * nx + si.vf * ny, vt = -si.uf * ny + si.vf * nx;
     T M, P, Tt;
@@ -572,10 +601,11 @@ __device__ __forceinline__ CellOut<T> cell_update(const StepArgs<T> &a, T dt, T 
 #pragma unroll
     for (int k = 0; k < 3; k++) {
         Side<T> si;
-        si.z = zi; si.hc = hi;
-        if (SCHEME == SWE_SCHEME_MUSCL) {
+        si.z = zi; si.hc = hi; si.zc = zi;
+        if (face_scheme(SCHEME)) {
             const Vec4<T> f = src.own_face(k);
             si.ef = f.x; si.uf = f.y; si.vf = f.z;
+            if (SCHEME == FLUX_MUSCL_HR2) si.z = f.w;          // the face bed (R16)
         } else {
             si.ef = hi + zi; si.uf = ui; si.vf = vi;
         }
@@ -584,23 +614,23 @@ __device__ __forceinline__ CellOut<T> cell_update(const StepArgs<T> &a, T dt, T 
             Side<T> sj;
             Vec4<T> Ui{}, Uj{};
             T dlen = T(0);
-            if (SCHEME == SWE_SCHEME_MUSCL) {
+            if (face_scheme(SCHEME)) {
                 const Vec4<T> f = src.nbr_face(nb[k]);
-                sj.ef = f.x; sj.uf = f.y; sj.vf = f.z; sj.z = f.w; sj.hc = T(0);
+                sj.ef = f.x; sj.uf = f.y; sj.vf = f.z; sj.z = f.w; sj.hc = T(0); sj.zc = f.w;
             } else if (SCHEME == SWE_SCHEME_WAF) {
                 const Vec4<T> p = src.nbr_centre(nb[k]);
-                sj.hc = p.x; sj.uf = p.y; sj.vf = p.z; sj.z = p.w; sj.ef = p.x + p.w;
+                sj.hc = p.x; sj.uf = p.y; sj.vf = p.z; sj.z = p.w; sj.ef = p.x + p.w; sj.zc = p.w;
                 Ui = src.own_up(k);
                 Uj = src.nbr_up(nb[k]);
                 dlen = dsqrt(fma_rn(dd[k].x, dd[k].x, mul_rn(dd[k].y, dd[k].y)));
             } else {
                 const Vec4<T> q = src.nbr_state(nb[k]);
-                sj.hc = q.x; sj.z = q.w; sj.ef = q.x + q.w;
+                sj.hc = q.x; sj.z = q.w; sj.ef = q.x + q.w; sj.zc = q.w;
                 primitives(q.x, q.y, q.z, h_eps, sj.uf, sj.vf);
             }
             interior_edge<T, SCHEME>(a, dt, si, sj, nb[k].own, ln[k].x, ln[k].y, dlen, Ui, Uj, c, nullptr);
         } else {
-            c = boundary_edge<T>(a, si, nb[k].tag, ln[k].x, ln[k].y, bs);
+            c = boundary_edge<T, SCHEME == FLUX_MUSCL_HR2>(a, si, nb[k].tag, ln[k].x, ln[k].y, bs);
         }
         accumulate(k, c, R0, R1, R2);
     }

@@ -34,7 +34,9 @@ __device__ __forceinline__ int block_member(const int *begin, int n_mem)
 }
 
 // Register caps as for the single-mesh kernels (swe_kernels.cu): FP32 MUSCL
-// prep at 40 and flux at 48 registers.
+// prep at 40 and flux at 48 registers.  SCHEME FLUX_MUSCL_HR2 is the LSQ
+// MUSCL scheme with the second-order hydrostatic reconstruction (its prep
+// reconstructs h as well and is left uncapped).
 template <typename T, int SCHEME>
 __global__ void __maxnreg__((sizeof(T) == 4 && SCHEME == SWE_SCHEME_MUSCL ? 40 : 255))
     k_prep_ens(const EnsEntry<T> *tab, const int *begin, int n_mem, int phase)
@@ -44,13 +46,14 @@ __global__ void __maxnreg__((sizeof(T) == 4 && SCHEME == SWE_SCHEME_MUSCL ? 40 :
     const StepArgs<T> &a = e.a[phase];
     const int i = ((int)blockIdx.x - begin[m]) * blockDim.x + threadIdx.x;
     if (i >= a.m.n) return;
-    if (SCHEME == SWE_SCHEME_MUSCL) prep_muscl_cell(a, i, e.F);
+    if (SCHEME == FLUX_MUSCL_HR2) prep_muscl_cell<T, 4>(a, i, e.F);
+    else if (SCHEME == SWE_SCHEME_MUSCL) prep_muscl_cell(a, i, e.F);
     else if (SCHEME == SWE_SCHEME_MUSCL_EDGE) prep_muscl_edge_cell(a, i, e.F);
     else prep_waf_cell(a, i, e.F, e.U);
 }
 
 template <typename T, int SCHEME>
-__global__ void __maxnreg__((sizeof(T) == 4 && SCHEME == SWE_SCHEME_MUSCL ? 48 : 255))
+__global__ void __maxnreg__((sizeof(T) == 4 && face_scheme(SCHEME) ? 48 : 255))
     k_flux_ens(const EnsEntry<T> *tab, const int *begin, int n_mem, int phase)
 {
     const int m = block_member(begin, n_mem);
@@ -69,7 +72,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
 }  // namespace
 
 template <typename T>
-cudaError_t launch_ensemble(int scheme, bool fused, const EnsEntry<T> *tab, const int *begin, int n_mem,
+cudaError_t launch_ensemble(int scheme, bool hr2, bool fused, const EnsEntry<T> *tab, const int *begin, int n_mem,
                             int phase, int grid, int block, cudaStream_t s)
 {
     if (fused) {
@@ -78,7 +81,10 @@ cudaError_t launch_ensemble(int scheme, bool fused, const EnsEntry<T> *tab, cons
         kern<<<grid, block, smem, s>>>(tab, begin, n_mem, phase);
         return cudaGetLastError();
     }
-    if (scheme == SWE_SCHEME_MUSCL) {
+    if (scheme == SWE_SCHEME_MUSCL && hr2) {
+        k_prep_ens<T, FLUX_MUSCL_HR2><<<grid, block, 0, s>>>(tab, begin, n_mem, phase);
+        k_flux_ens<T, FLUX_MUSCL_HR2><<<grid, block, 0, s>>>(tab, begin, n_mem, phase);
+    } else if (scheme == SWE_SCHEME_MUSCL) {
         k_prep_ens<T, SWE_SCHEME_MUSCL><<<grid, block, 0, s>>>(tab, begin, n_mem, phase);
         k_flux_ens<T, SWE_SCHEME_MUSCL><<<grid, block, 0, s>>>(tab, begin, n_mem, phase);
     } else if (scheme == SWE_SCHEME_MUSCL_EDGE) {
@@ -104,9 +110,9 @@ template <typename T> cudaError_t ensemble_prepare(int scheme, bool fused, int b
     return e;
 }
 
-template cudaError_t launch_ensemble<float>(int, bool, const EnsEntry<float> *, const int *, int, int, int, int,
+template cudaError_t launch_ensemble<float>(int, bool, bool, const EnsEntry<float> *, const int *, int, int, int, int,
                                             cudaStream_t);
-template cudaError_t launch_ensemble<double>(int, bool, const EnsEntry<double> *, const int *, int, int, int, int,
+template cudaError_t launch_ensemble<double>(int, bool, bool, const EnsEntry<double> *, const int *, int, int, int, int,
                                              cudaStream_t);
 template cudaError_t ensemble_prepare<float>(int, bool, int);
 template cudaError_t ensemble_prepare<double>(int, bool, int);

@@ -43,9 +43,9 @@ __device__ __forceinline__ Side<T> slot_side(const FusedSmem<T> &sm, int B, int 
     const Vec4<T> p = sm.Ps[slot];
     if (SCHEME == SWE_SCHEME_MUSCL) {
         const Vec4<T> f = sm.Fs[k * B + slot];
-        s.ef = f.x; s.uf = f.y; s.vf = f.z; s.z = f.w; s.hc = p.w;
+        s.ef = f.x; s.uf = f.y; s.vf = f.z; s.z = f.w; s.hc = p.w; s.zc = f.w;   // first-order bed
     } else {
-        s.hc = p.x; s.uf = p.y; s.vf = p.z; s.z = p.w; s.ef = p.x + p.w;
+        s.hc = p.x; s.uf = p.y; s.vf = p.z; s.z = p.w; s.ef = p.x + p.w; s.zc = p.w;
     }
     return s;
 }

@@ -34,11 +34,11 @@ using namespace swe_dev;
 // MUSCL face values: unweighted least squares over the face neighbours, then
 // Barth-Jespersen limiting at the three edge midpoints.  Zero gradient if the
 // cell or a neighbour is dry or the 2x2 system is singular.
-template <typename T>
-__global__ void __maxnreg__((sizeof(T) == 4 ? 40 : 255)) k_prep_muscl(StepArgs<T> a, Vec4<T> *F)
+template <typename T, int NQ = 3>
+__global__ void __maxnreg__((sizeof(T) == 4 && NQ == 3 ? 40 : 255)) k_prep_muscl(StepArgs<T> a, Vec4<T> *F)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < a.m.n) prep_muscl_cell(a, i, F);
+    if (i < a.m.n) prep_muscl_cell<T, NQ>(a, i, F);
 }
 
 // The paper's MUSCL (Sec. 6.2.3): edge-upwind slopes, beta-limited.
@@ -56,12 +56,12 @@ __global__ void k_prep_waf(StepArgs<T> a, Vec4<T> *P, Vec4<T> *U)
     if (i < a.m.n) prep_waf_cell(a, i, P, U);
 }
 
-// Register cap of the FP32 MUSCL flux kernel: 48 registers fit five
+// Register cap of the FP32 MUSCL flux kernels: 48 registers fit five
 // 256-thread blocks per SM without spills (the other instances are left to
 // the compiler, which would spill under the same cap).
 template <typename T, int SCHEME> constexpr int flux_maxnreg()
 {
-    return sizeof(T) == 4 && SCHEME == SWE_SCHEME_MUSCL ? 48 : 255;
+    return sizeof(T) == 4 && face_scheme(SCHEME) ? 48 : 255;
 }
 
 template <typename T, int SCHEME>
@@ -237,7 +237,8 @@ int mass_partials_needed(int64_t n) { return (int)((n + MASS_BLOCK * MASS_ITEMS 
 template <typename T>
 cudaError_t launch_prep(int scheme, const StepArgs<T> &a, Vec4<T> *F, Vec4<T> *U, int block, cudaStream_t s)
 {
-    if (scheme == SWE_SCHEME_MUSCL) k_prep_muscl<T><<<grid_for(a.m.n, block), block, 0, s>>>(a, F);
+    if (scheme == SWE_SCHEME_MUSCL && a.hr2) k_prep_muscl<T, 4><<<grid_for(a.m.n, block), block, 0, s>>>(a, F);
+    else if (scheme == SWE_SCHEME_MUSCL) k_prep_muscl<T><<<grid_for(a.m.n, block), block, 0, s>>>(a, F);
     else if (scheme == SWE_SCHEME_MUSCL_EDGE) k_prep_muscl_edge<T><<<grid_for(a.m.n, block), block, 0, s>>>(a, F);
     else if (scheme == SWE_SCHEME_WAF) k_prep_waf<T><<<grid_for(a.m.n, block), block, 0, s>>>(a, F, U);
     return cudaGetLastError();
@@ -253,6 +254,7 @@ template <typename T>
 cudaError_t launch_flux(int scheme, const StepArgs<T> &a, int block, cudaStream_t s)
 {
     // the paper's MUSCL differs only in prep: its flux kernel is the MUSCL one
+    if (scheme == SWE_SCHEME_MUSCL && a.hr2) return launch_flux_s<T, FLUX_MUSCL_HR2>(a, block, s);
     if (scheme == SWE_SCHEME_MUSCL || scheme == SWE_SCHEME_MUSCL_EDGE) return launch_flux_s<T, SWE_SCHEME_MUSCL>(a, block, s);
     if (scheme == SWE_SCHEME_WAF) return launch_flux_s<T, SWE_SCHEME_WAF>(a, block, s);
     return launch_flux_s<T, SWE_SCHEME_HLLC>(a, block, s);
@@ -263,7 +265,9 @@ cudaError_t launch_flux_list(int scheme, const StepArgs<T> &a, int block, cudaSt
 {
     if (a.n_list <= 0) return cudaSuccess;
     const unsigned grid = grid_for(a.n_list, block);
-    if (scheme == SWE_SCHEME_MUSCL || scheme == SWE_SCHEME_MUSCL_EDGE)
+    if (scheme == SWE_SCHEME_MUSCL && a.hr2)
+        k_flux_list<T, FLUX_MUSCL_HR2><<<grid, block, 0, s>>>(a);
+    else if (scheme == SWE_SCHEME_MUSCL || scheme == SWE_SCHEME_MUSCL_EDGE)
         k_flux_list<T, SWE_SCHEME_MUSCL><<<grid, block, 0, s>>>(a);
     else if (scheme == SWE_SCHEME_WAF)
         k_flux_list<T, SWE_SCHEME_WAF><<<grid, block, 0, s>>>(a);

@@ -6,7 +6,9 @@
 
 namespace swe_dev {
 
-template <typename T>
+// NQ = 4: also the limited gradient of h, for the face bed of the
+// second-order hydrostatic reconstruction (R16); F[3i + k].w is the face bed.
+template <typename T, int NQ = 3>
 __device__ __forceinline__ void prep_muscl_cell(const StepArgs<T> &a, int i, Vec4<T> *F)
 {
     const T h_eps = a.h_eps;
@@ -23,9 +25,11 @@ __device__ __forceinline__ void prep_muscl_cell(const StepArgs<T> &a, int i, Vec
     }
     T ui, vi;
     primitives(hi, a.hu[i], a.hv[i], h_eps, ui, vi);
-    T qi[3] = {hi + zi, ui, vi};
+    T qi[NQ];
+    qi[0] = hi + zi; qi[1] = ui; qi[2] = vi;
+    if (NQ == 4) qi[NQ - 1] = hi;
     Vec2<T> ln[3], dd[3];
-    T qn[3][3], ox[3], oy[3];
+    T qn[3][NQ], ox[3], oy[3];
     bool has[3];
     bool ok = hi > h_eps;
     int cnt = 0;
@@ -42,15 +46,17 @@ __device__ __forceinline__ void prep_muscl_cell(const StepArgs<T> &a, int i, Vec
             primitives(hj, a.hu[j], a.hv[j], h_eps, uj, vj);
             ok = ok && hj > h_eps;
             qn[k][0] = hj + a.m.z[j]; qn[k][1] = uj; qn[k][2] = vj;
+            if (NQ == 4) qn[k][NQ - 1] = hj;
             dd[k] = centroid_offset(a.m.ln, ox[k], oy[k], j, (w >> 1) & 3);
             cnt++;
         } else {
-            qn[k][0] = qi[0]; qn[k][1] = qi[1]; qn[k][2] = qi[2];
+#pragma unroll
+            for (int s = 0; s < NQ; s++) qn[k][s] = qi[s];
             dd[k].x = T(0); dd[k].y = T(0);
         }
     }
     Vec4<T> f[3];
-    muscl_faces(qi, zi, ok, cnt, qn, has, ox, oy, dd, f);
+    muscl_faces<T, NQ>(qi, zi, ok, cnt, qn, has, ox, oy, dd, f);
 #pragma unroll
     for (int k = 0; k < 3; k++) F[3 * i + k] = f[k];
 }

@@ -55,7 +55,7 @@ class Params(C.Structure):
     _fields_ = [("scheme", C.c_int), ("precision", C.c_int), ("time_scheme", C.c_int),
                 ("waf_limiter", C.c_int), ("g", C.c_double), ("h_eps", C.c_double),
                 ("r_eps", C.c_double), ("kernel", C.c_int), ("block", C.c_int), ("cfl_mode", C.c_int),
-                ("muscl_beta", C.c_double)]
+                ("muscl_beta", C.c_double), ("hr_order", C.c_int)]
 
 
 class BcValues(C.Structure):

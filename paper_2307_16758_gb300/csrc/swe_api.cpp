@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "swe_dev.h"
+#include "swe_ensemble.h"
 #include "swe_mesh.h"
 #include "swe_partition.h"
 #include "swe_tiles.h"
@@ -559,8 +560,8 @@ template <typename T> struct EnsembleT {
     bool built_fused = false;
     int built_block = 0;
     EnsEntry<T> *d_tab = nullptr;
-    int *d_begin = nullptr;
-    size_t tab_cap = 0;
+    int2 *d_blk = nullptr;        // per block of the batched grid: (member, block within the member)
+    size_t tab_cap = 0, blk_cap = 0;
     int grid = 0;
     // CUDA graphs of kGraphSteps batched steps, keyed by the starting step
     // phase (steps taken mod 6); captured on a private stream, dropped when
@@ -575,7 +576,7 @@ template <typename T> struct EnsembleT {
         clear_graphs();
         if (cap_stream) cudaStreamDestroy(cap_stream);
         dev_free(d_tab, stream);
-        dev_free(d_begin, stream);
+        dev_free(d_blk, stream);
     }
 
     void clear_graphs()
@@ -586,7 +587,7 @@ template <typename T> struct EnsembleT {
 
     cudaError_t launch_one(int phase, cudaStream_t s)
     {
-        return launch_ensemble<T>(scheme, mem[0]->p.hr_order == 2, built_fused, d_tab, d_begin, (int)mem.size(), phase, grid, built_block, s);
+        return launch_ensemble<T>(scheme, mem[0]->p.hr_order == 2, built_fused, d_tab, d_blk, phase, grid, built_block, s);
     }
 
     // kGraphSteps batched steps through a cached CUDA graph.
@@ -653,16 +654,24 @@ template <typename T> struct EnsembleT {
             if ((int64_t)begin[m] + blocks > INT32_MAX) { swe_set_error("ensemble too large"); return SWE_ERR_ARG; }
             begin[m + 1] = begin[m] + (int)blocks;
         }
+        const size_t nb = (size_t)begin[nm];
+        std::vector<int2> blk(nb);
+        for (size_t m = 0; m < nm; m++)
+            for (int b = begin[m]; b < begin[m + 1]; b++) blk[b] = make_int2((int)m, b - begin[m]);
         if (tab_cap < nm) {
             dev_free(d_tab, stream);
-            dev_free(d_begin, stream);
             d_tab = (EnsEntry<T> *)dev_alloc(sizeof(EnsEntry<T>) * nm, stream);
-            d_begin = (int *)dev_alloc(sizeof(int) * (nm + 1), stream);
-            if (!d_tab || !d_begin) { swe_set_error("device allocation failed"); return SWE_ERR_NOMEM; }
+            if (!d_tab) { swe_set_error("device allocation failed"); return SWE_ERR_NOMEM; }
             tab_cap = nm;
         }
+        if (blk_cap < nb) {
+            dev_free(d_blk, stream);
+            d_blk = (int2 *)dev_alloc(sizeof(int2) * nb, stream);
+            if (!d_blk) { swe_set_error("device allocation failed"); return SWE_ERR_NOMEM; }
+            blk_cap = nb;
+        }
         CK(cudaMemcpyAsync(d_tab, h.data(), sizeof(EnsEntry<T>) * nm, cudaMemcpyHostToDevice, stream));
-        CK(cudaMemcpyAsync(d_begin, begin.data(), sizeof(int) * (nm + 1), cudaMemcpyHostToDevice, stream));
+        CK(cudaMemcpyAsync(d_blk, blk.data(), sizeof(int2) * nb, cudaMemcpyHostToDevice, stream));
         CK(cudaStreamSynchronize(stream));
         CK(ensemble_prepare<T>(mem[0]->p.scheme, fused, block));
         clear_graphs();

@@ -86,15 +86,6 @@ struct FusedArgs {
     int block;      // threads per block (largest tile + halo)
 };
 
-// One member of a batched ensemble: its step arguments for each phase of the
-// launch pattern (steps taken mod 6: ping-pong buffer and CFL slot ring),
-// its fused-kernel tiling and its split-kernel scratch.
-template <typename T> struct EnsEntry {
-    StepArgs<T> a[6];
-    FusedArgs f;
-    Vec4<T> *F, *U;
-};
-
 // Launchers (defined in swe_kernels.cu and swe_fused.cu).  All launches go to `stream`.
 template <typename T>
 cudaError_t launch_prep(int scheme, const StepArgs<T> &a, Vec4<T> *F, Vec4<T> *U, int block, cudaStream_t s);
@@ -130,10 +121,5 @@ template <typename T>
 cudaError_t launch_pack_halo(int64_t n, const int32_t *cells, const T *h, const T *hu, const T *hv, T *buf,
                              cudaStream_t s);
 template <typename T> int split_max_threads(int scheme);     // launch limit of the split kernels
-
-template <typename T>
-cudaError_t launch_ensemble(int scheme, bool hr2, bool fused, const EnsEntry<T> *tab, const int *begin, int n_mem, int phase,
-                            int grid, int block, cudaStream_t s);
-template <typename T> cudaError_t ensemble_prepare(int scheme, bool fused, int block);
 
 int mass_partials_needed(int64_t n);

@@ -1,12 +1,13 @@
 // Batched ensemble kernels: one launch advances every member of an ensemble
 // of independent meshes by one explicit step.  The grid is the concatenation
-// of the members' grids; a block finds its member by binary search over the
-// members' first-block offsets and runs the same per-mesh device code as the
-// single-mesh kernels, with that member's arguments (its own buffers, CFL
-// slots and time step).
+// of the members' grids; a block reads its member and its block index within
+// the member from a per-block table (one 8-byte load, no search and no
+// barrier) and runs the same per-mesh device code as the single-mesh
+// kernels, with that member's arguments (its own buffers, CFL slots and time
+// step).
 #include <cuda_runtime.h>
 
-#include "swe_dev.h"
+#include "swe_ensemble.h"
 #include "swe_device.cuh"
 #include "swe_fused.cuh"
 #include "swe_split.cuh"
@@ -14,37 +15,18 @@
 namespace {
 using namespace swe_dev;
 
-// Member of block b: the largest m with begin[m] <= b (thread 0 searches, the
-// block shares the answer).
-__device__ __forceinline__ int block_member(const int *begin, int n_mem)
-{
-    __shared__ int sh_m;
-    if (threadIdx.x == 0) {
-        int lo = 0, hi = n_mem - 1;
-        const int b = (int)blockIdx.x;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (begin[mid] <= b) lo = mid;
-            else hi = mid - 1;
-        }
-        sh_m = lo;
-    }
-    __syncthreads();
-    return sh_m;
-}
-
 // Register caps as for the single-mesh kernels (swe_kernels.cu): FP32 MUSCL
 // prep at 40 and flux at 48 registers.  SCHEME FLUX_MUSCL_HR2 is the LSQ
 // MUSCL scheme with the second-order hydrostatic reconstruction (its prep
-// reconstructs h as well and is left uncapped).
+// reconstructs h as well: 48 registers).
 template <typename T, int SCHEME>
-__global__ void __maxnreg__((sizeof(T) == 4 && SCHEME == SWE_SCHEME_MUSCL ? 40 : 255))
-    k_prep_ens(const EnsEntry<T> *tab, const int *begin, int n_mem, int phase)
+__global__ void __maxnreg__((sizeof(T) != 4 ? 255 : SCHEME == SWE_SCHEME_MUSCL ? 40 : SCHEME == FLUX_MUSCL_HR2 ? 48 : 255))
+    k_prep_ens(const EnsEntry<T> *__restrict__ tab, const int2 *__restrict__ blk, int phase)
 {
-    const int m = block_member(begin, n_mem);
-    const EnsEntry<T> &e = tab[m];
+    const int2 b = blk[blockIdx.x];
+    const EnsEntry<T> &e = tab[b.x];
     const StepArgs<T> &a = e.a[phase];
-    const int i = ((int)blockIdx.x - begin[m]) * blockDim.x + threadIdx.x;
+    const int i = b.y * (int)blockDim.x + (int)threadIdx.x;
     if (i >= a.m.n) return;
     if (SCHEME == FLUX_MUSCL_HR2) prep_muscl_cell<T, 4>(a, i, e.F);
     else if (SCHEME == SWE_SCHEME_MUSCL) prep_muscl_cell(a, i, e.F);
@@ -54,47 +36,47 @@ __global__ void __maxnreg__((sizeof(T) == 4 && SCHEME == SWE_SCHEME_MUSCL ? 40 :
 
 template <typename T, int SCHEME>
 __global__ void __maxnreg__((sizeof(T) == 4 && face_scheme(SCHEME) ? 48 : 255))
-    k_flux_ens(const EnsEntry<T> *tab, const int *begin, int n_mem, int phase)
+    k_flux_ens(const EnsEntry<T> *__restrict__ tab, const int2 *__restrict__ blk, int phase)
 {
-    const int m = block_member(begin, n_mem);
-    flux_block<T, SCHEME>(tab[m].a[phase], (int)blockIdx.x - begin[m]);
+    const int2 b = blk[blockIdx.x];
+    flux_block<T, SCHEME>(tab[b.x].a[phase], b.y);
 }
 
 template <typename T, int SCHEME>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
-    k_fused_ens(const EnsEntry<T> *tab, const int *begin, int n_mem, int phase)
+    k_fused_ens(const EnsEntry<T> *__restrict__ tab, const int2 *__restrict__ blk, int phase)
 {
     extern __shared__ __align__(32) unsigned char smem_raw[];
-    const int m = block_member(begin, n_mem);
-    fused_tile<T, SCHEME>(tab[m].a[phase], tab[m].f, (int)blockIdx.x - begin[m], smem_raw);
+    const int2 b = blk[blockIdx.x];
+    fused_tile<T, SCHEME>(tab[b.x].a[phase], tab[b.x].f, b.y, smem_raw);
 }
 
 }  // namespace
 
 template <typename T>
-cudaError_t launch_ensemble(int scheme, bool hr2, bool fused, const EnsEntry<T> *tab, const int *begin, int n_mem,
-                            int phase, int grid, int block, cudaStream_t s)
+cudaError_t launch_ensemble(int scheme, bool hr2, bool fused, const EnsEntry<T> *tab, const int2 *blk, int phase,
+                            int grid, int block, cudaStream_t s)
 {
     if (fused) {
         const size_t smem = fused_smem_bytes<T>(scheme, block);
         auto kern = scheme == SWE_SCHEME_WAF ? k_fused_ens<T, SWE_SCHEME_WAF> : k_fused_ens<T, SWE_SCHEME_MUSCL>;
-        kern<<<grid, block, smem, s>>>(tab, begin, n_mem, phase);
+        kern<<<grid, block, smem, s>>>(tab, blk, phase);
         return cudaGetLastError();
     }
     if (scheme == SWE_SCHEME_MUSCL && hr2) {
-        k_prep_ens<T, FLUX_MUSCL_HR2><<<grid, block, 0, s>>>(tab, begin, n_mem, phase);
-        k_flux_ens<T, FLUX_MUSCL_HR2><<<grid, block, 0, s>>>(tab, begin, n_mem, phase);
+        k_prep_ens<T, FLUX_MUSCL_HR2><<<grid, block, 0, s>>>(tab, blk, phase);
+        k_flux_ens<T, FLUX_MUSCL_HR2><<<grid, block, 0, s>>>(tab, blk, phase);
     } else if (scheme == SWE_SCHEME_MUSCL) {
-        k_prep_ens<T, SWE_SCHEME_MUSCL><<<grid, block, 0, s>>>(tab, begin, n_mem, phase);
-        k_flux_ens<T, SWE_SCHEME_MUSCL><<<grid, block, 0, s>>>(tab, begin, n_mem, phase);
+        k_prep_ens<T, SWE_SCHEME_MUSCL><<<grid, block, 0, s>>>(tab, blk, phase);
+        k_flux_ens<T, SWE_SCHEME_MUSCL><<<grid, block, 0, s>>>(tab, blk, phase);
     } else if (scheme == SWE_SCHEME_MUSCL_EDGE) {
-        k_prep_ens<T, SWE_SCHEME_MUSCL_EDGE><<<grid, block, 0, s>>>(tab, begin, n_mem, phase);
-        k_flux_ens<T, SWE_SCHEME_MUSCL><<<grid, block, 0, s>>>(tab, begin, n_mem, phase);
+        k_prep_ens<T, SWE_SCHEME_MUSCL_EDGE><<<grid, block, 0, s>>>(tab, blk, phase);
+        k_flux_ens<T, SWE_SCHEME_MUSCL><<<grid, block, 0, s>>>(tab, blk, phase);
     } else if (scheme == SWE_SCHEME_WAF) {
-        k_prep_ens<T, SWE_SCHEME_WAF><<<grid, block, 0, s>>>(tab, begin, n_mem, phase);
-        k_flux_ens<T, SWE_SCHEME_WAF><<<grid, block, 0, s>>>(tab, begin, n_mem, phase);
+        k_prep_ens<T, SWE_SCHEME_WAF><<<grid, block, 0, s>>>(tab, blk, phase);
+        k_flux_ens<T, SWE_SCHEME_WAF><<<grid, block, 0, s>>>(tab, blk, phase);
     } else {
-        k_flux_ens<T, SWE_SCHEME_HLLC><<<grid, block, 0, s>>>(tab, begin, n_mem, phase);
+        k_flux_ens<T, SWE_SCHEME_HLLC><<<grid, block, 0, s>>>(tab, blk, phase);
     }
     return cudaGetLastError();
 }
@@ -110,9 +92,9 @@ template <typename T> cudaError_t ensemble_prepare(int scheme, bool fused, int b
     return e;
 }
 
-template cudaError_t launch_ensemble<float>(int, bool, bool, const EnsEntry<float> *, const int *, int, int, int, int,
+template cudaError_t launch_ensemble<float>(int, bool, bool, const EnsEntry<float> *, const int2 *, int, int, int,
                                             cudaStream_t);
-template cudaError_t launch_ensemble<double>(int, bool, bool, const EnsEntry<double> *, const int *, int, int, int, int,
+template cudaError_t launch_ensemble<double>(int, bool, bool, const EnsEntry<double> *, const int2 *, int, int, int,
                                              cudaStream_t);
 template cudaError_t ensemble_prepare<float>(int, bool, int);
 template cudaError_t ensemble_prepare<double>(int, bool, int);

@@ -1,0 +1,21 @@
+// Batched ensemble: the per-member table and the launcher (swe_ensemble.cu).
+#pragma once
+#include "swe_dev.h"
+
+// One member of a batched ensemble: its step arguments for each phase of the
+// launch pattern (steps taken mod 6: ping-pong buffer and CFL slot ring),
+// its fused-kernel tiling and its split-kernel scratch.
+template <typename T> struct EnsEntry {
+    StepArgs<T> a[6];
+    FusedArgs f;
+    Vec4<T> *F, *U;
+};
+
+// Block b of a batched launch runs block blk[b].y of member blk[b].x.
+// One launch (two for the split kernels with a prep pass) advances every
+// member by one step of the given phase.  hr2: the members use the
+// second-order hydrostatic reconstruction (all or none of them).
+template <typename T>
+cudaError_t launch_ensemble(int scheme, bool hr2, bool fused, const EnsEntry<T> *tab, const int2 *blk, int phase,
+                            int grid, int block, cudaStream_t s);
+template <typename T> cudaError_t ensemble_prepare(int scheme, bool fused, int block);

@@ -33,9 +33,12 @@ using namespace swe_dev;
 
 // MUSCL face values: unweighted least squares over the face neighbours, then
 // Barth-Jespersen limiting at the three edge midpoints.  Zero gradient if the
-// cell or a neighbour is dry or the 2x2 system is singular.
+// cell or a neighbour is dry or the 2x2 system is singular.  NQ = 4 also
+// reconstructs h (second-order hydrostatic reconstruction).  FP32 register
+// caps: 40 (six 256-thread blocks per SM) and 48 for NQ = 4 (five blocks;
+// at 54 uncapped registers it ran four).
 template <typename T, int NQ = 3>
-__global__ void __maxnreg__((sizeof(T) == 4 && NQ == 3 ? 40 : 255)) k_prep_muscl(StepArgs<T> a, Vec4<T> *F)
+__global__ void __maxnreg__((sizeof(T) == 4 ? (NQ == 3 ? 40 : 48) : 255)) k_prep_muscl(StepArgs<T> a, Vec4<T> *F)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < a.m.n) prep_muscl_cell<T, NQ>(a, i, F);

@@ -80,7 +80,8 @@ typedef struct {
     double h_eps;     /* depth below which a cell counts as dry [m] */
     double r_eps;     /* WAF: relative size of a local change treated as zero */
     int kernel;       /* SWE_KERNEL_*: split (face values in scratch) or fused tile kernel */
-    int block;        /* threads per block (0: default) */
+    int block;        /* threads per block of the flux or fused kernel (0: default; the
+                         split prep kernels use 128 unless swe_autotune picks another) */
     int cfl_mode;     /* SWE_CFL_GLOBAL (default) or SWE_CFL_LOCAL */
     double muscl_beta; /* SWE_SCHEME_MUSCL_EDGE limiter, 1 (MINBEE) .. 2 (SUPERBEE, default) */
     int hr_order;     /* hydrostatic reconstruction: 1 on the cell bed (default); 2 (SWE_SCHEME_MUSCL,
@@ -235,7 +236,9 @@ int swe_muscl_step_noalloc(int64_t n_cells, const int32_t *nbr, const float *ln,
  * the fastest; the simulation state, time and step count are left as they
  * were (every configuration computes the same bits).  m is the state's mesh
  * (needed to tile it for the fused kernel; NULL limits the search to the split
- * kernels).  Outputs (may be NULL): SWE_KERNEL_*, threads per block, ms per step. */
+ * kernels).  With the split kernels it then times the prep kernel's own
+ * block size (64/128/256 threads; 128 until tuned).  Outputs (may be NULL):
+ * SWE_KERNEL_*, threads per block of the flux (or fused) kernel, ms per step. */
 int swe_autotune(swe_state *s, const swe_mesh *m, int trial_steps, double cfl, int *kernel, int *block,
                  double *ms_per_step);
 

@@ -105,6 +105,11 @@ template <typename T> struct StateT {
     std::map<std::pair<int, double>, cudaGraphExec_t> graphs;
     cudaStream_t cap_stream = nullptr;
     bool use_graphs = true;
+    // Threads per block of the split prep kernels, apart from the flux
+    // kernel's: prep is bound by memory latency and runs best in short blocks
+    // (FP32 MUSCL on a 13M-cell river: 128 threads 0.227 ms, 256 0.234, 512
+    // 0.248); the autotuner may pick another.
+    int prep_bl = 128;
     int64_t k = 0;            // steps launched (selects the smax slots)
     bool smax_valid = false;
     T qlen[SWE_MAX_GROUPS] = {}, level[SWE_MAX_GROUPS] = {};
@@ -323,7 +328,7 @@ template <typename T> struct StateT {
     {
         if (fused) return traced(SWE_K_FUSED, [&] { return launch_fused<T>(p.scheme, a, fa, stream); });
         if (p.scheme != SWE_SCHEME_HLLC) {
-            cudaError_t e = traced(SWE_K_PREP, [&] { return launch_prep<T>(p.scheme, a, F, U, bl, stream); });
+            cudaError_t e = traced(SWE_K_PREP, [&] { return launch_prep<T>(p.scheme, a, F, U, prep_bl, stream); });
             if (e != cudaSuccess) return e;
         }
         if (!sched) return traced(SWE_K_FLUX, [&] { return launch_flux<T>(p.scheme, a, bl, stream); });
@@ -538,9 +543,34 @@ int autotune(StateT<T> &S, const swe_mesh *m, int trials, double cfl, int &best_
         if (rc == SWE_OK) rc = rr;
         if (rc != SWE_OK) break;
     }
+    // the split kernels' prep block, with the chosen kernel and block
+    int rc2 = S.configure(best.fused, best.block, m);
+    if (rc == SWE_OK && rc2 == SWE_OK && !best.fused && S.p.scheme != SWE_SCHEME_HLLC) {
+        const int pb0 = S.prep_bl;
+        int best_pb = pb0;
+        double best_pms = 1e30;
+        for (int pb : {64, 128, 256}) {
+            S.prep_bl = pb;
+            rc = S.one_step(cfl, nullptr);                  // warm-up
+            if (rc == SWE_OK) rc = S.restore(sn);
+            if (rc == SWE_OK) rc = (cudaEventRecord(e0, S.stream) == cudaSuccess) ? SWE_OK : SWE_ERR_CUDA;
+            for (int q = 0; q < trials && rc == SWE_OK; q++) rc = S.one_step(cfl, nullptr);
+            float ms = 0.f;
+            if (rc == SWE_OK && cudaEventRecord(e1, S.stream) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+                cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms / trials < best_pms) {
+                best_pms = ms / trials;
+                best_pb = pb;
+            }
+            int rr = S.restore(sn);
+            if (rc == SWE_OK) rc = rr;
+            if (rc != SWE_OK) break;
+        }
+        S.prep_bl = rc == SWE_OK ? best_pb : pb0;
+        if (rc == SWE_OK && best_pms < best_ms) best_ms = best_pms;
+        S.clear_graphs();
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    int rc2 = S.configure(best.fused, best.block, m);
     if (rc2 == SWE_OK) rc2 = S.restore(sn);
     S.drop(sn);
     if (rc != SWE_OK) return rc;

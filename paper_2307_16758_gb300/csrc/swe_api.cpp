@@ -179,7 +179,7 @@ template <typename T> struct StateT {
             swe_set_error("the boundary-first schedule runs the split kernels (clear the partition first)");
             return SWE_ERR_ARG;
         }
-        const int lim = want_fused ? fused_max_threads<T>(p.scheme) : split_max_threads<T>(p.scheme);
+        const int lim = want_fused ? fused_max_threads<T>(p.scheme) : split_max_threads<T>(p.scheme, p.hr_order == 2);
         if (lim <= 0) { swe_set_error("cannot query the kernels (no usable GPU?)"); return SWE_ERR_CUDA; }
         if (block <= 0 || block % 32 || block > lim) {
             swe_set_error("block of " + std::to_string(block) + " threads is not a multiple of 32 within the kernel's limit of " +
@@ -498,7 +498,7 @@ struct Candidate { bool fused; int block; };
 template <typename T> std::vector<Candidate> candidates(const StateT<T> &S, const swe_mesh *m)
 {
     std::vector<Candidate> c;
-    const int ls = split_max_threads<T>(S.p.scheme);
+    const int ls = split_max_threads<T>(S.p.scheme, S.p.hr_order == 2);
     for (int b : {128, 256, 512})
         if (b <= ls) c.push_back({false, b});
     if ((S.p.scheme == SWE_SCHEME_MUSCL || S.p.scheme == SWE_SCHEME_WAF) && m && !S.sched && S.p.hr_order == 1) {
@@ -674,6 +674,12 @@ template <typename T> struct EnsembleT {
         std::vector<int> begin(nm + 1, 0);
         const bool fused = mem[0]->fused;
         const int block = mem[0]->block();
+        const int lim = ensemble_max_threads<T>(mem[0]->p.scheme, mem[0]->p.hr_order == 2, fused);
+        if (block > lim) {
+            swe_set_error("block of " + std::to_string(block) + " threads exceeds the batched kernels' limit of " +
+                          std::to_string(lim));
+            return lim > 0 ? SWE_ERR_ARG : SWE_ERR_CUDA;
+        }
         for (size_t m = 0; m < nm; m++) {
             StateT<T> &s = *mem[m];
             for (int ph = 0; ph < 6; ph++) h[m].a[ph] = s.args_for_phase(ph, cfl_);

@@ -120,6 +120,6 @@ template <typename T> cudaError_t launch_flux_list(int scheme, const StepArgs<T>
 template <typename T>
 cudaError_t launch_pack_halo(int64_t n, const int32_t *cells, const T *h, const T *hu, const T *hv, T *buf,
                              cudaStream_t s);
-template <typename T> int split_max_threads(int scheme);     // launch limit of the split kernels
+template <typename T> int split_max_threads(int scheme, bool hr2);     // launch limit of the flux kernels
 
 int mass_partials_needed(int64_t n);

@@ -92,6 +92,36 @@ template <typename T> cudaError_t ensemble_prepare(int scheme, bool fused, int b
     return e;
 }
 
+namespace {
+template <typename K> int max_threads(K kern)
+{
+    cudaFuncAttributes fa{};
+    return cudaFuncGetAttributes(&fa, kern) == cudaSuccess ? fa.maxThreadsPerBlock : 0;
+}
+template <typename T, int SCHEME, bool PREP> int split_ens_max_threads()
+{
+    const int f = max_threads(k_flux_ens<T, SCHEME>);
+    if (!PREP) return f;
+    const int p = max_threads(k_prep_ens<T, SCHEME>);
+    return p < f ? p : f;
+}
+}  // namespace
+
+template <typename T> int ensemble_max_threads(int scheme, bool hr2, bool fused)
+{
+    if (fused) return max_threads(scheme == SWE_SCHEME_WAF ? k_fused_ens<T, SWE_SCHEME_WAF> : k_fused_ens<T, SWE_SCHEME_MUSCL>);
+    if (scheme == SWE_SCHEME_MUSCL && hr2) return split_ens_max_threads<T, FLUX_MUSCL_HR2, true>();
+    if (scheme == SWE_SCHEME_MUSCL) return split_ens_max_threads<T, SWE_SCHEME_MUSCL, true>();
+    if (scheme == SWE_SCHEME_MUSCL_EDGE) {
+        const int p = max_threads(k_prep_ens<T, SWE_SCHEME_MUSCL_EDGE>), f = max_threads(k_flux_ens<T, SWE_SCHEME_MUSCL>);
+        return p < f ? p : f;
+    }
+    if (scheme == SWE_SCHEME_WAF) return split_ens_max_threads<T, SWE_SCHEME_WAF, true>();
+    return split_ens_max_threads<T, SWE_SCHEME_HLLC, false>();
+}
+template int ensemble_max_threads<float>(int, bool, bool);
+template int ensemble_max_threads<double>(int, bool, bool);
+
 template cudaError_t launch_ensemble<float>(int, bool, bool, const EnsEntry<float> *, const int2 *, int, int, int,
                                             cudaStream_t);
 template cudaError_t launch_ensemble<double>(int, bool, bool, const EnsEntry<double> *, const int2 *, int, int, int,

@@ -19,3 +19,5 @@ template <typename T>
 cudaError_t launch_ensemble(int scheme, bool hr2, bool fused, const EnsEntry<T> *tab, const int2 *blk, int phase,
                             int grid, int block, cudaStream_t s);
 template <typename T> cudaError_t ensemble_prepare(int scheme, bool fused, int block);
+// The largest block that every batched kernel of this configuration launches with.
+template <typename T> int ensemble_max_threads(int scheme, bool hr2, bool fused);

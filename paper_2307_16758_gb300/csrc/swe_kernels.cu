@@ -223,17 +223,29 @@ inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 
 
 }  // namespace
 
-template <typename T> int split_max_threads(int scheme)
+namespace {
+template <typename K> int max_threads(K kern)
 {
     cudaFuncAttributes fa{};
-    cudaError_t e;
-    if (scheme == SWE_SCHEME_MUSCL || scheme == SWE_SCHEME_MUSCL_EDGE) e = cudaFuncGetAttributes(&fa, k_flux<T, SWE_SCHEME_MUSCL>);
-    else if (scheme == SWE_SCHEME_WAF) e = cudaFuncGetAttributes(&fa, k_flux<T, SWE_SCHEME_WAF>);
-    else e = cudaFuncGetAttributes(&fa, k_flux<T, SWE_SCHEME_HLLC>);
-    return e == cudaSuccess ? fa.maxThreadsPerBlock : 0;
+    return cudaFuncGetAttributes(&fa, kern) == cudaSuccess ? fa.maxThreadsPerBlock : 0;
 }
-template int split_max_threads<float>(int);
-template int split_max_threads<double>(int);
+template <typename T, int SCHEME> int flux_max_threads()
+{
+    const int a = max_threads(k_flux<T, SCHEME>), b = max_threads(k_flux_list<T, SCHEME>);
+    return a < b ? a : b;
+}
+}  // namespace
+
+// The largest block that the flux kernels (plain and list-driven) launch with.
+template <typename T> int split_max_threads(int scheme, bool hr2)
+{
+    if (scheme == SWE_SCHEME_MUSCL && hr2) return flux_max_threads<T, FLUX_MUSCL_HR2>();
+    if (scheme == SWE_SCHEME_MUSCL || scheme == SWE_SCHEME_MUSCL_EDGE) return flux_max_threads<T, SWE_SCHEME_MUSCL>();
+    if (scheme == SWE_SCHEME_WAF) return flux_max_threads<T, SWE_SCHEME_WAF>();
+    return flux_max_threads<T, SWE_SCHEME_HLLC>();
+}
+template int split_max_threads<float>(int, bool);
+template int split_max_threads<double>(int, bool);
 
 int mass_partials_needed(int64_t n) { return (int)((n + MASS_BLOCK * MASS_ITEMS - 1) / (MASS_BLOCK * MASS_ITEMS)); }
 

@@ -133,3 +133,36 @@ def test_ensemble_autotune():
         (h, hu, hv), (t, k), _ = _alone(w, p, 20)
         assert np.array_equal(st.get_state()[0], h)
         assert st.time()[1] == 20
+
+
+@pytest.mark.parametrize("scheme", ["hllc", "muscl", "waf", "muscl_edge"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_ensemble_autotune_every_scheme_and_block_limit(scheme, precision):
+    """Every candidate the ensemble autotuner keeps launches (the batched kernels have their own
+    register counts and so their own largest block), and the result is still stepping alone."""
+    ws = _scenarios()[:2]
+    p = swe.swe_params_default(scheme, precision)
+    meshes = [swe.Mesh.from_workload(w) for w in ws]
+    states = [swe.State.from_workload(m, p, w) for m, w in zip(meshes, ws)]
+    ens = swe.Ensemble(states)
+    kernel, block, ms = ens.autotune(meshes, trial_steps=2)
+    assert ms > 0 and block in (128, 256, 512)
+    ens.step(12, 0.9)
+    ens.sync()
+    p_alone = swe.swe_params_default(scheme, precision, kernel=kernel, block=block)
+    for w, st in zip(ws, states):
+        (h, hu, hv), (t, k), _ = _alone(w, p_alone, 12)
+        assert np.array_equal(st.get_state()[0], h) and k == 12
+    # 1024 threads: refused where a kernel cannot launch them, else the same bits as stepping alone
+    big = swe.swe_params_default(scheme, precision, kernel="split", block=1024)
+    try:
+        members = [swe.State.from_workload(m, big, w) for m, w in zip(meshes, ws)]
+        e2 = swe.Ensemble(members)
+        e2.step(3, 0.9)
+        e2.sync()
+    except swe.SweError as err:
+        assert err.code == -1          # an argument error, not a failed launch
+        return
+    for w, st in zip(ws, members):
+        (h, hu, hv), (t, k), _ = _alone(w, big, 3)
+        assert np.array_equal(st.get_state()[0], h)

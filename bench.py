@@ -391,9 +391,14 @@ def run_gpu(args):
     if any(iss.values()):
         out["issue_roofline"] = {k: v for k, v in iss.items() if v}
 
+    c32 = ncu_counters(f"{kname}:{dom}:{skey}:fp32")
+    if c32 and "flops_per_cell" in c32:
+        out["roofline"]["flops_per_cell"] = c32["flops_per_cell"]
     if rank == 0 and not args.quick:
         out.update(fp64_comparison(args, mesh, w, swe, torch))
         out["fp64"]["fp32_speedup"] = out["fp64"]["ms_per_step"] / step_ms
+        out["alu_peaks"] = alu_peaks(swe, torch, local, clocks)
+        out["fp64"]["roofline"] = fp64_alu_roofline(out["fp64"], out["alu_peaks"], kname, skey, n)
         if ws == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(w, n)
     if rank == 0:
@@ -405,6 +410,33 @@ def run_gpu(args):
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def alu_peaks(swe, torch, dev, clocks):
+    """FMA rates of this GPU measured by the library's probe, next to the figures that the
+    unit counts give (per SM and clock: 128 FP32 FMAs, 2 FP64 FMAs) at the highest SM clock."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clocks.get("sm_max_mhz") or 0.0
+    stream = torch.cuda.current_stream().cuda_stream
+    return {"unit": "TFLOP/s",
+            "fp32": swe.swe_fma_peak("fp32", stream=stream) / 1e12,
+            "fp64": swe.swe_fma_peak("fp64", stream=stream) / 1e12,
+            "fp32_from_units": 2 * 128 * sms * mhz * 1e6 / 1e12,
+            "fp64_from_units": 2 * 2 * sms * mhz * 1e6 / 1e12,
+            "source": "swe_fma_peak (8 independent FMA chains per thread, 8 x 256 threads per SM)"}
+
+
+def fp64_alu_roofline(fp64, peaks, kname, skey, n):
+    """The FP64 flux kernel against the measured FP64 FMA rate: ncu's FP64 operations per cell
+    (add, mul, 2 x fma) over the kernel's CUDA-event time."""
+    c = ncu_counters(f"{kname}:flux:{skey}:fp64")
+    ms = fp64.get("per_kernel_ms", {}).get("flux")
+    if not c or "fp64_flops_per_cell" not in c or not ms:
+        return None
+    achieved = c["fp64_flops_per_cell"] * n / (ms / 1e3) / 1e12
+    return {"bound": "alu", "kernel": "flux", "achieved": achieved, "peak": peaks["fp64"], "unit": "TFLOP/s",
+            "frac": achieved / peaks["fp64"], "fp64_flops_per_cell": c["fp64_flops_per_cell"],
+            "peak_source": "measured FP64 FMA rate (swe_fma_peak)", "kernel_ms": ms}
 
 
 def fp64_comparison(args, mesh, w, swe, torch):
@@ -427,6 +459,10 @@ def fp64_comparison(args, mesh, w, swe, torch):
     dts = s64.dt_history(m_steps)
     h64, hu64, hv64 = s64.get_state()
     mass64 = s64.mass()
+    # per-kernel device time of the FP64 path (CUDA events around each launch)
+    s64.profile_begin()
+    s64.step(10, args.cfl)
+    prof64 = s64.profile_end()
     p32 = swe.swe_params_default(args.scheme, "fp32", kernel=args.kernel, hr_order=args.hr_order)
     p32.h_eps = p64.h_eps         # same algorithm, precision differs only
     p32.r_eps = p64.r_eps
@@ -458,7 +494,8 @@ def fp64_comparison(args, mesh, w, swe, torch):
     s32.close()
     s64.close()
     v64 = n * m_steps / (ms64 / 1e3)
-    return {"fp64": {"value": v64, "unit": UNIT, "ms_per_step": ms64 / m_steps, "steps": m_steps},
+    return {"fp64": {"value": v64, "unit": UNIT, "ms_per_step": ms64 / m_steps, "steps": m_steps,
+                     "per_kernel_ms": {k: v[0] / v[1] for k, v in prof64.items()}},
             "error_fp32_vs_fp64": err}
 
 

@@ -194,6 +194,19 @@ int swe_profile_end(swe_state *s, double *kernel_ms, int64_t *launches);
 /* The last n time steps taken (oldest first), n <= min(steps taken, SWE_DT_HISTORY). */
 int swe_dt_history(swe_state *s, double *dt, int n);
 
+/* ---- Arithmetic peak ------------------------------------------------------ */
+
+/* Not in the paper.  Fused multiply-adds per second of this GPU in FP32 or
+ * FP64 (precision SWE_FP32 / SWE_FP64), measured by one launch of
+ * 8 x 256 threads per SM, each running 8 independent FMA chains `iters`
+ * times (1 .. 2^20; about 65536 for FP32 and 2048 for FP64 give a few ms),
+ * timed with CUDA events on `stream` (a cudaStream_t, may be NULL) after one
+ * shorter warm-up launch.  *flops_per_s counts an FMA as two operations.
+ * It is the denominator of the arithmetic roofline of the FP64 path.  Uses a
+ * small device buffer from the allocator; blocks until the launch ends.
+ * Errors: SWE_ERR_ARG, SWE_ERR_NOMEM, SWE_ERR_CUDA. */
+int swe_fma_peak(int precision, int iters, void *stream, double *flops_per_s);
+
 /* ---- One step without device allocation ---------------------------------- */
 
 /* The paper has no counterpart to this entry point; it exists for callers

@@ -23,6 +23,7 @@ SOURCES = [
     ("swe_kernels.cu", ["-Xptxas", "-v"] if os.environ.get("SWE_PTXAS_VERBOSE") else []),
     ("swe_fused.cu", ["-Xptxas", "-v"] if os.environ.get("SWE_PTXAS_VERBOSE") else []),
     ("swe_noalloc.cu", []),
+    ("swe_probe.cu", []),
     ("swe_ensemble.cu", ["-Xptxas", "-v"] if os.environ.get("SWE_PTXAS_VERBOSE") else []),
     ("swe_api.cpp", []),
     ("swe_tiles.cpp", []),

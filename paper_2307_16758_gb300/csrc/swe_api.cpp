@@ -26,11 +26,13 @@ static thread_local std::string g_err;
 void swe_set_error(const std::string &msg) { g_err = msg; }
 
 namespace {
-
 swe_alloc_fn g_alloc = nullptr;
 swe_free_fn g_free = nullptr;
 void *g_ctx = nullptr;
+}  // namespace
 
+// Device memory through the allocator installed by swe_set_allocator, else
+// cudaMalloc (also used by the arithmetic-peak probe).
 void *dev_alloc(size_t bytes, cudaStream_t s)
 {
     if (bytes == 0) bytes = 16;
@@ -47,6 +49,8 @@ void dev_free(void *p, cudaStream_t s)
     if (g_free) g_free(p, (void *)s, g_ctx);
     else cudaFree(p);
 }
+
+namespace {
 
 #define CK(call)                                                                  \
     do {                                                                          \

@@ -39,7 +39,7 @@ EXPORTED = [
     "swe_ensemble_sync", "swe_profile_begin", "swe_profile_end", "swe_dt_history",
     "swe_muscl_step_noalloc", "swe_autotune", "swe_ensemble_autotune",
     "swe_partition_create", "swe_partition_destroy", "swe_partition_info", "swe_partition_export",
-    "swe_set_partition", "swe_halo_get",
+    "swe_set_partition", "swe_halo_get", "swe_fma_peak",
 ]
 NOALLOC_MAX_CELLS = 262144
 KERNEL_KINDS = ["prep", "flux", "heun_avg", "smax", "fused", "ensemble", "k6", "k7"]
@@ -113,6 +113,7 @@ def load_library(path: str = LIB_PATH, use_torch_allocator: bool = True):
     lib.swe_partition_export.argtypes = [vp, i32, vp, vp, vp]
     lib.swe_set_partition.argtypes = [vp, vp]
     lib.swe_halo_get.argtypes = [vp, i32, vp, vp, vp]
+    lib.swe_fma_peak.argtypes = [i32, i32, vp, C.POINTER(dp)]
     if use_torch_allocator:
         import torch
 
@@ -368,6 +369,16 @@ def swe_halo_get(s, part, n):
     h, hu, hv = np.empty(max(n, 1)), np.empty(max(n, 1)), np.empty(max(n, 1))
     _check(load_library().swe_halo_get(s, int(part), _p(h), _p(hu), _p(hv)))
     return h[:n], hu[:n], hv[:n]
+
+
+def swe_fma_peak(precision="fp32", iters=None, stream=None):
+    """Fused multiply-add rate of the GPU (FLOP/s, an FMA counted as two)."""
+    prec = PRECISION.get(precision, precision)
+    if iters is None:
+        iters = 65536 if prec == PRECISION["fp32"] else 2048
+    out = C.c_double(0.0)
+    _check(load_library().swe_fma_peak(prec, int(iters), stream, C.byref(out)))
+    return out.value
 
 
 class Mesh:

@@ -141,3 +141,11 @@ def test_binding_classes_own_their_handles():
         for m in methods:
             assert callable(getattr(cls, m, None)), (cls.__name__, m)
     assert swe.State.close is not swe.Ensemble.close
+
+
+@pytest.mark.parametrize("args", [("fp32", 0), ("fp32", 1 << 21), (7, 100)])
+def test_fma_peak_rejects_bad_arguments_before_any_launch(args):
+    precision, iters = args
+    with pytest.raises(swe.SweError) as e:
+        swe.swe_fma_peak(precision, iters)
+    assert e.value.code == -1

@@ -626,10 +626,12 @@ def run_time_error(args):
                     st.step(1, cfl)
                     steps += 1
                 st.close()
+                # warm-up on the state that is timed (it captures the 24-step CUDA graph the timed
+                # run replays), then back to the initial condition; the time is taken from there
                 st = swe.State.from_workload(mesh, p, w)
-                st.step(min(steps, 3), cfl)                   # graphs and caches warm, then restart
-                st.close()
-                st = swe.State.from_workload(mesh, p, w)
+                st.step(24, cfl)
+                st.set_state(w.h, w.hu, w.hv)
+                t0 = st.time()[0]
                 torch.cuda.synchronize()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
@@ -637,7 +639,7 @@ def run_time_error(args):
                 e1.record(stream)
                 e1.synchronize()
                 ms = e0.elapsed_time(e1)
-                t = st.time()[0]
+                t = st.time()[0] - t0
                 h = st.get_state()[0]
                 st.close()
                 hex_, _ = stoker(cx, t, 5.0, 1.0, 0.5)
@@ -650,6 +652,95 @@ def run_time_error(args):
     print(json.dumps({"study": "GPU time against L2 error, wet-bed dam break (Sec. 6.3)",
                       "unit": {"ms": "GPU ms to t = 1 s", "l2_h": "relative L2 of h against Stoker"},
                       "rows": rows}))
+
+
+def run_configs(args):
+    """Every configuration of the workload list at its full size: GPU throughput (CFL steps in CUDA
+    graphs, device events) in the precisions each one names, and the FP64 oracle on the host cores,
+    all cores and one core, over the full step count (the 13M river: 20 steps; one core: at most 20
+    steps), with the GPU result after the oracle's steps (its time steps replayed) against the
+    oracle's, at checkpoints along the run.  One JSON line per configuration and scheme."""
+    import torch
+
+    import oracle
+    from paper_2307_16758_gb300 import swe
+    from paper_2307_16758_gb300 import workloads as W
+    import __graft_entry__
+
+    __graft_entry__.build()
+    swe.load_library()
+    oracle.build()
+    stream = torch.cuda.current_stream()
+    cores = os.cpu_count() or 1
+    cfgs = [
+        (1, "dam break, 100x10 squares (Sec. 6.3 setup)", lambda: W.dam_break_1d(100, 10, 100.0, 10.0, 1.0, 0.5),
+         ["hllc"], ["fp64"], 200, 200),
+        (2, "partial dam break over Gaussian bathymetry, 1000x500 jittered grid", lambda: W.partial_dam_break(),
+         ["muscl", "waf"], ["fp64"], 1000, 1000),
+        (3, "river 4160x1563 jittered grid", lambda: W.river(), ["muscl"], ["fp32", "fp64"], 2000, 20),
+        (4, "river 2310x866 jittered grid", lambda: W.river(2310, 866), ["waf", "muscl"], ["fp32"], 2000, 2000),
+    ]
+    for cid, name, make, schemes, precisions, steps, o_steps in cfgs:
+        if args.config and cid not in args.config:
+            continue
+        w = make()
+        mesh = swe.Mesh.from_workload(w, "morton")
+        om = oracle.Mesh(w.nodes, w.tris, w.bnd_edges, w.bnd_tag, w.cut_edges)
+        n = mesh.n
+        for scheme in schemes:
+            row = {"config": cid, "workload": name, "cells": n, "scheme": scheme, "steps": steps, "gpu": {}}
+            for precision in precisions:
+                p = swe.swe_params_default(scheme, precision)
+                st = swe.State.from_workload(mesh, p, w)
+                st.step(24, args.cfl)              # captures the 24-step graph that the timed run replays
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                st.step(steps, args.cfl)
+                e1.record(stream)
+                e1.synchronize()
+                ms = e0.elapsed_time(e1)
+                row["gpu"][precision] = {"ms_per_step": ms / steps, "value": n * steps / (ms / 1e3), "unit": UNIT}
+                st.close()
+            # the oracle with the GPU's thresholds of the first precision named (same algorithm)
+            p0 = swe.swe_params_default(scheme, precisions[0])
+            o = oracle.opts(scheme, h_eps=p0.h_eps, r_eps=p0.r_eps, cfl=args.cfl, threads=cores)
+            # the oracle in chunks; after each the GPU replays the chunk's time steps and the two
+            # are compared (how far they drift apart with the number of steps)
+            st = swe.State.from_workload(mesh, p0, w)
+            oh, ohu, ohv = w.h, w.hu, w.hv
+            el, done, growth = 0.0, 0, []
+            for mark in [c for c in (25, 50, 100, 200, 500, 1000, 2000) if c < o_steps] + [o_steps]:
+                t0 = time.perf_counter()
+                oh, ohu, ohv, dts, _ = oracle.run(om, o, w.z, w.nman, oh, ohu, ohv, mark - done, q_in=w.q_in,
+                                                  level=w.level)
+                el += time.perf_counter() - t0
+                done = mark
+                st.step_dt(dts)
+                gh, ghu, ghv = st.get_state()
+                growth.append({"steps": done, "l1_h": rel_l1(gh, oh), "l1_hu": rel_l1(ghu, ohu),
+                               "l1_hv": rel_l1(ghv, ohv)})
+            st.close()
+            s1 = min(o_steps, 20)
+            o1 = oracle.opts(scheme, h_eps=p0.h_eps, r_eps=p0.r_eps, cfl=args.cfl, threads=1)
+            t0 = time.perf_counter()
+            oracle.run(om, o1, w.z, w.nman, w.h, w.hu, w.hv, s1, q_in=w.q_in, level=w.level)
+            el1 = time.perf_counter() - t0
+            row["oracle"] = {"steps": o_steps, "cores": cores, "value": n * o_steps / el, "unit": UNIT,
+                             "one_core": {"steps": s1, "value": n * s1 / el1}}
+            qs = max(np.abs(ohu).max(), np.abs(ohv).max(), 1e-300)
+            cx = w.centroids()[0]
+            # wetting front: the largest along-valley x of the cells that were dry at t = 0 and now
+            # hold more than 1 mm (NaN while the flow has wetted none)
+            front = lambda hh: float(cx[(hh > 1e-3) & (w.h <= 0.0)].max()) if ((hh > 1e-3) & (w.h <= 0.0)).any() \
+                else float("nan")
+            row["front_x"] = {"gpu": front(gh), "oracle": front(oh), "steps": o_steps}
+            row["error_vs_oracle"] = {"precision": precisions[0], "steps": o_steps, "l1_h": rel_l1(gh, oh),
+                                      "linf_h": rel_inf(gh, oh), "l1_hu": rel_l1(ghu, ohu), "l1_hv": rel_l1(ghv, ohv),
+                                      "linf_q": float(max(np.abs(ghu - ohu).max(), np.abs(ghv - ohv).max()) / qs),
+                                      "growth": growth}
+            print(json.dumps(row), flush=True)
+        mesh.close()
 
 
 def main():
@@ -674,6 +765,9 @@ def main():
     ap.add_argument("--time-error", action="store_true",
                     help="GPU time against L2 error on the paper's dam break, 20k-600k cells, all schemes")
     ap.add_argument("--members", type=int, default=64)
+    ap.add_argument("--configs", action="store_true",
+                    help="every workload configuration at full size: GPU and FP64 oracle throughput, GPU vs oracle")
+    ap.add_argument("--config", type=int, action="append", help="with --configs: only this configuration")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -683,6 +777,8 @@ def main():
         run_ensemble(args)
     elif args.time_error:
         run_time_error(args)
+    elif args.configs:
+        run_configs(args)
     else:
         run_gpu(args)
 

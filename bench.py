@@ -500,14 +500,14 @@ def fp64_comparison(args, mesh, w, swe, torch):
 
 
 def cpu_baseline(w, n):
-    """The FP64 oracle as it stands, on the host cores: 10 steps of the full mesh on all cores and
+    """The FP64 oracle as it stands, on the host cores: 20 steps of the full mesh on all cores and
     one step on one core (bounded samples)."""
     import oracle
     import platform
     oracle.build()
     om = oracle.Mesh(w.nodes, w.tris, w.bnd_edges, w.bnd_tag)
     cores = os.cpu_count() or 1
-    steps = 10
+    steps = 20
     t0 = time.perf_counter()
     oracle.run(om, oracle.opts("muscl", threads=cores), w.z, w.nman, w.h, w.hu, w.hv, steps, q_in=w.q_in,
                level=w.level)

@@ -2,8 +2,8 @@
 
 13,004,160-cell river (the benchmark): the oracle can afford one full-mesh
 step, so the FP64 path is compared with it cell by cell (one step, 1e-12).
-The FP32 benchmark configuration (split kernels, block 256, CUDA graphs,
-CFL 0.9) is checked through properties that hold at any size: its one-step
+The FP32 benchmark configuration (split kernels, flux blocks of 256 and
+prep blocks of 128 threads, CUDA graphs, CFL 0.9) is checked through properties that hold at any size: its one-step
 result against the same oracle step (same h_eps), the mass budget, and that
 the fused kernel gives the same bits.
 
@@ -64,7 +64,7 @@ def test_fp64_one_step_matches_oracle_at_full_size(river13m):
 
 def test_fp32_bench_configuration_at_full_size(river13m):
     w, mesh, om = river13m
-    p = swe.swe_params_default("muscl", "fp32")           # split kernels, block 256: the benchmark's path
+    p = swe.swe_params_default("muscl", "fp32")           # the benchmark's path: split kernels, flux block 256, prep 128
     st = swe.State.from_workload(mesh, p, w)
     m0 = st.mass()[0]
     st.step(1, 0.9)

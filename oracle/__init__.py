@@ -38,7 +38,7 @@ class _Opts(C.Structure):
     _fields_ = [("scheme", C.c_int), ("time_scheme", C.c_int), ("waf_limiter", C.c_int),
                 ("threads", C.c_int), ("g", C.c_double), ("h_eps", C.c_double),
                 ("r_eps", C.c_double), ("cfl", C.c_double), ("cfl_local", C.c_int),
-                ("beta", C.c_double), ("hr_order", C.c_int)]
+                ("beta", C.c_double), ("hr_order", C.c_int), ("waf_surface", C.c_int)]
 
 
 def _load():
@@ -70,10 +70,12 @@ def _p(a):
 
 
 def opts(scheme="hllc", time_scheme="euler", waf_limiter="superbee", g=9.81, h_eps=1e-6,
-         r_eps=1e-12, cfl=0.9, threads=0, cfl_mode="global", beta=2.0, hr_order=1) -> _Opts:
+         r_eps=1e-12, cfl=0.9, threads=0, cfl_mode="global", beta=2.0, hr_order=1,
+         waf_ratio="depth") -> _Opts:
     return _Opts(SCHEMES[scheme], {"euler": 0, "heun": 1}[time_scheme],
                  {"superbee": 0, "phi1": 1, "phi0": 2}[waf_limiter], threads,
-                 g, h_eps, r_eps, cfl, {"global": 0, "local": 1}[cfl_mode], beta, hr_order)
+                 g, h_eps, r_eps, cfl, {"global": 0, "local": 1}[cfl_mode], beta, hr_order,
+                 {"depth": 0, "surface": 1}[waf_ratio])
 
 
 class Mesh:

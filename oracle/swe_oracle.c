@@ -73,6 +73,10 @@
  *      the side's cell, the other cell or one of its upwind cells is dry;
  *      boundary edges use the cell-centre values.  HR, Riemann flux and
  *      update are those of the other schemes.
+ *  R17 WAF ratio on the free surface (an option; Sec. 6.2.2 takes the depth):
+ *      r_L and r_R use eta = h + z for the cell values and the upwind means,
+ *      so that the limiter sees waves and not the bed; on a flat bed it is
+ *      the depth ratio exactly.
  */
 #include "swe_oracle.h"
 
@@ -628,16 +632,17 @@ static void face_values(const om_mesh *m, const om_opts *o, const work_t *w, con
     }
 }
 
-/* mean of h and of the velocity over the two other neighbours of cell i
- * (its edges k+1 and k+2); a missing neighbour stands in with cell i (R4) */
-static void upwind_means(const om_mesh *m, const work_t *w, const double *h, int64_t i, int k,
+/* mean of q and of the velocity over the two other neighbours of cell i
+ * (its edges k+1 and k+2); a missing neighbour stands in with cell i (R4).
+ * q is the depth h, or the free surface eta with the option of R17. */
+static void upwind_means(const om_mesh *m, const work_t *w, const double *q, int64_t i, int k,
                          double *hm, double *um, double *vm)
 {
     double sh = 0, su = 0, sv = 0;
     for (int d = 1; d <= 2; d++) {
         int32_t j = m->nbr[3 * i + (k + d) % 3];
         int64_t c = j >= 0 ? j : i;
-        sh += h[c]; su += w->u[c]; sv += w->v[c];
+        sh += q[c]; su += w->u[c]; sv += w->v[c];
     }
     *hm = sh / 2.0; *um = su / 2.0; *vm = sv / 2.0;
 }
@@ -767,11 +772,12 @@ static void euler_stage(const om_mesh *m, const om_opts *o, work_t *w,
                 double out[4];
                 if (scheme == 2) {
                     double hma, uma, vma, hmb, umb, vmb;
-                    upwind_means(m, w, h, a, ka, &hma, &uma, &vma);
-                    upwind_means(m, w, h, b, kb, &hmb, &umb, &vmb);
+                    const double *q = o->waf_surface ? w->eta : h;     /* R17 */
+                    upwind_means(m, w, q, a, ka, &hma, &uma, &vma);
+                    upwind_means(m, w, q, b, kb, &hmb, &umb, &vmb);
                     double ddx = m->cx[b] - m->cx[a], ddy = m->cy[b] - m->cy[a];
                     double wf[8] = {dt / sqrt(ddx * ddx + ddy * ddy), hma, hmb,
-                                    -uma * cny + vma * cnx, -umb * cny + vmb * cnx, h[a], h[b], 0.0};
+                                    -uma * cny + vma * cnx, -umb * cny + vmb * cnx, q[a], q[b], 0.0};
                     edge_flux(o, scheme, in, wf, out);
                 } else {
                     edge_flux(o, scheme, in, NULL, out);

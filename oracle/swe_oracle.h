@@ -64,6 +64,8 @@ typedef struct {
     double beta;       /* scheme 3: limiter parameter (1 MINBEE, 2 SUPERBEE) */
     int hr_order;      /* scheme 1: 1 hydrostatic reconstruction on the cell bed (R6),
                           2 second order with a linear bed in each cell (R16) */
+    int waf_surface;   /* scheme 2: 0 the ratio r_L, r_R on the depth h (Sec. 6.2.2),
+                          1 on the free surface eta (R17) */
 } om_opts;
 
 /* Advance n_steps.  h,hu,hv are updated in place.  dt_given (length n_steps)

@@ -632,3 +632,71 @@ def test_fixed_level_boundary_fills_to_its_level():
     assert d["t"] > 100.0
     assert np.abs(h - 1.1).max() < 2e-3
     assert math.isclose(m.mass(h) - m.mass(w.h), d["boundary_in"], rel_tol=1e-10)
+
+
+# --------------------------------------------------------------------------
+# WAF ratio on the free surface (R17, an option next to the paper's depth ratio)
+# --------------------------------------------------------------------------
+
+def test_waf_surface_ratio_is_the_depth_ratio_on_a_flat_bed():
+    """With z = 0 the free surface is the depth, so both ratios give the same bits (1D dam break
+    and the 2D circular dam break)."""
+    for w, steps in ((W.dam_break_1d(60, 6, 10.0, 1.0, 1.0, 0.5, x_dam=5.0), 120),
+                     (W.circular_dam_break(n=16, radius=6.0, half=16.0), 60)):
+        assert not w.z.any()
+        m = _mesh(w)
+        a = oracle.run(m, oracle.opts("waf"), w.z, w.nman, w.h, w.hu, w.hv, steps)
+        b = oracle.run(m, oracle.opts("waf", waf_ratio="surface"), w.z, w.nman, w.h, w.hu, w.hv, steps)
+        for x, y in zip(a[:3], b[:3]):
+            assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("bc", ["wall", "level", "open"])
+def test_waf_surface_ratio_keeps_a_lake_at_rest(bc):
+    w = W.partial_dam_break(nx=40, ny=20, spacing=1.0, n_gauss=20, breach=False, seed=9)
+    kind = {"wall": W.WALL, "level": W.LEVEL, "open": W.OPEN}[bc]
+    w.bnd_tag = np.full(len(w.bnd_edges), W.tag(kind), np.int32)
+    m = _mesh(w, cut=False)
+    h, hu, hv, *_ = oracle.run(m, oracle.opts("waf", waf_ratio="surface"), w.z, w.nman, w.h, w.hu, w.hv,
+                               300, level=[2.0])
+    assert np.array_equal(h, w.h) and not hu.any() and not hv.any()
+
+
+def test_waf_surface_ratio_conserves_mass_rotates_and_differs_over_a_bed():
+    w = W.partial_dam_break(nx=40, ny=20, spacing=1.0, n_gauss=20, seed=9)
+    m = _mesh(w)
+    o = oracle.opts("waf", waf_ratio="surface")
+    h, hu, hv, dts, d = oracle.run(m, o, w.z, w.nman, w.h, w.hu, w.hv, 300)
+    m0 = m.mass(w.h)
+    assert abs(m.mass(h) - m0 - d["clipped"]) <= 1e-13 * m0
+    hd, *_ = oracle.run(m, oracle.opts("waf"), w.z, w.nman, w.h, w.hu, w.hv, 300, dt=dts)
+    assert np.abs(h - hd).max() > 1e-6                  # over a bed the two ratios differ
+    w = W.partial_dam_break(nx=24, ny=12, spacing=1.0, n_gauss=8, seed=5)
+    w.hu = 0.1 * w.h
+    m = _mesh(w)
+    rot = np.stack([-w.nodes[:, 1], w.nodes[:, 0]], axis=1)
+    mr = oracle.Mesh(rot, w.tris, w.bnd_edges, w.bnd_tag, w.cut_edges)
+    a = oracle.run(m, o, w.z, w.nman, w.h, w.hu, w.hv, 20)
+    b = oracle.run(mr, o, w.z, w.nman, w.h, -w.hv, w.hu, 20)
+    assert np.abs(a[0] - b[0]).max() < 1e-13
+    assert np.abs(a[1] - b[2]).max() < 1e-12 and np.abs(a[2] + b[1]).max() < 1e-12
+
+
+def test_waf_surface_ratio_stays_bounded_where_the_depth_ratio_does_not():
+    """River of 30,000 cells, 2000 WAF-SUPERBEE steps: with the paper's depth ratio the limiter
+    reacts to the steep channel banks and the speed next to the inflow passes 20 m/s (about 50 by
+    step 1600); with the free-surface ratio it stays below 10 m/s (about 4) over the whole run."""
+    w = W.river(200, 75)
+    m = _mesh(w)
+    worst = {}
+    for ratio in ("depth", "surface"):
+        o = oracle.opts("waf", h_eps=1e-4, r_eps=1e-6, waf_ratio=ratio)
+        h, hu, hv = w.h, w.hu, w.hv
+        worst[ratio] = 0.0
+        for _ in range(20):
+            h, hu, hv, dts, d = oracle.run(m, o, w.z, w.nman, h, hu, hv, 100, q_in=w.q_in, level=w.level)
+            u = np.where(h > 1e-4, np.hypot(hu, hv) / np.maximum(h, 1e-300), 0.0)
+            worst[ratio] = max(worst[ratio], float(u.max()))
+            if worst[ratio] > 20.0:
+                break
+    assert worst["depth"] > 20.0 and worst["surface"] < 10.0, worst

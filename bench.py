@@ -678,7 +678,8 @@ def run_configs(args):
         (2, "partial dam break over Gaussian bathymetry, 1000x500 jittered grid", lambda: W.partial_dam_break(),
          ["muscl", "waf"], ["fp64"], 1000, 1000),
         (3, "river 4160x1563 jittered grid", lambda: W.river(), ["muscl"], ["fp32", "fp64"], 2000, 20),
-        (4, "river 2310x866 jittered grid", lambda: W.river(2310, 866), ["waf", "muscl"], ["fp32"], 2000, 2000),
+        (4, "river 2310x866 jittered grid", lambda: W.river(2310, 866), ["waf", "waf:surface", "muscl"], ["fp32"],
+         2000, 2000),
     ]
     for cid, name, make, schemes, precisions, steps, o_steps in cfgs:
         if args.config and cid not in args.config:
@@ -687,10 +688,13 @@ def run_configs(args):
         mesh = swe.Mesh.from_workload(w, "morton")
         om = oracle.Mesh(w.nodes, w.tris, w.bnd_edges, w.bnd_tag, w.cut_edges)
         n = mesh.n
-        for scheme in schemes:
-            row = {"config": cid, "workload": name, "cells": n, "scheme": scheme, "steps": steps, "gpu": {}}
+        for label in schemes:
+            # "waf:surface": WAF with its ratios on the free surface (an option next to the paper's depth)
+            scheme, opt = (label.split(":") + [""])[:2]
+            kw = {"waf_ratio": "surface"} if opt == "surface" else {}
+            row = {"config": cid, "workload": name, "cells": n, "scheme": label, "steps": steps, "gpu": {}}
             for precision in precisions:
-                p = swe.swe_params_default(scheme, precision)
+                p = swe.swe_params_default(scheme, precision, **kw)
                 st = swe.State.from_workload(mesh, p, w)
                 st.step(24, args.cfl)              # captures the 24-step graph that the timed run replays
                 torch.cuda.synchronize()
@@ -703,8 +707,8 @@ def run_configs(args):
                 row["gpu"][precision] = {"ms_per_step": ms / steps, "value": n * steps / (ms / 1e3), "unit": UNIT}
                 st.close()
             # the oracle with the GPU's thresholds of the first precision named (same algorithm)
-            p0 = swe.swe_params_default(scheme, precisions[0])
-            o = oracle.opts(scheme, h_eps=p0.h_eps, r_eps=p0.r_eps, cfl=args.cfl, threads=cores)
+            p0 = swe.swe_params_default(scheme, precisions[0], **kw)
+            o = oracle.opts(scheme, h_eps=p0.h_eps, r_eps=p0.r_eps, cfl=args.cfl, threads=cores, **kw)
             # the oracle in chunks; after each the GPU replays the chunk's time steps and the two
             # are compared (how far they drift apart with the number of steps)
             st = swe.State.from_workload(mesh, p0, w)
@@ -722,7 +726,7 @@ def run_configs(args):
                                "l1_hv": rel_l1(ghv, ohv)})
             st.close()
             s1 = min(o_steps, 20)
-            o1 = oracle.opts(scheme, h_eps=p0.h_eps, r_eps=p0.r_eps, cfl=args.cfl, threads=1)
+            o1 = oracle.opts(scheme, h_eps=p0.h_eps, r_eps=p0.r_eps, cfl=args.cfl, threads=1, **kw)
             t0 = time.perf_counter()
             oracle.run(om, o1, w.z, w.nman, w.h, w.hu, w.hv, s1, q_in=w.q_in, level=w.level)
             el1 = time.perf_counter() - t0
@@ -735,6 +739,9 @@ def run_configs(args):
             front = lambda hh: float(cx[(hh > 1e-3) & (w.h <= 0.0)].max()) if ((hh > 1e-3) & (w.h <= 0.0)).any() \
                 else float("nan")
             row["front_x"] = {"gpu": front(gh), "oracle": front(oh), "steps": o_steps}
+            speed = lambda hh, qx, qy: float(np.where(hh > 1e-3, np.hypot(qx, qy) / np.maximum(hh, 1e-300), 0.0).max())
+            row["max_speed"] = {"gpu": speed(gh, ghu, ghv), "oracle": speed(oh, ohu, ohv), "steps": o_steps,
+                                "unit": "m/s", "over": "cells deeper than 1 mm"}
             row["error_vs_oracle"] = {"precision": precisions[0], "steps": o_steps, "l1_h": rel_l1(gh, oh),
                                       "linf_h": rel_inf(gh, oh), "l1_hu": rel_l1(ghu, ohu), "l1_hv": rel_l1(ghv, ohv),
                                       "linf_q": float(max(np.abs(ghu - ohu).max(), np.abs(ghv - ohv).max()) / qs),

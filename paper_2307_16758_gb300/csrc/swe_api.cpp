@@ -183,6 +183,11 @@ template <typename T> struct StateT {
             swe_set_error("the boundary-first schedule runs the split kernels (clear the partition first)");
             return SWE_ERR_ARG;
         }
+        if (want_fused && (p.hr_order != 1 || p.waf_ratio != SWE_WAF_RATIO_DEPTH || p.scheme == SWE_SCHEME_MUSCL_EDGE)) {
+            swe_set_error("the fused kernel has neither the second-order reconstruction, the surface WAF ratio "
+                          "nor the paper's MUSCL");
+            return SWE_ERR_ARG;
+        }
         const int lim = want_fused ? fused_max_threads<T>(p.scheme) : split_max_threads<T>(p.scheme, p.hr_order == 2);
         if (lim <= 0) { swe_set_error("cannot query the kernels (no usable GPU?)"); return SWE_ERR_CUDA; }
         if (block <= 0 || block % 32 || block > lim) {
@@ -321,6 +326,7 @@ template <typename T> struct StateT {
         a.g = (T)p.g; a.h_eps = (T)p.h_eps; a.r_eps = (T)p.r_eps;
         a.beta = (T)p.muscl_beta;
         a.hr2 = p.hr_order == 2;
+        a.waf_surface = p.waf_ratio == SWE_WAF_RATIO_SURFACE;
         a.waf_limiter = p.waf_limiter;
         for (int q = 0; q < SWE_MAX_GROUPS; q++) { a.qlen[q] = qlen[q]; a.level[q] = level[q]; }
         return a;
@@ -505,7 +511,8 @@ template <typename T> std::vector<Candidate> candidates(const StateT<T> &S, cons
     const int ls = split_max_threads<T>(S.p.scheme, S.p.hr_order == 2);
     for (int b : {128, 256, 512})
         if (b <= ls) c.push_back({false, b});
-    if ((S.p.scheme == SWE_SCHEME_MUSCL || S.p.scheme == SWE_SCHEME_WAF) && m && !S.sched && S.p.hr_order == 1) {
+    if ((S.p.scheme == SWE_SCHEME_MUSCL || S.p.scheme == SWE_SCHEME_WAF) && m && !S.sched && S.p.hr_order == 1 &&
+        S.p.waf_ratio == SWE_WAF_RATIO_DEPTH) {
         const int lf = fused_max_threads<T>(S.p.scheme);
         for (int b : {128, 256})
             if (b <= lf) c.push_back({true, b});
@@ -819,7 +826,9 @@ bool valid_params(const swe_params *p)
            (p->cfl_mode == SWE_CFL_GLOBAL || p->cfl_mode == SWE_CFL_LOCAL) &&
            (p->scheme != SWE_SCHEME_MUSCL_EDGE || (p->muscl_beta >= 1.0 && p->muscl_beta <= 2.0)) &&
            (p->scheme != SWE_SCHEME_MUSCL_EDGE || p->kernel != SWE_KERNEL_FUSED) &&
-           (p->hr_order == 1 || (p->hr_order == 2 && p->scheme == SWE_SCHEME_MUSCL && p->kernel != SWE_KERNEL_FUSED));
+           (p->hr_order == 1 || (p->hr_order == 2 && p->scheme == SWE_SCHEME_MUSCL && p->kernel != SWE_KERNEL_FUSED)) &&
+           (p->waf_ratio == SWE_WAF_RATIO_DEPTH ||
+            (p->waf_ratio == SWE_WAF_RATIO_SURFACE && p->scheme == SWE_SCHEME_WAF && p->kernel != SWE_KERNEL_FUSED));
 }
 
 template <typename T>
@@ -928,6 +937,7 @@ int swe_params_default(swe_params *p, int scheme, int precision)
     p->cfl_mode = SWE_CFL_GLOBAL;
     p->muscl_beta = 2.0;
     p->hr_order = 1;
+    p->waf_ratio = SWE_WAF_RATIO_DEPTH;
     return SWE_OK;
 }
 

@@ -63,6 +63,7 @@ template <typename T> struct StepArgs {
     int n_list;                 //   (n_list of them) instead of 0..n-1
     int no_advance;             // 1: not the step's last flux launch (time is advanced by the last)
     int hr2;                    // 1: second-order hydrostatic reconstruction (linear bed, MUSCL)
+    int waf_surface;            // 1: WAF ratios on the free surface instead of the depth
     int waf_limiter;
     T qlen[SWE_MAX_GROUPS];     // inflow discharge per unit length [m^2/s]
     T level[SWE_MAX_GROUPS];    // fixed free-surface levels [m]

@@ -474,7 +474,9 @@ __device__ __forceinline__ void interior_edge(const StepArgs<T> &a, T dt, const 
         wi.hupL = UA.x; wi.hupR = UB.x;
         wi.vupL = -UA.y * cny + UA.z * cnx;
         wi.vupR = -UB.y * cny + UB.z * cnx;
-        wi.hcL = A.hc; wi.hcR = B.hc;
+        // the ratios' cell values: depth, or free surface (eta = h + z)
+        wi.hcL = a.waf_surface ? A.hc + A.zc : A.hc;
+        wi.hcR = a.waf_surface ? B.hc + B.zc : B.hc;
         fl = riemann<T, true>(hsA, unA, vtA, hsB, unB, vtB, g, h_eps, wi, a.waf_limiter, a.r_eps);
     } else {
         WafIn<T> wi{};

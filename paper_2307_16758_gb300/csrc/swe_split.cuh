@@ -148,12 +148,14 @@ __device__ __forceinline__ void prep_muscl_edge_cell(const StepArgs<T> &a, int i
 }
 
 // WAF: centre primitives P[i] = (h, u, v, z) and, per edge k, the mean of
-// (h, u, v) over the neighbours across edges k+1 and k+2 (a missing neighbour
-// stands in with the cell itself).
+// (q, u, v) over the neighbours across edges k+1 and k+2 (a missing neighbour
+// stands in with the cell itself); q is the depth h, or the free surface
+// eta = h + z when the ratios are taken on it.
 template <typename T>
 __device__ __forceinline__ void prep_waf_cell(const StepArgs<T> &a, int i, Vec4<T> *P, Vec4<T> *U)
 {
     T hi = a.h[i], ui, vi;
+    const T zi = a.m.z[i];
     primitives(hi, a.hu[i], a.hv[i], a.h_eps, ui, vi);
     T qh[3], qu[3], qv[3];
 #pragma unroll
@@ -161,14 +163,15 @@ __device__ __forceinline__ void prep_waf_cell(const StepArgs<T> &a, int i, Vec4<
         int nb = a.m.nbr[3 * i + k];
         if (nb >= 0) {
             int j = nb >> 3;
-            qh[k] = a.h[j];
-            primitives(qh[k], a.hu[j], a.hv[j], a.h_eps, qu[k], qv[k]);
+            const T hj = a.h[j];
+            primitives(hj, a.hu[j], a.hv[j], a.h_eps, qu[k], qv[k]);
+            qh[k] = a.waf_surface ? hj + a.m.z[j] : hj;
         } else {
-            qh[k] = hi; qu[k] = ui; qv[k] = vi;
+            qh[k] = a.waf_surface ? hi + zi : hi; qu[k] = ui; qv[k] = vi;
         }
     }
     Vec4<T> p;
-    p.x = hi; p.y = ui; p.z = vi; p.w = a.m.z[i];
+    p.x = hi; p.y = ui; p.z = vi; p.w = zi;
     P[i] = p;
 #pragma unroll
     for (int k = 0; k < 3; k++) {

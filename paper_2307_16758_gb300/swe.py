@@ -29,6 +29,7 @@ TIME_SCHEME = {"euler": 0, "heun": 1}
 WAF_LIMITER = {"superbee": 0, "phi1": 1, "phi0": 2}
 KERNEL = {"auto": 0, "split": 1, "fused": 2}
 CFL_MODE = {"global": 0, "local": 1}
+WAF_RATIO = {"depth": 0, "surface": 1}
 MAX_GROUPS = 16
 
 EXPORTED = [
@@ -55,7 +56,7 @@ class Params(C.Structure):
     _fields_ = [("scheme", C.c_int), ("precision", C.c_int), ("time_scheme", C.c_int),
                 ("waf_limiter", C.c_int), ("g", C.c_double), ("h_eps", C.c_double),
                 ("r_eps", C.c_double), ("kernel", C.c_int), ("block", C.c_int), ("cfl_mode", C.c_int),
-                ("muscl_beta", C.c_double), ("hr_order", C.c_int)]
+                ("muscl_beta", C.c_double), ("hr_order", C.c_int), ("waf_ratio", C.c_int)]
 
 
 class BcValues(C.Structure):
@@ -170,6 +171,8 @@ def swe_params_default(scheme="muscl", precision="fp32", **over) -> Params:
             v = KERNEL.get(v, v)
         elif k == "cfl_mode":
             v = CFL_MODE.get(v, v)
+        elif k == "waf_ratio":
+            v = WAF_RATIO.get(v, v)
         setattr(p, k, v)
     return p
 

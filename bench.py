@@ -38,6 +38,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "cell-updates/s MUSCL-HLLC 13M tri, FP32 vs FP64 at stated error; % HBM peak"
 UNIT = "cell-updates/s"
+SCHEME_NAMES = {"muscl": "MUSCL-HLLC", "muscl_edge": "edge-upwind MUSCL-HLLC", "hllc": "first-order HLLC",
+                "waf": "WAF-HLLC"}
 RIVER_GRID = (4160, 1563)
 SEED = 20230733
 
@@ -366,7 +368,7 @@ def run_gpu(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {
             "workload": f"river {grid[0]}x{grid[1]} jittered grid, {n} triangles, "
-                        f"{'MUSCL-HLLC' if args.scheme == 'muscl' else 'edge-upwind MUSCL-HLLC'} FP32 bulk "
+                        f"{SCHEME_NAMES[args.scheme]} FP32 bulk "
                         "(FP64 mass/time), Euler, CFL 0.9, Morton order"
                         + (", second-order hydrostatic reconstruction" if args.hr_order == 2 else ""),
             "cells": n, "scheme": args.scheme, "hr_order": args.hr_order, "precision": "fp32", "time_scheme": "euler", "kernel": kname,
@@ -758,8 +760,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cfl", type=float, default=0.9)
     ap.add_argument("--kernel", default="auto", choices=["auto", "split", "fused"])
-    ap.add_argument("--scheme", default="muscl", choices=["muscl", "muscl_edge"],
-                    help="MUSCL-HLLC with least-squares gradients (default) or the paper's edge-upwind MUSCL")
+    ap.add_argument("--scheme", default="muscl", choices=list(SCHEME_NAMES),
+                    help="MUSCL-HLLC with least-squares gradients (default), the paper's edge-upwind MUSCL, "
+                         "first-order HLLC or WAF-HLLC")
     ap.add_argument("--hr-order", type=int, default=1, choices=[1, 2],
                     help="hydrostatic reconstruction: 1 (cell bed) or 2 (linear bed; LSQ MUSCL only)")
     ap.add_argument("--fp64-steps", type=int, default=1000)

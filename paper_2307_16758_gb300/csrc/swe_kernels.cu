@@ -59,12 +59,14 @@ __global__ void k_prep_waf(StepArgs<T> a, Vec4<T> *P, Vec4<T> *U)
     if (i < a.m.n) prep_waf_cell(a, i, P, U);
 }
 
-// Register cap of the FP32 MUSCL flux kernels: 48 registers fit five
-// 256-thread blocks per SM without spills (the other instances are left to
-// the compiler, which would spill under the same cap).
+// Register cap of the FP32 flux kernels: 48 registers fit five 256-thread
+// blocks per SM.  MUSCL fits without spills; HLLC (69 registers uncapped,
+// three blocks) spills 4 bytes and runs 0.362 against 0.395 ms on the 13M
+// river, WAF (72) spills 64 bytes and runs 0.515 against 0.606 ms.  The FP64
+// instances are bound by the FP64 units and left to the compiler.
 template <typename T, int SCHEME> constexpr int flux_maxnreg()
 {
-    return sizeof(T) == 4 && face_scheme(SCHEME) ? 48 : 255;
+    return sizeof(T) == 4 ? 48 : 255;
 }
 
 template <typename T, int SCHEME>

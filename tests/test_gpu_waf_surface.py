@@ -112,3 +112,13 @@ def test_bounded_speeds_on_a_river():
     st.close()
     m.close()
     assert worst < 10.0, worst
+
+
+def test_autotune_stays_on_the_split_kernels():
+    w = W.river(90, 34, seed=7, q_in=3000.0)
+    m = swe.Mesh.from_workload(w)
+    a = swe.State.from_workload(m, swe.swe_params_default("waf", "fp32", **S), w)
+    kernel, block, ms = a.autotune(m, trial_steps=4)
+    assert kernel == "split" and ms > 0
+    a.close()
+    m.close()

@@ -561,6 +561,7 @@ def run_ensemble(args):
     e1.synchronize()
     ms_separate = e0.elapsed_time(e1) / args.steps
     ens.sync()
+    wet = sum(int((st.get_state()[0] > p.h_eps).sum()) for st in states) / n     # prep's bytes depend on it
     # per-member FP32 error against the FP64 GPU path at matched time
     m_steps = min(args.fp64_steps, 200)
     errs = []
@@ -588,7 +589,23 @@ def run_ensemble(args):
                               "launches_per_step": len(ws) * 2},
         "autotune_ms_per_step": tune_ms,
         "error_fp32_vs_fp64_l1_h": {"steps": m_steps, "max": max(errs), "median": float(np.median(errs))},
+        # the whole batched step against the HBM copy rate: prep's and flux's algorithmic bytes per cell
+        "roofline": ensemble_roofline(kernel, n, ms_batched, wet),
     }))
+
+
+def ensemble_roofline(kernel, n, ms, wet):
+    """The batched step's algorithmic bytes per cell-update over its time: flux 116 B; prep 100 B for a
+    wet cell and 56 B for a dry one (which reads only its depth and bed), at the members' wet fraction."""
+    peak, src = measured_peaks()
+    if kernel == "fused":
+        per_cell = float(algo_bytes("fused", "muscl", "fp32"))
+    else:
+        per_cell = algo_bytes("flux", "muscl", "fp32") + 56.0 + (algo_bytes("prep", "muscl", "fp32") - 56.0) * wet
+    achieved = per_cell * n / (ms / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": "the batched step (all launches)", "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "traffic": None, "peak_source": src,
+            "algo_bytes_per_cell": per_cell, "wet_fraction": wet}
 
 
 def run_time_error(args):

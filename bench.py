@@ -382,7 +382,8 @@ def run_gpu(args):
                      "algo_bytes_per_cell": algo_bytes(dom, args.scheme, "fp32"),
                      "kernel_ms": dom_ms, "per_kernel_ms": {k: v[0] / v[1] for k, v in prof.items()},
                      "step_ideal_bytes_per_cell": step_bytes_ideal(args.scheme, "fp32"),
-                     "step_frac_of_ideal": step_ideal / peak},
+                     "step_frac_of_ideal": step_ideal / peak,
+                     "step_split": split_step_roofline(args.scheme, kname, st, p32.h_eps, n, step_ms, peak)},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "clocks": clocks,
@@ -592,6 +593,19 @@ def run_ensemble(args):
         # the whole batched step against the HBM copy rate: prep's and flux's algorithmic bytes per cell
         "roofline": ensemble_roofline(kernel, n, ms_batched, wet),
     }))
+
+
+def split_step_roofline(scheme, kname, st, h_eps, n, step_ms, peak):
+    """The whole step of the split kernels against the HBM copy rate: the sum of the kernels'
+    algorithmic bytes per cell-update (MUSCL prep: 100 B for a wet cell, 56 B for a dry one, at the
+    state's wet fraction) over the step time."""
+    if kname != "split" or scheme not in ("muscl", "muscl_edge"):
+        return None
+    h = st.get_state()[0]
+    wet = float((h > h_eps).mean())
+    per_cell = algo_bytes("flux", scheme, "fp32") + 56.0 + (algo_bytes("prep", scheme, "fp32") - 56.0) * wet
+    achieved = per_cell * n / (step_ms / 1e3) / 1e9
+    return {"algo_bytes_per_cell": per_cell, "wet_fraction": wet, "achieved": achieved, "frac": achieved / peak}
 
 
 def ensemble_roofline(kernel, n, ms, wet):

@@ -688,8 +688,9 @@ def run_time_error(args):
 
 
 def run_configs(args):
-    """Every configuration of the workload list at its full size: GPU throughput (CFL steps in CUDA
-    graphs, device events) in the precisions each one names, and the FP64 oracle on the host cores,
+    """The CPU-baseline leg for every configuration of the workload list at its full size: GPU
+    throughput (CFL steps in CUDA graphs, device events) in the precisions each one names, and the
+    FP64 oracle timed on the host cores,
     all cores and one core, over the full step count (the 13M river: 20 steps; one core: at most 20
     steps), with the GPU result after the oracle's steps (its time steps replayed) against the
     oracle's, at checkpoints along the run.  One JSON line per configuration and scheme."""

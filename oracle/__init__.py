@@ -1,7 +1,8 @@
 """FP64 CPU oracle for the shallow-water finite-volume step (test infrastructure).
 
-Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
-``bench.py`` import this package.  The product library never calls it.  The
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline legs of
+``bench.py`` (the default run's baseline, ``--impl reference`` and the
+per-configuration study ``--configs``) import this package.  The product library never calls it.  The
 oracle is plain C (``swe_oracle.c``) compiled with gcc into an in-tree shared
 library and called through ctypes.  Arrays are numpy, in the caller's cell
 order.

@@ -67,3 +67,18 @@ def test_single_process_needs_no_group():
     import bench
     value, ms = bench.job_throughput(500, 4, 2.0)
     assert ms == 2.0 and value == pytest.approx(500 * 4 / 2e-3)
+
+
+def test_step_byte_counts_follow_the_wet_fraction():
+    """Host arithmetic of the bench's whole-step figures: the split step moves the flux kernel's
+    116 B plus prep's 56 B (dry) to 100 B (wet) per cell; the fused kernel 68 B."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.algo_bytes("flux", "muscl", "fp32") == 116 and bench.algo_bytes("prep", "muscl", "fp32") == 100
+    assert bench.algo_bytes("fused", "muscl", "fp32") == 68 and bench.algo_bytes("flux", "hllc", "fp32") == 68
+    for wet, per_cell in ((0.0, 172.0), (0.5, 194.0), (1.0, 216.0)):
+        r = bench.ensemble_roofline("split", 1_000_000, 1.0, wet)
+        assert r["algo_bytes_per_cell"] == per_cell
+        assert abs(r["achieved"] - per_cell * 1e6 / 1e-3 / 1e9) < 1e-9 and abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
+    assert bench.ensemble_roofline("fused", 10, 1.0, 0.3)["algo_bytes_per_cell"] == 68.0

@@ -61,3 +61,22 @@ def test_bad_part_counts_are_rejected():
             swe.Partition(m, k)
         assert e.value.code == -1
     m.close()
+
+
+def test_one_cell_per_part():
+    """The degenerate split: every cell its own sub-domain (halo1 = its neighbours, every cell on a
+    boundary list)."""
+    w = W.dam_break_1d(4, 2, 4.0, 2.0)
+    m = swe.Mesh.from_workload(w, "morton")
+    nbr = m.export()["nbr"]
+    n = m.n
+    part = swe.Partition(m, n)
+    for p in range(n):
+        a, b, n1, n2, nb = part.info(p)
+        assert (a, b) == (p, p + 1)
+        h1, h2, bnd = part.export(p)
+        e1, e2 = _brute(nbr, a, b)
+        assert h1.tolist() == e1 and h2.tolist() == e2
+        assert bnd.tolist() == [p]
+    part.close()
+    m.close()

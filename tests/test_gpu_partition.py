@@ -94,3 +94,15 @@ def test_unsupported_configurations_are_rejected():
     other.close()
     part.close()
     m.close()
+
+
+@pytest.mark.parametrize("scheme", ["hllc", "muscl", "waf"])
+def test_one_cell_per_part_same_bits(scheme):
+    """The degenerate schedule: every cell its own sub-domain, every cell a boundary cell."""
+    w = W.dam_break_1d(8, 2, 8.0, 2.0, 1.0, 0.5, x_dam=4.0)
+    (ref, t_ref, _), *_ = _run(w, scheme, "fp64", 0, steps=30)
+    n = 2 * 8 * 2
+    (got, t_got, _), *_ = _run(w, scheme, "fp64", n, steps=30)
+    for a, b in zip(got, ref):
+        assert np.array_equal(a, b)
+    assert t_got == t_ref

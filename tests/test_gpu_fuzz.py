@@ -51,3 +51,20 @@ def test_random_problem_fp64_matches_the_oracle(seed):
     assert np.isfinite(o["h"]).all() and (o["h"] >= 0).all()
     g = run_gpu(w, scheme, dt=o["dts"])
     assert max(state_errors(g, o)) <= 1e-9, (scheme, w.n_cells)
+
+
+OPTIONS = [("muscl", dict(hr_order=2)), ("waf", dict(waf_ratio="surface")), ("muscl", dict(time_scheme="heun")),
+           ("hllc", dict(time_scheme="heun")), ("muscl_edge", dict(beta=1.0)), ("waf", dict(waf_limiter="phi1"))]
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_problem_with_options_fp64_matches_the_oracle(seed):
+    """The same random problems with the options: second-order hydrostatic reconstruction, the WAF ratio
+    on the free surface, Heun steps, the paper's MUSCL with the MINBEE limiter, WAF without limiting."""
+    w, _ = random_problem(100 + seed)
+    scheme, kw = OPTIONS[seed % len(OPTIONS)]
+    gkw = {("muscl_beta" if k == "beta" else k): v for k, v in kw.items()}
+    o = run_oracle(w, scheme, steps=15, **kw)
+    assert np.isfinite(o["h"]).all()
+    g = run_gpu(w, scheme, dt=o["dts"], **gkw)
+    assert max(state_errors(g, o)) <= 1e-9, (scheme, kw, w.n_cells)

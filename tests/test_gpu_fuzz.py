@@ -68,3 +68,16 @@ def test_random_problem_with_options_fp64_matches_the_oracle(seed):
     assert np.isfinite(o["h"]).all()
     g = run_gpu(w, scheme, dt=o["dts"], **gkw)
     assert max(state_errors(g, o)) <= 1e-9, (scheme, kw, w.n_cells)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_problem_fp32_stays_close_to_the_oracle(seed):
+    """The FP32 path on the random problems (the oracle with FP32's dry and ratio thresholds): after 15
+    replayed steps the relative L1 differences stay at the FP32 rounding level, 1e-5 for h and 1e-4
+    for the discharges."""
+    from gpu_common import rel_l1
+    w, scheme = random_problem(200 + seed)
+    o = run_oracle(w, scheme, steps=15, h_eps=1e-4, r_eps=1e-6)
+    g = run_gpu(w, scheme, "fp32", dt=o["dts"])
+    assert rel_l1(g["h"], o["h"]) <= 1e-5, (scheme, w.n_cells)
+    assert rel_l1(g["hu"], o["hu"]) <= 1e-4 and rel_l1(g["hv"], o["hv"]) <= 1e-4, (scheme, w.n_cells)

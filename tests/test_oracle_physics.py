@@ -700,3 +700,169 @@ def test_waf_surface_ratio_stays_bounded_where_the_depth_ratio_does_not():
             if worst[ratio] > 20.0:
                 break
     assert worst["depth"] > 20.0 and worst["surface"] < 10.0, worst
+
+
+# --------------------------------------------------------------------------
+# WAF limiter path (Sec. 6.2.2): the SUPERBEE A(r, c) branches and the
+# upwind changes of the ratios, against Toro's TVD WAF written in sum form
+# --------------------------------------------------------------------------
+
+def _phi_superbee(r):
+    """SUPERBEE as a flux limiter, max(0, min(2r, 1), min(r, 2)) (Toro's form, not the branch table)."""
+    return max(0.0, min(2.0 * r, 1.0), min(r, 2.0))
+
+
+def _hll_speeds_paper(hL, uL, hR, uR, g=G):
+    """Wave-speed estimates of Sec. 6.2.1 (p_k read as sqrt(h*(h*+h_k)/2)/h_k, reading R1), wet states."""
+    aL, aR = math.sqrt(g * hL), math.sqrt(g * hR)
+    h0 = 0.5 * (hL + hR) - 0.25 * (uR - uL) * (hL + hR) / (aL + aR)
+    if h0 <= min(hL, hR):
+        hs = (0.5 * (aL + aR) + 0.25 * (uL - uR)) ** 2 / g
+    else:
+        gk = [math.sqrt(g * (h0 + hk) / (2.0 * h0 * hk)) for hk in (hL, hR)]
+        hs = (hL * gk[0] + hR * gk[1] + uL - uR) / (gk[0] + gk[1])
+    p = [math.sqrt(hs * (hs + hk) / 2.0) / hk if hs > hk else 1.0 for hk in (hL, hR)]
+    SL, SR = uL - aL * p[0], uR + aR * p[1]
+    Ss = (SL * hR * (uR - SR) - SR * hL * (uL - SL)) / (hR * (uR - SR) - hL * (uL - SL))
+    return SL, SR, Ss
+
+
+def _waf_sum_form(st, waf, phi=_phi_superbee, swap_upwind=False, g=G):
+    """TVD WAF flux (F1, F2, F3) in Toro's sum form: F = (G_L + G_R)/2 - 1/2 sum_k sgn(c_k) A_k dF_k
+    with dF_L = F_HLL - G_L and dF_R = G_R - F_HLL, A_k = 1 - (1 - |c_k|) phi(r_k); the third
+    component is F1 times the limited average of v across the shear wave.  r_k is the upwind
+    change over the local change of h (v for the shear wave), the upwind side being the side the
+    wave comes from (S_k >= 0: left, reading R4)."""
+    hL, uL, vL, hR, uR, vR = st[1], st[3], st[4], st[6], st[8], st[9]
+    dtdx, hupL, hupR, vupL, vupR, hcL, hcR = waf[:7]
+    SL, SR, Ss = _hll_speeds_paper(hL, uL, hR, uR, g)
+    GL = np.array([hL * uL, hL * uL * uL + 0.5 * g * hL * hL])
+    GR = np.array([hR * uR, hR * uR * uR + 0.5 * g * hR * hR])
+    UL, UR = np.array([hL, hL * uL]), np.array([hR, hR * uR])
+    if SL >= 0:
+        Fh = GL
+    elif SR <= 0:
+        Fh = GR
+    else:
+        Fh = (SR * GL - SL * GR + SL * SR * (UR - UL)) / (SR - SL)
+
+    def ratio(S, qL, qR, qupL, qupR):
+        loc = qR - qL
+        left = (S >= 0) != swap_upwind
+        return (qL - qupL if left else qupR - qR) / loc
+
+    def A(S, r):
+        c = S * dtdx
+        return math.copysign(1.0, c) if c != 0 else 1.0, 1.0 - (1.0 - abs(c)) * phi(r)
+
+    sL, AL = A(SL, ratio(SL, hcL, hcR, hupL, hupR))
+    sR, AR = A(SR, ratio(SR, hcL, hcR, hupL, hupR))
+    ss, As = A(Ss, ratio(Ss, vL, vR, vupL, vupR))
+    F = 0.5 * (GL + GR) - 0.5 * (sL * AL * (Fh - GL) + sR * AR * (GR - Fh))
+    F3 = F[0] * (0.5 * (vL + vR) - 0.5 * ss * As * (vR - vL))
+    return F[0], F[1], F3, (SL, SR, Ss)
+
+
+def _waf_cases(seed, n):
+    """Edge states spanning every SUPERBEE interval of r_L, r_R and r_*, subsonic and supersonic
+    waves of both directions, and |c| < 1; the upwind means are set so that each ratio hits a
+    chosen target interval."""
+    rng = np.random.default_rng(seed)
+    targets = [(-3.0, -0.05), (0.05, 0.45), (0.55, 0.95), (1.05, 1.95), (2.05, 6.0)]
+    cases = []
+    for i in range(n):
+        kind = i % 3                              # 0 subsonic, 1 supersonic right, 2 supersonic left
+        hL, hR = rng.uniform(0.3, 3.0), rng.uniform(0.3, 3.0)
+        if abs(hR - hL) < 0.05:
+            hR = hL + 0.1
+        if kind == 0:
+            uL, uR = rng.uniform(-1.5, 1.5), rng.uniform(-1.5, 1.5)
+        else:
+            s = 1.0 if kind == 1 else -1.0
+            uL, uR = s * rng.uniform(8.0, 12.0), s * rng.uniform(8.0, 12.0)
+        vL, vR = rng.uniform(-1, 1), rng.uniform(-1, 1)
+        if abs(vR - vL) < 0.05:
+            vR = vL + 0.1
+        SL, SR, Ss = _hll_speeds_paper(hL, uL, hR, uR)
+        smax = max(abs(SL), abs(SR), abs(Ss))
+        dtdx = rng.uniform(0.05, 0.95) / smax      # every |c| < 1
+        tL = targets[rng.integers(5)]
+        tR = targets[rng.integers(5)]
+        ts = targets[rng.integers(5)]
+        rL, rR, rs = rng.uniform(*tL), rng.uniform(*tR), rng.uniform(*ts)
+        loc = hR - hL
+        # the upwind mean that wave L reads is set from r_L; where wave R reads the other mean
+        # (subsonic), it is set from r_R
+        hupL, hupR = rng.uniform(0.3, 3.0), rng.uniform(0.3, 3.0)
+        if SL >= 0:
+            hupL = hL - rL * loc
+        else:
+            hupR = hR + rL * loc
+        if SR >= 0 and SL < 0:
+            hupL = hL - rR * loc
+        vloc = vR - vL
+        vupL, vupR = rng.uniform(-1, 1), rng.uniform(-1, 1)
+        if Ss >= 0:
+            vupL = vL - rs * vloc
+        else:
+            vupR = vR + rs * vloc
+        st = _state(hL, uL, vL, hR, uR, vR)
+        waf = np.array([dtdx, hupL, hupR, vupL, vupR, hL, hR, 0.0])
+        cases.append((st, waf))
+    return cases
+
+
+def test_waf_superbee_flux_equals_toro_sum_form():
+    """Sec. 6.2.2 with readings R3 and R4: the oracle's limited WAF flux equals Toro's TVD WAF in
+    sum form with SUPERBEE written as max(0, min(2r, 1), min(r, 2)), on states that put r_L, r_R
+    and r_* in each of SUPERBEE's five intervals, with subsonic and both supersonic wave patterns
+    and both signs of S_*.  A wrong coefficient in a branch of A(r, c), or an upwind change taken
+    from the wrong side, fails it (checked below on the test's own form)."""
+    o = oracle.opts("waf", waf_limiter="superbee")
+    hit = {k: set() for k in ("L", "R", "*")}
+    pattern = set()
+    for st, waf in _waf_cases(11, 600):
+        M, PL, PR, T = oracle.edge_flux(o, st, waf)
+        F1, F2, F3, (SL, SR, Ss) = _waf_sum_form(st, waf)
+        hL, hR = st[1], st[6]
+        scale = max(1.0, abs(F1), abs(F2))
+        assert abs(M - F1) <= 1e-12 * scale, (st, waf, M, F1)
+        assert abs(PL + 0.5 * G * hL * hL - F2) <= 1e-12 * scale, (st, waf)
+        assert abs(PR + 0.5 * G * hR * hR - F2) <= 1e-12 * scale, (st, waf)
+        assert abs(T - F3) <= 1e-12 * max(1.0, abs(F3)), (st, waf, T, F3)
+        pattern.add(("sub" if SL < 0 < SR else ("right" if SL >= 0 else "left"), Ss >= 0))
+        for key, S, qL, qR, qup in (("L", SL, hL, hR, (waf[1], waf[2])), ("R", SR, hL, hR, (waf[1], waf[2])),
+                                    ("*", Ss, st[4], st[9], (waf[3], waf[4]))):
+            r = (qL - qup[0] if S >= 0 else qup[1] - qR) / (qR - qL)
+            hit[key].add(0 if r <= 0 else 1 if r <= 0.5 else 2 if r <= 1 else 3 if r <= 2 else 4)
+    for key in hit:
+        assert hit[key] == {0, 1, 2, 3, 4}, (key, hit[key])
+    assert {("sub", True), ("sub", False), ("right", True), ("left", False)} <= pattern, pattern
+
+
+def test_waf_pin_has_power_against_plausible_mistakes():
+    """The sum-form check above would catch each plausible mistake: for every SUPERBEE branch
+    with a wrong coefficient, and for an upwind change taken from the wrong side, some case
+    moves the flux far beyond the 1e-12 tolerance."""
+    o = oracle.opts("waf", waf_limiter="superbee")
+    cases = _waf_cases(12, 300)
+    ref = [oracle.edge_flux(o, st, waf) for st, waf in cases]
+
+    def worst(**kw):
+        d = 0.0
+        for (st, waf), (M, PL, PR, T) in zip(cases, ref):
+            F1, F2, F3, _ = _waf_sum_form(st, waf, **kw)
+            d = max(d, abs(M - F1), abs(PL + 0.5 * G * st[1] ** 2 - F2), abs(T - F3))
+        return d
+
+    assert worst() < 1e-11
+    mutants = {
+        "swapped upwind side": dict(swap_upwind=True),
+        "0<r<=1/2 slope 1 instead of 2": dict(phi=lambda r: max(0.0, min(r, 1.0), min(r, 2.0))),
+        "1<r<=2 capped at 1": dict(phi=lambda r: max(0.0, min(2 * r, 1.0), min(r, 1.0))),
+        "r>2 capped at 1.5": dict(phi=lambda r: max(0.0, min(2 * r, 1.0), min(r, 1.5))),
+        "r<=0 not zero": dict(phi=lambda r: max(0.5 * r, min(2 * r, 1.0), min(r, 2.0)) if r <= 0
+                              else _phi_superbee(r)),
+    }
+    for name, kw in mutants.items():
+        assert worst(**kw) > 1e-6, name

@@ -45,8 +45,7 @@ enum {
     SWE_ERR_CUDA = -3,       /* a CUDA runtime call failed */
     SWE_ERR_DRY = -4,        /* CFL rule: no wet cell, no time step defined */
     SWE_ERR_NONFINITE = -5,  /* a non-finite depth or discharge was produced */
-    SWE_ERR_TIMEOUT = -6,    /* a bounded device wait gave up */
-    SWE_ERR_NOMEM = -7       /* host or device allocation failed */
+    SWE_ERR_NOMEM = -7       /* host or device allocation failed (-6 is unused) */
 };
 
 enum { SWE_WALL = 0, SWE_OPEN = 1, SWE_INFLOW = 2, SWE_LEVEL = 3 };
@@ -172,14 +171,26 @@ int swe_step_dt(swe_state *s, const double *dt, int n_steps);
 /* Wait for the stream and return the device status (SWE_OK or an error). */
 int swe_sync(swe_state *s);
 
-/* Copy the conserved variables to FP64 host arrays in the original order. */
+/* Copy the conserved variables U = (h, hu, hv) of Sec. 6.1 (cell averages of
+ * the finite-volume form) to FP64 host arrays in the original order. */
 int swe_get_state(swe_state *s, double *h, double *hu, double *hv);
-/* Sum of area*h in FP64 (deterministic, compensated), the mass added by
+/* Mass budget of the continuity equation (Sec. 6.1: integrated over the
+ * cells, sum |Omega_i| h_i changes only through the boundary fluxes):
+ * the sum of area*h in FP64 (deterministic, compensated), the mass added by
  * clipping negative depths and the net mass that entered through the
  * boundary since init (m^3).  Any output pointer may be NULL. */
 int swe_mass(swe_state *s, double *mass, double *clipped_mass, double *boundary_net_inflow);
-/* Simulated time (FP64 accumulation of the steps) and the number of steps. */
+/* Simulated time, the FP64 sum of the explicit Euler steps' dt (Sec. 6.1),
+ * and the number of steps. */
 int swe_time(swe_state *s, double *t, int64_t *steps);
+/* Flags of the state since init (waits for the stream): SWE_FLAG_CLIPPED
+ * when a negative depth was clipped to zero at least once (the wet/dry
+ * treatment of Sec. 6.2.3 keeps h >= 0; the mass added is in swe_mass) --
+ * a warning, not an error; SWE_FLAG_NONFINITE and SWE_FLAG_DRY when the
+ * device saw a non-finite value or no wet cell for the CFL rule (those also
+ * make the next synchronising call return an error). */
+enum { SWE_FLAG_CLIPPED = 1, SWE_FLAG_NONFINITE = 2, SWE_FLAG_DRY = 4 };
+int swe_flags(swe_state *s, int *flags);
 /* Device bytes held by the state and the kernel configuration in use. */
 int swe_state_info(const swe_state *s, int64_t *device_bytes, int *kernel, int *block);
 
@@ -229,17 +240,20 @@ int swe_fma_peak(int precision, int iters, void *stream, double *flops_per_s);
  *  ln[3n][2] scaled outward normals (lnx, lny; the centroid offsets of the
  *           gradient are derived from them), z[n] bed, manning_n[n] (may be
  *           NULL), h, hu, hv[n];
- *  p: scheme SWE_SCHEME_MUSCL and precision SWE_FP32 (g, h_eps, r_eps, block
- *     are used); inflow_qlen[n_inflow] inflow discharge per unit length
- *     (m^2/s) per group; level[n_level] fixed levels; stream a cudaStream_t.
- * Outputs h_out, hu_out, hv_out[n] (must not alias the inputs).
+ *  p: scheme SWE_SCHEME_MUSCL, precision SWE_FP32 and hr_order 1 (g, h_eps,
+ *     r_eps, block are used); inflow_qlen[n_inflow] inflow discharge per unit
+ *     length (m^2/s) per group; level[n_level] fixed levels; dt finite and
+ *     >= 0; stream a cudaStream_t.
+ * Outputs h_out, hu_out, hv_out[n]: no output may overlap another output or
+ * any input (else SWE_ERR_ARG).
  * The face values (48 bytes per cell) go to a scratch array compiled into
  * the library (about 12.6 MB per GPU, held until the process exits), so
  * n_cells must not exceed SWE_NOALLOC_MAX_CELLS (else SWE_ERR_ARG).  The
  * first call on a GPU looks the array up (cudaGetSymbolAddress) with that GPU
  * current: make it before any stream capture.  All calls on a GPU share the
- * array, so calls that overlap on the GPU race.  Asynchronous on `stream`;
- * no status is read back. */
+ * array, so calls that overlap on the GPU race.  Each call enqueues three
+ * kernels on `stream` (dt travels as a kernel argument, nothing is copied
+ * from the host) and returns without waiting; no status is read back. */
 #define SWE_NOALLOC_MAX_CELLS 262144
 int swe_muscl_step_noalloc(int64_t n_cells, const int32_t *nbr, const float *ln, const float *z,
                            const float *manning_n, const float *h, const float *hu,
@@ -304,7 +318,10 @@ int swe_halo_get(swe_state *s, int part, double *h, double *hu, double *hv);
  * queried (swe_get_state, swe_mass, swe_time) as usual. */
 int swe_ensemble_create(swe_state *const *members, int n_members, swe_ensemble **out);
 int swe_ensemble_destroy(swe_ensemble *e);
+/* Advance every member n_steps explicit steps, each with its own CFL time
+ * step dt = cfl * r_min / max_wet(sqrt(g h)+|u|) of Sec. 6.1 (asynchronous). */
 int swe_ensemble_step(swe_ensemble *e, int n_steps, double cfl);
+/* Wait for the members' stream and return the first member error, if any. */
 int swe_ensemble_sync(swe_ensemble *e);
 /* Autotune the members' common kernel configuration on the whole ensemble
  * (as swe_autotune; meshes[i] is member i's mesh, NULL for split kernels only). */

@@ -1158,6 +1158,19 @@ int swe_time(swe_state *s, double *t, int64_t *steps)
     })());
 }
 
+int swe_flags(swe_state *s, int *flags)
+{
+    if (!s || !flags) { swe_set_error("swe_flags: bad argument"); return SWE_ERR_ARG; }
+    return DISPATCH(s, ([&]() -> int {
+        DevScalars d;
+        int rc = S.read_scalars(d);
+        if (rc) return rc;
+        *flags = (d.clipped > 0.0 ? SWE_FLAG_CLIPPED : 0) | ((d.status & ST_NONFINITE) ? SWE_FLAG_NONFINITE : 0) |
+                 ((d.status & ST_DRY) ? SWE_FLAG_DRY : 0);
+        return SWE_OK;
+    })());
+}
+
 int swe_state_info(const swe_state *s, int64_t *device_bytes, int *kernel, int *block)
 {
     if (!s) { swe_set_error("swe_state_info: NULL state"); return SWE_ERR_ARG; }

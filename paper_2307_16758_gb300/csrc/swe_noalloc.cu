@@ -20,6 +20,8 @@
 //    before any stream capture.
 #include <cuda_runtime.h>
 
+#include <cmath>
+#include <cstdint>
 #include <mutex>
 #include <string>
 
@@ -64,6 +66,25 @@ int scratch_address(unsigned char **out)
     return SWE_OK;
 }
 
+// Clears the step's scalars that the previous call left and stores this
+// call's dt, both in the scratch array; dt arrives by value as a kernel
+// argument, so nothing is copied from host memory.
+__global__ void k_noalloc_reset(DevScalars *sc, double *dtv, double dt)
+{
+    if (threadIdx.x == 0) {
+        *sc = DevScalars{};
+        *dtv = dt;
+    }
+}
+
+// True when the byte ranges [a, a + na) and [b, b + nb) share a byte.
+bool overlaps(const void *a, size_t na, const void *b, size_t nb)
+{
+    if (!a || !b) return false;
+    const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return x < y + nb && y < x + na;
+}
+
 }  // namespace
 
 extern "C" int swe_muscl_step_noalloc(int64_t n_cells, const int32_t *nbr, const float *ln, const float *z,
@@ -78,12 +99,28 @@ extern "C" int swe_muscl_step_noalloc(int64_t n_cells, const int32_t *nbr, const
         return SWE_ERR_ARG;
     }
     if (!nbr || !ln || !z || !h || !hu || !hv || !h_out || !hu_out || !hv_out || !p ||
-        !(dt >= 0.0) || p->precision != SWE_FP32 || p->scheme != SWE_SCHEME_MUSCL || !(p->g > 0) ||
-        !(p->h_eps > 0) || n_inflow < 0 || n_inflow > SWE_MAX_GROUPS || n_level < 0 ||
-        n_level > SWE_MAX_GROUPS || (n_inflow > 0 && !inflow_qlen) || (n_level > 0 && !level) ||
-        p->block < 0 || p->block > 1024 || (p->block % 32) != 0 || h_out == h) {
-        swe_set_error("swe_muscl_step_noalloc: bad argument");
+        !(dt >= 0.0) || !std::isfinite(dt) || p->precision != SWE_FP32 || p->scheme != SWE_SCHEME_MUSCL ||
+        p->hr_order != 1 || !(p->g > 0) || !(p->h_eps > 0) || n_inflow < 0 || n_inflow > SWE_MAX_GROUPS ||
+        n_level < 0 || n_level > SWE_MAX_GROUPS || (n_inflow > 0 && !inflow_qlen) || (n_level > 0 && !level) ||
+        p->block < 0 || p->block > 1024 || (p->block % 32) != 0) {
+        swe_set_error("swe_muscl_step_noalloc: bad argument (null pointer, non-finite or negative dt, "
+                      "or params other than FP32 MUSCL with hr_order 1)");
         return SWE_ERR_ARG;
+    }
+    // every output must be apart from every other output and from every input
+    {
+        const size_t nf = (size_t)n_cells * sizeof(float);
+        const void *outs[3] = {h_out, hu_out, hv_out};
+        const void *ins[7] = {h, hu, hv, z, manning_n, ln, nbr};
+        const size_t in_len[7] = {nf, nf, nf, nf, nf, 6 * nf, 3 * (size_t)n_cells * sizeof(int32_t)};
+        bool bad = overlaps(outs[0], nf, outs[1], nf) || overlaps(outs[0], nf, outs[2], nf) ||
+                   overlaps(outs[1], nf, outs[2], nf);
+        for (int o = 0; o < 3 && !bad; o++)
+            for (int q = 0; q < 7 && !bad; q++) bad = overlaps(outs[o], nf, ins[q], in_len[q]);
+        if (bad) {
+            swe_set_error("swe_muscl_step_noalloc: an output overlaps another output or an input");
+            return SWE_ERR_ARG;
+        }
     }
     unsigned char *base = nullptr;
     int rc = scratch_address(&base);
@@ -92,9 +129,10 @@ extern "C" int swe_muscl_step_noalloc(int64_t n_cells, const int32_t *nbr, const
     Vec4<float> *F = reinterpret_cast<Vec4<float> *>(base);
     DevScalars *sc = reinterpret_cast<DevScalars *>(base + kScalarOff);
     double *dtv = reinterpret_cast<double *>(base + kDtOff);
-    // the scalars keep the previous call's values: clear them, then set dt
-    cudaError_t e = cudaMemsetAsync(sc, 0, sizeof(DevScalars), st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dtv, &dt, sizeof(double), cudaMemcpyHostToDevice, st);
+    // the scalars keep the previous call's values: clear them and set dt
+    // (one small kernel on the stream; dt travels as its argument)
+    k_noalloc_reset<<<1, 32, 0, st>>>(sc, dtv, dt);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         swe_set_error(std::string("swe_muscl_step_noalloc: ") + cudaGetErrorString(e));
         return SWE_ERR_CUDA;

@@ -20,7 +20,8 @@ LIB_PATH = os.path.join(HERE, "libswe.so")
 
 SWE_OK = 0
 ERRORS = {-1: "SWE_ERR_ARG", -2: "SWE_ERR_MESH", -3: "SWE_ERR_CUDA", -4: "SWE_ERR_DRY",
-          -5: "SWE_ERR_NONFINITE", -6: "SWE_ERR_TIMEOUT", -7: "SWE_ERR_NOMEM"}
+          -5: "SWE_ERR_NONFINITE", -7: "SWE_ERR_NOMEM"}
+FLAG_CLIPPED, FLAG_NONFINITE, FLAG_DRY = 1, 2, 4
 SWE_WALL, SWE_OPEN, SWE_INFLOW, SWE_LEVEL = 0, 1, 2, 3
 REORDER = {"none": 0, "morton": 1, "rcm": 2}
 SCHEME = {"hllc": 0, "muscl": 1, "waf": 2, "muscl_edge": 3}
@@ -36,7 +37,7 @@ EXPORTED = [
     "swe_last_error", "swe_params_default", "swe_set_allocator", "swe_mesh_create", "swe_mesh_destroy",
     "swe_mesh_info", "swe_mesh_export", "swe_state_init", "swe_state_destroy", "swe_set_stream",
     "swe_set_state", "swe_step", "swe_step_dt", "swe_sync", "swe_get_state", "swe_mass", "swe_time",
-    "swe_state_info", "swe_ensemble_create", "swe_ensemble_destroy", "swe_ensemble_step",
+    "swe_flags", "swe_state_info", "swe_ensemble_create", "swe_ensemble_destroy", "swe_ensemble_step",
     "swe_ensemble_sync", "swe_profile_begin", "swe_profile_end", "swe_dt_history",
     "swe_muscl_step_noalloc", "swe_autotune", "swe_ensemble_autotune",
     "swe_partition_create", "swe_partition_destroy", "swe_partition_info", "swe_partition_export",
@@ -97,6 +98,7 @@ def load_library(path: str = LIB_PATH, use_torch_allocator: bool = True):
     lib.swe_get_state.argtypes = [vp, vp, vp, vp]
     lib.swe_mass.argtypes = [vp, C.POINTER(dp), C.POINTER(dp), C.POINTER(dp)]
     lib.swe_time.argtypes = [vp, C.POINTER(dp), C.POINTER(i64)]
+    lib.swe_flags.argtypes = [vp, C.POINTER(i32)]
     lib.swe_state_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i32), C.POINTER(i32)]
     lib.swe_ensemble_create.argtypes = [C.POINTER(vp), i32, C.POINTER(vp)]
     lib.swe_ensemble_destroy.argtypes = [vp]
@@ -266,6 +268,12 @@ def swe_time(s):
     t, k = C.c_double(), C.c_int64()
     _check(load_library().swe_time(s, C.byref(t), C.byref(k)))
     return t.value, k.value
+
+
+def swe_flags(s):
+    f = C.c_int()
+    _check(load_library().swe_flags(s, C.byref(f)))
+    return f.value
 
 
 def swe_state_info(s):
@@ -441,6 +449,10 @@ class State:
 
     def time(self):
         return swe_time(self.handle)
+
+    def flags(self):
+        """Bit flags since init: FLAG_CLIPPED (a negative depth was clipped), FLAG_NONFINITE, FLAG_DRY."""
+        return swe_flags(self.handle)
 
     def info(self):
         return swe_state_info(self.handle)

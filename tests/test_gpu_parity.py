@@ -286,3 +286,33 @@ def test_mass_is_the_correctly_rounded_sum(precision):
     m.close()
     exact = math.fsum((a["area"] * h[a["perm"]]).tolist())
     assert abs(mass - exact) <= 4 * np.spacing(exact), (mass, exact)
+
+
+# ---- the clipping flag --------------------------------------------------------
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_clipping_flag_follows_the_clipped_mass(precision):
+    """swe_flags: SWE_FLAG_CLIPPED is set exactly when a negative depth was clipped (the clipped
+    mass of swe_mass is then positive); a lake at rest sets no flag."""
+    rest = W.partial_dam_break(nx=40, ny=20, spacing=1.0, n_gauss=20, breach=False, seed=9)
+    p = swe.swe_params_default("muscl", precision)
+    m = swe.Mesh.from_workload(rest)
+    s = swe.State.from_workload(m, p, rest)
+    s.step(50, 0.9)
+    assert s.flags() == 0
+    s.close()
+    m.close()
+    w = W.dam_break_1d(h_right=0.0)            # dry-bed dam break: MUSCL with Euler clips at the front
+    m = swe.Mesh.from_workload(w)
+    s = swe.State.from_workload(m, p, w)
+    seen = False
+    for _ in range(10):
+        s.step(20, 0.9)
+        clipped = s.mass()[1]
+        f = s.flags()
+        assert bool(f & swe.FLAG_CLIPPED) == (clipped > 0), (f, clipped)
+        assert not f & (swe.FLAG_NONFINITE | swe.FLAG_DRY)
+        seen = seen or clipped > 0
+    assert seen, "the dry-bed dam break clipped no depth"
+    s.close()
+    m.close()

@@ -6,9 +6,9 @@ could block -- so they cannot create a swe_state.  swe_muscl_step_noalloc
 serves them: it takes caller-owned device buffers and keeps its only scratch
 (the per-cell face values) in an array compiled into the library.  This test
 gives it the same mesh and state as a regular state advanced with
-swe_step_dt, and compares two calls in a row (the second call reads the
-first call's output while the shared scratch still holds the first call's
-face values).  The file is collected last so that a failing run stops only
+swe_step_dt, and compares two calls in a row bit for bit (the second call
+reads the first call's output while the shared scratch still holds the
+first call's face values).  The file is collected last so that a failing run stops only
 after every other test has run; it also passes alone in a fresh process.
 """
 import ctypes as C
@@ -82,10 +82,8 @@ def test_noalloc_step_matches_regular_entry_point_twice():
         for k, got in enumerate(dst):
             out = np.empty(n)
             out[perm] = got.cpu().numpy().astype(np.float64)
-            want = expected[call][k]
-            scale = max(np.abs(want).max(), 1e-30)
-            # same kernels and inputs: FP32 tolerance of the parity tests, in practice equal bits
-            assert np.abs(out - want).max() <= 1e-6 * scale, (call, k)
+            # the same kernels on the same inputs and the same dt: the same bits
+            assert np.array_equal(out, expected[call][k]), (call, k, np.abs(out - expected[call][k]).max())
     mesh.close()
 
 
@@ -96,3 +94,45 @@ def test_noalloc_rejects_meshes_above_its_limit():
     with pytest.raises(swe.SweError) as e:
         swe.swe_muscl_step_noalloc(swe.NOALLOC_MAX_CELLS + 1, *([1] * 10), 0.1, p, stream=C.c_void_p(None))
     assert e.value.code == -1
+
+
+def _small_buffers(n):
+    """Valid device buffers of n cells (so that a check that failed to reject could not fault)."""
+    import torch
+
+    f = lambda: torch.zeros(n, dtype=torch.float32, device="cuda")
+    nbr = torch.full((3 * n,), -1, dtype=torch.int32, device="cuda")      # every edge a wall
+    ln = torch.zeros(6 * n, dtype=torch.float32, device="cuda")
+    return nbr, ln, f(), f(), [f(), f(), f()], [f(), f(), f()]
+
+
+@pytest.mark.parametrize("case", ["dt_inf", "dt_nan", "dt_negative", "hr_order_2", "out_is_in_hu",
+                                  "outs_alias", "out_overlaps_z", "fp64"])
+def test_noalloc_rejects_bad_arguments(case):
+    B.build()
+    swe.load_library()
+    n = 64
+    nbr, ln, z, nm, src, dst = _small_buffers(n)
+    p = swe.swe_params_default("muscl", "fp32")
+    dt = 0.01
+    outs = [b.data_ptr() for b in dst]
+    if case == "dt_inf":
+        dt = float("inf")
+    elif case == "dt_nan":
+        dt = float("nan")
+    elif case == "dt_negative":
+        dt = -1e-3
+    elif case == "hr_order_2":
+        p.hr_order = 2
+    elif case == "out_is_in_hu":
+        outs[1] = src[1].data_ptr()
+    elif case == "outs_alias":
+        outs[2] = outs[0] + 4 * (n // 2)                                       # overlaps h_out's tail
+    elif case == "out_overlaps_z":
+        outs[0] = z.data_ptr()
+    elif case == "fp64":
+        p = swe.swe_params_default("muscl", "fp64")
+    with pytest.raises(swe.SweError) as e:
+        swe.swe_muscl_step_noalloc(n, nbr.data_ptr(), ln.data_ptr(), z.data_ptr(), nm.data_ptr(),
+                                   *[b.data_ptr() for b in src], *outs, dt, p, stream=C.c_void_p(None))
+    assert e.value.code == -1, case

@@ -19,12 +19,19 @@ LIB = os.path.join(HERE, "libswe.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
+# Device code is compiled without floating-point contraction (-fmad=false):
+# otherwise the compiler (and ptxas, for plain multiplies and adds) may fuse a
+# product into a multiply-add differently in each kernel that inlines the same
+# function, and the split, tile and batched kernels would round differently.
+# Fused multiply-adds that the arithmetic wants are written out (fma_rn).
+_V = ["-Xptxas", "-v"] if os.environ.get("SWE_PTXAS_VERBOSE") else []
+_NOFMA = ["-fmad=false"]
 SOURCES = [
-    ("swe_kernels.cu", ["-Xptxas", "-v"] if os.environ.get("SWE_PTXAS_VERBOSE") else []),
-    ("swe_fused.cu", ["-Xptxas", "-v"] if os.environ.get("SWE_PTXAS_VERBOSE") else []),
-    ("swe_noalloc.cu", []),
+    ("swe_kernels.cu", _NOFMA + _V),
+    ("swe_tile.cu", _NOFMA + _V),
+    ("swe_noalloc.cu", _NOFMA),
     ("swe_probe.cu", []),
-    ("swe_ensemble.cu", ["-Xptxas", "-v"] if os.environ.get("SWE_PTXAS_VERBOSE") else []),
+    ("swe_ensemble.cu", _NOFMA + _V),
     ("swe_api.cpp", []),
     ("swe_tiles.cpp", []),
     ("swe_partition.cpp", []),

@@ -92,9 +92,9 @@ template <typename T> struct StateT {
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> ev_used;
-    // fused tile kernel
+    // one-pass tile step
     bool fused = false;
-    FusedArgs fa{};
+    TileArgs ta{};
     // boundary-first schedule (swe_set_partition)
     bool sched = false;
     int32_t *d_bnd = nullptr, *d_int = nullptr, *d_recv = nullptr;
@@ -175,20 +175,27 @@ template <typename T> struct StateT {
         graphs.clear();
     }
 
-    // Select the split kernels or the fused tile kernel with `block` threads
-    // (building the tiling from the mesh); allocates what that kernel needs.
+    // Tile steps need a scheme and options that the tile kernel implements.
+    bool tile_capable() const
+    {
+        return (p.scheme == SWE_SCHEME_MUSCL || p.scheme == SWE_SCHEME_HLLC) && p.hr_order == 1;
+    }
+
+    // Select the split kernels or the one-pass tile step with `block` threads
+    // (cells per tile; the tile plan is built from the mesh); allocates what
+    // that path needs.
     int configure(bool want_fused, int block, const swe_mesh *m)
     {
         if (want_fused && sched) {
             swe_set_error("the boundary-first schedule runs the split kernels (clear the partition first)");
             return SWE_ERR_ARG;
         }
-        if (want_fused && (p.hr_order != 1 || p.waf_ratio != SWE_WAF_RATIO_DEPTH || p.scheme == SWE_SCHEME_MUSCL_EDGE)) {
-            swe_set_error("the fused kernel has neither the second-order reconstruction, the surface WAF ratio "
-                          "nor the paper's MUSCL");
+        if (want_fused && !tile_capable()) {
+            swe_set_error("the tile step runs LSQ MUSCL or first-order HLLC with the first-order hydrostatic "
+                          "reconstruction (WAF, the paper's MUSCL and hr_order 2 run the split kernels)");
             return SWE_ERR_ARG;
         }
-        const int lim = want_fused ? fused_max_threads<T>(p.scheme) : split_max_threads<T>(p.scheme, p.hr_order == 2);
+        const int lim = want_fused ? tile_max_threads<T>(p.scheme) : split_max_threads<T>(p.scheme, p.hr_order == 2);
         if (lim <= 0) { swe_set_error("cannot query the kernels (no usable GPU?)"); return SWE_ERR_CUDA; }
         if (block <= 0 || block % 32 || block > lim) {
             swe_set_error("block of " + std::to_string(block) + " threads is not a multiple of 32 within the kernel's limit of " +
@@ -197,47 +204,31 @@ template <typename T> struct StateT {
         }
         CK(cudaStreamSynchronize(stream));
         clear_graphs();
-        if (want_fused) {
-            if (!m || m->n != n) { swe_set_error("the fused kernel needs the state's mesh"); return SWE_ERR_ARG; }
-            Tiling tl;
-            if (swe_build_tiling(*m, block, tl) != 0) { swe_set_error("unsupported tile block"); return SWE_ERR_ARG; }
-            if (fused_smem_bytes<T>(p.scheme, block) > 227 * 1024) {
-                swe_set_error("tile needs more shared memory than a block has");
-                return SWE_ERR_ARG;
-            }
-            CK(fused_prepare<T>(p.scheme, block));
-            release((void *)fa.tile_start); release((void *)fa.halo_ptr); release((void *)fa.halo_ids);
-            release((void *)fa.edge_ptr); release((void *)fa.edges); release((void *)fa.nbr_local);
-            fa = FusedArgs{};
-            fa.block = block;
-            fa.n_tiles = tl.n_tiles;
-            fa.tile_start = alloc<int32_t>(tl.tile_start.size());
-            fa.halo_ptr = alloc<int32_t>(tl.halo_ptr.size());
-            fa.halo_ids = alloc<int32_t>(std::max<size_t>(tl.halo_ids.size(), 1));
-            fa.edge_ptr = alloc<int32_t>(tl.edge_ptr.size());
-            fa.edges = alloc<uint32_t>(std::max<size_t>(tl.edges.size(), 1));
-            fa.nbr_local = alloc<uint16_t>(3 * n);
-            if (!fa.tile_start || !fa.halo_ptr || !fa.halo_ids || !fa.edge_ptr || !fa.edges || !fa.nbr_local) {
-                swe_set_error("device allocation failed");
-                return SWE_ERR_NOMEM;
-            }
-            auto up = [&](const void *dst, const void *src, size_t bytes) {
-                return bytes ? cudaMemcpy((void *)dst, src, bytes, cudaMemcpyHostToDevice) : cudaSuccess;
-            };
-            CK(up(fa.tile_start, tl.tile_start.data(), sizeof(int32_t) * tl.tile_start.size()));
-            CK(up(fa.halo_ptr, tl.halo_ptr.data(), sizeof(int32_t) * tl.halo_ptr.size()));
-            CK(up(fa.halo_ids, tl.halo_ids.data(), sizeof(int32_t) * tl.halo_ids.size()));
-            CK(up(fa.edge_ptr, tl.edge_ptr.data(), sizeof(int32_t) * tl.edge_ptr.size()));
-            CK(up(fa.edges, tl.edges.data(), sizeof(uint32_t) * tl.edges.size()));
-            CK(up(fa.nbr_local, tl.nbr_local.data(), sizeof(uint16_t) * 3 * n));
-            p.kernel = SWE_KERNEL_FUSED;
-        } else {
+        if (!want_fused) {
             if ((p.scheme == SWE_SCHEME_MUSCL || p.scheme == SWE_SCHEME_MUSCL_EDGE) && !F) F = alloc<Vec4<T>>(3 * n);
             if (p.scheme == SWE_SCHEME_WAF && !F) { F = alloc<Vec4<T>>(n); U = alloc<Vec4<T>>(3 * n); }
             if (p.scheme != SWE_SCHEME_HLLC && (!F || (p.scheme == SWE_SCHEME_WAF && !U))) {
                 swe_set_error("device allocation failed");
                 return SWE_ERR_NOMEM;
             }
+        }
+        if (want_fused) {
+            if (!m || m->n != n) { swe_set_error("the tile step needs the state's mesh"); return SWE_ERR_ARG; }
+            TilePlan tp;
+            if (swe_build_tile_plan(*m, block, tp) != 0) { swe_set_error("unsupported tile size"); return SWE_ERR_ARG; }
+            const size_t smem = tile_smem_bytes<T>(block, std::max(tp.emax, 1), std::max(tp.xmax, 1));
+            if (smem > 227 * 1024) {
+                swe_set_error("tile needs more shared memory than a block has");
+                return SWE_ERR_ARG;
+            }
+            CK(tile_prepare<T>(p.scheme, smem));
+            ta = TileArgs{};
+            ta.tile = block;
+            ta.n_tiles = tp.n_tiles;
+            ta.emax = std::max(tp.emax, 1);
+            ta.xmax = std::max(tp.xmax, 1);
+            p.kernel = SWE_KERNEL_FUSED;
+        } else {
             p.kernel = SWE_KERNEL_SPLIT;
         }
         fused = want_fused;
@@ -332,11 +323,11 @@ template <typename T> struct StateT {
         return a;
     }
 
-    int block() const { return fused ? fa.block : (p.block > 0 ? p.block : 256); }
+    int block() const { return fused ? ta.tile : (p.block > 0 ? p.block : 256); }
 
     cudaError_t launch_step_kernels(const StepArgs<T> &a, int bl)
     {
-        if (fused) return traced(SWE_K_FUSED, [&] { return launch_fused<T>(p.scheme, a, fa, stream); });
+        if (fused) return traced(SWE_K_FUSED, [&] { return launch_tile<T>(p.scheme, a, ta, stream); });
         if (p.scheme != SWE_SCHEME_HLLC) {
             cudaError_t e = traced(SWE_K_PREP, [&] { return launch_prep<T>(p.scheme, a, F, U, prep_bl, stream); });
             if (e != cudaSuccess) return e;
@@ -497,6 +488,7 @@ template <typename T> struct StateT {
         if (rc) return rc;
         if (s.status & ST_NONFINITE) { swe_set_error("a non-finite depth or discharge was produced"); return SWE_ERR_NONFINITE; }
         if (s.status & ST_DRY) { swe_set_error("CFL rule: no wet cell"); return SWE_ERR_DRY; }
+        if (s.status & ST_TILE) { swe_set_error("a tile's edge list exceeded its plan (internal error)"); return SWE_ERR_CUDA; }
         return SWE_OK;
     }
 };
@@ -511,10 +503,9 @@ template <typename T> std::vector<Candidate> candidates(const StateT<T> &S, cons
     const int ls = split_max_threads<T>(S.p.scheme, S.p.hr_order == 2);
     for (int b : {128, 256, 512})
         if (b <= ls) c.push_back({false, b});
-    if ((S.p.scheme == SWE_SCHEME_MUSCL || S.p.scheme == SWE_SCHEME_WAF) && m && !S.sched && S.p.hr_order == 1 &&
-        S.p.waf_ratio == SWE_WAF_RATIO_DEPTH) {
-        const int lf = fused_max_threads<T>(S.p.scheme);
-        for (int b : {128, 256})
+    if (S.tile_capable() && m && !S.sched) {
+        const int lf = tile_max_threads<T>(S.p.scheme);
+        for (int b : {256, 512})
             if (b <= lf) c.push_back({true, b});
     }
     return c;
@@ -604,6 +595,7 @@ template <typename T> struct EnsembleT {
     int2 *d_blk = nullptr;        // per block of the batched grid: (member, block within the member)
     size_t tab_cap = 0, blk_cap = 0;
     int grid = 0;
+    size_t smem = 0;              // the tile kernel's dynamic shared memory (the members' largest)
     // CUDA graphs of kGraphSteps batched steps, keyed by the starting step
     // phase (steps taken mod 6); captured on a private stream, dropped when
     // the table is rebuilt
@@ -628,7 +620,8 @@ template <typename T> struct EnsembleT {
 
     cudaError_t launch_one(int phase, cudaStream_t s)
     {
-        return launch_ensemble<T>(scheme, mem[0]->p.hr_order == 2, built_fused, d_tab, d_blk, phase, grid, built_block, s);
+        return launch_ensemble<T>(scheme, mem[0]->p.hr_order == 2, built_fused, d_tab, d_blk, phase, grid, built_block,
+                                  smem, s);
     }
 
     // kGraphSteps batched steps through a cached CUDA graph.
@@ -684,6 +677,7 @@ template <typename T> struct EnsembleT {
         std::vector<EnsEntry<T>> h(nm);
         std::vector<int> begin(nm + 1, 0);
         const bool fused = mem[0]->fused;
+        size_t smem_max = 0;
         const int block = mem[0]->block();
         const int lim = ensemble_max_threads<T>(mem[0]->p.scheme, mem[0]->p.hr_order == 2, fused);
         if (block > lim) {
@@ -694,17 +688,19 @@ template <typename T> struct EnsembleT {
         for (size_t m = 0; m < nm; m++) {
             StateT<T> &s = *mem[m];
             for (int ph = 0; ph < 6; ph++) h[m].a[ph] = s.args_for_phase(ph, cfl_);
-            h[m].f = s.fa;
+            h[m].t = s.ta;
             h[m].F = s.F;
             h[m].U = s.U;
-            const int64_t blocks = fused ? s.fa.n_tiles : (s.n + block - 1) / block;
+            const int64_t blocks = fused ? s.ta.n_tiles : (s.n + block - 1) / block;
             if ((int64_t)begin[m] + blocks > INT32_MAX) { swe_set_error("ensemble too large"); return SWE_ERR_ARG; }
             begin[m + 1] = begin[m] + (int)blocks;
+            if (fused) smem_max = std::max(smem_max, tile_smem_bytes<T>(s.ta.tile, s.ta.emax, s.ta.xmax));
         }
         const size_t nb = (size_t)begin[nm];
         std::vector<int2> blk(nb);
         for (size_t m = 0; m < nm; m++)
             for (int b = begin[m]; b < begin[m + 1]; b++) blk[b] = make_int2((int)m, b - begin[m]);
+        if (smem_max > 227 * 1024) { swe_set_error("tile needs more shared memory than a block has"); return SWE_ERR_ARG; }
         if (tab_cap < nm) {
             dev_free(d_tab, stream);
             d_tab = (EnsEntry<T> *)dev_alloc(sizeof(EnsEntry<T>) * nm, stream);
@@ -720,9 +716,10 @@ template <typename T> struct EnsembleT {
         CK(cudaMemcpyAsync(d_tab, h.data(), sizeof(EnsEntry<T>) * nm, cudaMemcpyHostToDevice, stream));
         CK(cudaMemcpyAsync(d_blk, blk.data(), sizeof(int2) * nb, cudaMemcpyHostToDevice, stream));
         CK(cudaStreamSynchronize(stream));
-        CK(ensemble_prepare<T>(mem[0]->p.scheme, fused, block));
+        CK(ensemble_prepare<T>(mem[0]->p.scheme, fused, smem_max));
         clear_graphs();
         grid = begin[nm];
+        smem = smem_max;
         cfl = cfl_;
         built_fused = fused;
         built_block = block;
@@ -889,8 +886,8 @@ int state_init(StateT<T> &s, const swe_mesh *m, const double *h, const double *h
     CK(cudaMemcpyAsync(s.area, m->area.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(s.sc, 0, sizeof(DevScalars), st));
     {
-        // kernel choice: the split kernels unless the fused tile kernel is requested
-        const bool want_fused = s.p.scheme != SWE_SCHEME_HLLC && s.p.kernel == SWE_KERNEL_FUSED;
+        // kernel choice: the split kernels unless the one-pass tile step is requested
+        const bool want_fused = s.p.kernel == SWE_KERNEL_FUSED;
         int rc = s.configure(want_fused, s.p.block > 0 ? s.p.block : 256, m);
         if (rc) return rc;
     }

@@ -27,11 +27,11 @@ struct DevScalars {
     long long steps;     // steps taken
     double clipped;      // mass added by clipping negative depths
     double bnd_in;       // net mass that entered through the boundary
-    int status;          // bit 0 non-finite value, bit 1 no wet cell
+    int status;          // bit 0 non-finite value, bit 1 no wet cell, bit 2 a tile's edge list overflowed
     int pad;
 };
 
-enum { ST_NONFINITE = 1, ST_DRY = 2 };
+enum { ST_NONFINITE = 1, ST_DRY = 2, ST_TILE = 4 };
 enum { MODE_EULER = 0, MODE_STAGE = 1 };
 
 template <typename T> struct DevMesh {
@@ -69,25 +69,17 @@ template <typename T> struct StepArgs {
     T level[SWE_MAX_GROUPS];    // fixed free-surface levels [m]
 };
 
-// Fused tile kernel (see swe_tiles.cpp): tile b holds the cells
-// [tile_start[b], tile_start[b+1]) in slots 0..nc-1 and its halo
-// halo_ids[halo_ptr[b] .. halo_ptr[b+1]) in the following slots.
-// nbr_local[3n]: (slot << 3) | (neighbour's local edge << 1) | owner, or
-// 0x8000 | tag on a boundary.  edges[edge_ptr[b] .. edge_ptr[b+1]): one word
-// per interior edge with a tile cell on side i: slot_i | k_i << 9 |
-// slot_j << 11 | k_j << 20 | owner_i << 22 | j_in_tile << 23.
-struct FusedArgs {
-    const int32_t *tile_start;
-    const int32_t *halo_ptr;
-    const int32_t *halo_ids;
-    const int32_t *edge_ptr;
-    const uint32_t *edges;
-    const uint16_t *nbr_local;
-    int n_tiles;
-    int block;      // threads per block (largest tile + halo)
+// One-pass tile step (swe_tile.cu, plan built by swe_tiles.cpp): tile b is
+// the cells [b * tile, min((b + 1) * tile, n)), one per thread; emax and
+// xmax bound one tile's edges inside the tile and its crossing edges (its
+// shared memory).
+struct TileArgs {
+    int64_t n_tiles;
+    int tile;
+    int emax, xmax;
 };
 
-// Launchers (defined in swe_kernels.cu and swe_fused.cu).  All launches go to `stream`.
+// Launchers (defined in swe_kernels.cu and swe_tile.cu).  All launches go to `stream`.
 template <typename T>
 cudaError_t launch_prep(int scheme, const StepArgs<T> &a, Vec4<T> *F, Vec4<T> *U, int block, cudaStream_t s);
 template <typename T>
@@ -109,11 +101,11 @@ cudaError_t launch_gather_out(int64_t n, const int32_t *perm, const T *h, const 
 template <typename T>
 cudaError_t launch_convert(int64_t n, const double *src, T *dst, cudaStream_t s);
 
-template <typename T>
-cudaError_t launch_fused(int scheme, const StepArgs<T> &a, const FusedArgs &f, cudaStream_t s);
-template <typename T> size_t fused_smem_bytes(int scheme, int block);
-template <typename T> int fused_max_threads(int scheme);     // launch limit of the fused kernel (registers)
-template <typename T> cudaError_t fused_prepare(int scheme, int block);   // shared-memory attribute, once
+// The tile step: one launch advances every tile.
+template <typename T> cudaError_t launch_tile(int scheme, const StepArgs<T> &a, const TileArgs &t, cudaStream_t s);
+template <typename T> size_t tile_smem_bytes(int tile, int emax, int xmax);
+template <typename T> int tile_max_threads(int scheme);     // launch limit of the tile kernel (registers)
+template <typename T> cudaError_t tile_prepare(int scheme, size_t smem);   // shared-memory attribute, once
 
 // Boundary-first schedule: flux over a list of cells (a.cells, a.n_list), and
 // the halo of every part packed (SoA, [3][n]) from the new state.

@@ -84,6 +84,14 @@ __device__ __forceinline__ Flux<T> riemann(T hsL, T uL, T vL, T hsR, T uR, T vR,
         f.M = T(0); f.Tt = T(0); f.DL2 = -GL2; f.DR2 = -GR2;
         return f;
     }
+    if (!WAF && hsL == hsR && uL == uR && vL == vR) {
+        // equal states (a lake at rest, or any uniform flow): whichever wave
+        // pattern the speeds give, dU = dG = 0, so the HLL flux is G(U) and
+        // the HLLC tangential flux is M v; the solver below would return the
+        // same values (up to the sign of a zero), so its speeds are skipped
+        f.M = GL1 + T(0); f.Tt = f.M * vL; f.DL2 = T(0); f.DR2 = T(0);
+        return f;
+    }
     T aL = dsqrt(g * hsL), aR = dsqrt(g * hsR);
     T SL, SR;
     if (dryL) {                            // dry-bed wave speeds
@@ -179,16 +187,22 @@ __device__ __forceinline__ void midpoint_offsets(const Vec2<T> ln[3], T ox[3], T
 // the midpoint offset of j's edge k_j from j's scaled normals.  (oxi, oyi) is
 // the midpoint offset of cell i's edge k.  The centroid offsets are thus
 // derived from the normals that the kernels read anyway, not stored.
+// a1, a2: the neighbour's scaled normals of its edges k_j + 1 and k_j + 2.
 template <typename T>
-__device__ __forceinline__ Vec2<T> centroid_offset(const Vec2<T> *ln, T oxi, T oyi, int j, int kj)
+__device__ __forceinline__ Vec2<T> centroid_offset_from(T oxi, T oyi, const Vec2<T> &a1, const Vec2<T> &a2)
 {
     const T s = T(1) / T(6);
-    const int k1 = kj == 2 ? 0 : kj + 1, k2 = kj == 0 ? 2 : kj - 1;
-    const Vec2<T> a1 = ln[3 * j + k1], a2 = ln[3 * j + k2];
     Vec2<T> d;
     d.x = oxi - mul_rn(a1.y - a2.y, s);
     d.y = oyi - mul_rn(a2.x - a1.x, s);
     return d;
+}
+
+template <typename T>
+__device__ __forceinline__ Vec2<T> centroid_offset(const Vec2<T> *ln, T oxi, T oyi, int j, int kj)
+{
+    const int k1 = kj == 2 ? 0 : kj + 1, k2 = kj == 0 ? 2 : kj - 1;
+    return centroid_offset_from(oxi, oyi, ln[3 * j + k1], ln[3 * j + k2]);
 }
 
 template <typename T>
@@ -306,7 +320,15 @@ __device__ __forceinline__ void muscl_faces(const T qi[NQ], T zi, bool ok, int c
     for (int s = 0; s < NQ; s++) { gx[s] = T(0); gy[s] = T(0); }
     // Every product below is either fused explicitly (fma_rn) or rounded on
     // its own (mul_rn), so all kernels that inline this give the same bits.
-    if (ok && cnt >= 2) {
+    // When every neighbour holds the cell's own values (a lake at rest, a
+    // uniform flow) the least-squares right-hand sides are exact zeros and the
+    // limited gradient is +0: the solve is skipped, with the same bits.
+    bool flat = true;
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+#pragma unroll
+        for (int s = 0; s < NQ; s++) flat = flat && qn[k][s] == qi[s];
+    if (ok && cnt >= 2 && !flat) {
         T Mxx = T(0), Mxy = T(0), Myy = T(0);
         T bx[NQ], by[NQ];
 #pragma unroll

@@ -9,7 +9,6 @@
 
 #include "swe_ensemble.h"
 #include "swe_device.cuh"
-#include "swe_fused.cuh"
 #include "swe_split.cuh"
 
 namespace {
@@ -42,27 +41,13 @@ __global__ void __maxnreg__((sizeof(T) == 4 ? 48 : 255))
     flux_block<T, SCHEME>(tab[b.x].a[phase], b.y);
 }
 
-template <typename T, int SCHEME>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
-    k_fused_ens(const EnsEntry<T> *__restrict__ tab, const int2 *__restrict__ blk, int phase)
-{
-    extern __shared__ __align__(32) unsigned char smem_raw[];
-    const int2 b = blk[blockIdx.x];
-    fused_tile<T, SCHEME>(tab[b.x].a[phase], tab[b.x].f, b.y, smem_raw);
-}
-
 }  // namespace
 
 template <typename T>
 cudaError_t launch_ensemble(int scheme, bool hr2, bool fused, const EnsEntry<T> *tab, const int2 *blk, int phase,
-                            int grid, int block, cudaStream_t s)
+                            int grid, int block, size_t smem, cudaStream_t s)
 {
-    if (fused) {
-        const size_t smem = fused_smem_bytes<T>(scheme, block);
-        auto kern = scheme == SWE_SCHEME_WAF ? k_fused_ens<T, SWE_SCHEME_WAF> : k_fused_ens<T, SWE_SCHEME_MUSCL>;
-        kern<<<grid, block, smem, s>>>(tab, blk, phase);
-        return cudaGetLastError();
-    }
+    if (fused) return launch_tile_ensemble<T>(scheme, tab, blk, phase, grid, block, smem, s);
     if (scheme == SWE_SCHEME_MUSCL && hr2) {
         k_prep_ens<T, FLUX_MUSCL_HR2><<<grid, block, 0, s>>>(tab, blk, phase);
         k_flux_ens<T, FLUX_MUSCL_HR2><<<grid, block, 0, s>>>(tab, blk, phase);
@@ -81,15 +66,9 @@ cudaError_t launch_ensemble(int scheme, bool hr2, bool fused, const EnsEntry<T> 
     return cudaGetLastError();
 }
 
-template <typename T> cudaError_t ensemble_prepare(int scheme, bool fused, int block)
+template <typename T> cudaError_t ensemble_prepare(int scheme, bool fused, size_t smem)
 {
-    if (!fused) return cudaSuccess;
-    const int smem = (int)fused_smem_bytes<T>(scheme, block);
-    auto kern = scheme == SWE_SCHEME_WAF ? k_fused_ens<T, SWE_SCHEME_WAF> : k_fused_ens<T, SWE_SCHEME_MUSCL>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-    return e;
+    return fused ? tile_ensemble_prepare<T>(scheme, smem) : cudaSuccess;
 }
 
 namespace {
@@ -109,7 +88,7 @@ template <typename T, int SCHEME, bool PREP> int split_ens_max_threads()
 
 template <typename T> int ensemble_max_threads(int scheme, bool hr2, bool fused)
 {
-    if (fused) return max_threads(scheme == SWE_SCHEME_WAF ? k_fused_ens<T, SWE_SCHEME_WAF> : k_fused_ens<T, SWE_SCHEME_MUSCL>);
+    if (fused) return tile_ensemble_max_threads<T>(scheme);
     if (scheme == SWE_SCHEME_MUSCL && hr2) return split_ens_max_threads<T, FLUX_MUSCL_HR2, true>();
     if (scheme == SWE_SCHEME_MUSCL) return split_ens_max_threads<T, SWE_SCHEME_MUSCL, true>();
     if (scheme == SWE_SCHEME_MUSCL_EDGE) {
@@ -123,8 +102,8 @@ template int ensemble_max_threads<float>(int, bool, bool);
 template int ensemble_max_threads<double>(int, bool, bool);
 
 template cudaError_t launch_ensemble<float>(int, bool, bool, const EnsEntry<float> *, const int2 *, int, int, int,
-                                            cudaStream_t);
+                                            size_t, cudaStream_t);
 template cudaError_t launch_ensemble<double>(int, bool, bool, const EnsEntry<double> *, const int2 *, int, int, int,
-                                             cudaStream_t);
-template cudaError_t ensemble_prepare<float>(int, bool, int);
-template cudaError_t ensemble_prepare<double>(int, bool, int);
+                                             size_t, cudaStream_t);
+template cudaError_t ensemble_prepare<float>(int, bool, size_t);
+template cudaError_t ensemble_prepare<double>(int, bool, size_t);

@@ -6,10 +6,12 @@
 
 namespace swe_dev {
 
-// NQ = 4: also the limited gradient of h, for the face bed of the
-// second-order hydrostatic reconstruction (R16); F[3i + k].w is the face bed.
+// MUSCL face values of cell i (least squares + Barth-Jespersen): f[k] =
+// (eta, u, v, z) at the midpoint of edge k.  NQ = 4: also the limited
+// gradient of h, for the face bed of the second-order hydrostatic
+// reconstruction (R16); f[k].w is then the face bed.
 template <typename T, int NQ = 3>
-__device__ __forceinline__ void prep_muscl_cell(const StepArgs<T> &a, int i, Vec4<T> *F)
+__device__ __forceinline__ void muscl_cell_faces(const StepArgs<T> &a, int64_t i, Vec4<T> f[3])
 {
     const T h_eps = a.h_eps;
     T hi = a.h[i], zi = a.m.z[i];
@@ -17,10 +19,8 @@ __device__ __forceinline__ void prep_muscl_cell(const StepArgs<T> &a, int i, Vec
         // a dry cell has a zero gradient and zero velocity: its three face
         // values are its centre values (eta, 0, 0), as muscl_faces gives them;
         // the neighbours and the geometry are not needed
-        Vec4<T> f;
-        f.x = hi + zi; f.y = T(0); f.z = T(0); f.w = zi;
 #pragma unroll
-        for (int k = 0; k < 3; k++) F[3 * i + k] = f;
+        for (int k = 0; k < 3; k++) { f[k].x = hi + zi; f[k].y = T(0); f[k].z = T(0); f[k].w = zi; }
         return;
     }
     T ui, vi;
@@ -55,8 +55,14 @@ __device__ __forceinline__ void prep_muscl_cell(const StepArgs<T> &a, int i, Vec
             dd[k].x = T(0); dd[k].y = T(0);
         }
     }
-    Vec4<T> f[3];
     muscl_faces<T, NQ>(qi, zi, ok, cnt, qn, has, ox, oy, dd, f);
+}
+
+template <typename T, int NQ = 3>
+__device__ __forceinline__ void prep_muscl_cell(const StepArgs<T> &a, int i, Vec4<T> *F)
+{
+    Vec4<T> f[3];
+    muscl_cell_faces<T, NQ>(a, i, f);
 #pragma unroll
     for (int k = 0; k < 3; k++) F[3 * i + k] = f[k];
 }

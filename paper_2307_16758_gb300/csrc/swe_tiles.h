@@ -1,21 +1,17 @@
-// Tiling of the renumbered cells for the fused kernel (built on the host).
+// Tile plan of the one-pass tile step (built on the host from the mesh).
 #pragma once
 #include <cstdint>
 #include <vector>
 
 struct swe_mesh;
 
-struct Tiling {
-    int block = 0;                    // threads per block = largest tile + halo
-    int n_tiles = 0;
-    int max_edges = 0;
-    std::vector<int32_t> tile_start;  // [n_tiles + 1]
-    std::vector<int32_t> halo_ptr;    // [n_tiles + 1]
-    std::vector<int32_t> halo_ids;    // halo cells of all tiles, sorted per tile
-    std::vector<int32_t> edge_ptr;    // [n_tiles + 1]
-    std::vector<uint32_t> edges;      // per tile, see FusedArgs
-    std::vector<uint16_t> nbr_local;  // [3n], see FusedArgs
+struct TilePlan {
+    int tile = 0;                     // cells per tile = threads per block
+    int64_t n_tiles = 0;
+    int emax = 0;                     // most edges inside one tile
+    int xmax = 0;                     // most crossing edges of one tile
+    int64_t n_cross = 0;              // crossing edges of all tiles
 };
 
-// Returns 0, or a negative value if the block size is unsupported.
-int swe_build_tiling(const swe_mesh &m, int block, Tiling &out);
+// Returns 0, or a negative value if the tile size is unsupported.
+int swe_build_tile_plan(const swe_mesh &m, int tile, TilePlan &out);

@@ -45,7 +45,7 @@ def _alone(w, p, steps):
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 @pytest.mark.parametrize("kernel,scheme", [("split", "muscl"), ("fused", "muscl"), ("split", "waf"),
-                                           ("fused", "waf"), ("split", "hllc"), ("split", "muscl_edge")])
+                                           ("split", "hllc"), ("fused", "hllc"), ("split", "muscl_edge")])
 def test_ensemble_members_match_stepping_alone(kernel, scheme, precision):
     ws = _scenarios()
     p = swe.swe_params_default(scheme, precision, kernel=kernel)

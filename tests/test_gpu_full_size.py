@@ -2,16 +2,16 @@
 
 13,004,160-cell river (the benchmark): the oracle can afford one full-mesh
 step, so the FP64 path is compared with it cell by cell (one step, 1e-12).
-The FP32 benchmark configuration (split kernels, flux blocks of 256 and
-prep blocks of 128 threads, CUDA graphs, CFL 0.9) is checked through properties that hold at any size: its one-step
-result against the same oracle step (same h_eps), the mass budget, and that
-the fused kernel gives the same bits.
+The FP32 benchmark configuration (the one-pass tile step with tiles of 256
+cells, CUDA graphs, CFL 0.9) is checked through properties that hold at any
+size: its one-step result against the same oracle step (same h_eps), the mass
+budget, and that the split kernels give the same bits.
 
 4,000,920-cell river: WAF and MUSCL in FP32 against the FP64 path after 1000
 steps (L1 error, mass drift, wetting front).
 
-1,000,000-cell partial dam break: MUSCL and WAF FP64 (split and fused
-kernels) against the oracle after 100 steps, cell by cell.
+1,000,000-cell partial dam break: MUSCL (split kernels and tile step) and
+WAF (split kernels) FP64 against the oracle after 100 steps, cell by cell.
 """
 import math
 import os
@@ -64,7 +64,7 @@ def test_fp64_one_step_matches_oracle_at_full_size(river13m):
 
 def test_fp32_bench_configuration_at_full_size(river13m):
     w, mesh, om = river13m
-    p = swe.swe_params_default("muscl", "fp32")           # the benchmark's path: split kernels, flux block 256, prep 128
+    p = swe.swe_params_default("muscl", "fp32")           # the benchmark's path: the tile step, tiles of 256
     st = swe.State.from_workload(mesh, p, w)
     m0 = st.mass()[0]
     st.step(1, 0.9)
@@ -78,7 +78,7 @@ def test_fp32_bench_configuration_at_full_size(river13m):
     assert st.time()[1] == 49
     hs = st.get_state()[0]
     st.close()
-    pf = swe.swe_params_default("muscl", "fp32", kernel="fused")
+    pf = swe.swe_params_default("muscl", "fp32", kernel="split")
     sf = swe.State.from_workload(mesh, pf, w)
     sf.step(49, 0.9)
     assert np.array_equal(sf.get_state()[0], hs)
@@ -176,8 +176,7 @@ def dam1m():
     yield w, om
 
 
-@pytest.mark.parametrize("kernel", ["split", "fused"])
-@pytest.mark.parametrize("scheme", ["muscl", "waf"])
+@pytest.mark.parametrize("scheme,kernel", [("muscl", "split"), ("muscl", "fused"), ("waf", "split")])
 def test_fp64_partial_dam_break_1m_against_oracle(dam1m, scheme, kernel):
     """100 steps at full size with the oracle's own time steps replayed: 1e-9 (the stated bar)."""
     w, om = dam1m

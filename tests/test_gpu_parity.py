@@ -56,10 +56,11 @@ def test_fp64_hllc_config1_200_steps_cfl():
 
 
 KERNELS = ["split", "fused"]
+# the one-pass tile step ("fused") runs LSQ MUSCL and first-order HLLC; WAF runs the split kernels
+SCHEME_KERNELS = [("hllc", "split"), ("hllc", "fused"), ("muscl", "split"), ("muscl", "fused"), ("waf", "split")]
 
 
-@pytest.mark.parametrize("kernel", KERNELS)
-@pytest.mark.parametrize("scheme", ["hllc", "muscl", "waf"])
+@pytest.mark.parametrize("scheme,kernel", SCHEME_KERNELS)
 def test_fp64_partial_dam_break(scheme, kernel):
     """Jittered mesh, Gaussian bed, ~30 % dry, breach, Manning: 1 and 100 steps."""
     w = _pdb()
@@ -73,8 +74,7 @@ def test_fp64_partial_dam_break(scheme, kernel):
     assert math.isclose(gc["t"], o["t"], rel_tol=1e-9)
 
 
-@pytest.mark.parametrize("kernel", KERNELS)
-@pytest.mark.parametrize("scheme", ["hllc", "muscl", "waf"])
+@pytest.mark.parametrize("scheme,kernel", SCHEME_KERNELS)
 def test_fp64_river_inflow_level_friction(scheme, kernel):
     w = _river()
     o = run_oracle(w, scheme, steps=100)
@@ -110,12 +110,13 @@ def test_block_above_the_kernel_limit_is_rejected():
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("scheme", ["muscl", "waf"])
+@pytest.mark.parametrize("scheme", ["muscl", "hllc"])
 def test_split_and_fused_kernels_agree_bitwise(precision, scheme):
-    """The fused tile kernel runs the same per-cell code as the split kernels."""
+    """The one-pass tile step runs the same per-edge and per-cell code as the split kernels, so
+    every tile size gives the split kernels' bits (CFL steps, inflow, level, friction, wet/dry)."""
     w = _river(90, 34)
     a = run_gpu(w, scheme, precision, steps=50, kernel="split")
-    for block in (128, 256):
+    for block in (64, 128, 256) + ((512,) if precision == "fp32" else ()):
         b = run_gpu(w, scheme, precision, steps=50, kernel="fused", block=block)
         for k in ("h", "hu", "hv"):
             assert np.array_equal(a[k], b[k]), (block, k)
@@ -123,9 +124,8 @@ def test_split_and_fused_kernels_agree_bitwise(precision, scheme):
 
 # ---- invariants on the GPU ----------------------------------------------------
 
-@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("scheme", ["hllc", "muscl", "waf"])
+@pytest.mark.parametrize("scheme,kernel", SCHEME_KERNELS)
 def test_lake_at_rest_bitwise(precision, scheme, kernel):
     w = W.partial_dam_break(nx=80, ny=40, spacing=1.0, n_gauss=40, breach=False, seed=9)
     w.bnd_tag = np.full(len(w.bnd_edges), W.tag(W.LEVEL), np.int32)
@@ -166,8 +166,7 @@ def test_renumbering_is_bitwise_invisible(precision, kernel):
 
 # ---- FP32 against the FP64 oracle ----------------------------------------------
 
-@pytest.mark.parametrize("kernel", KERNELS)
-@pytest.mark.parametrize("scheme", ["muscl", "waf", "hllc"])
+@pytest.mark.parametrize("scheme,kernel", SCHEME_KERNELS)
 def test_fp32_error_against_oracle(scheme, kernel):
     """FP32 state and fluxes (FP64 mass and time): relative L1 of h after 1000
     replayed steps <= 1e-4, mass drift <= 1e-6 (same h_eps on both sides)."""
@@ -187,13 +186,15 @@ def test_single_triangle_and_tiny_meshes():
     w = W.Workload("one", nodes, np.array([[0, 1, 2]], np.int32), np.zeros((0, 2), np.int32),
                    np.zeros(0, np.int32), np.zeros((0, 2), np.int32), np.zeros(n), np.zeros(n),
                    np.ones(n), np.zeros(n), np.zeros(n))
-    g = run_gpu(w, "muscl", steps=5)
-    assert np.array_equal(g["h"], [1.0]) and g["hu"][0] == 0 and g["hv"][0] == 0
+    for kernel in KERNELS:
+        g = run_gpu(w, "muscl", steps=5, kernel=kernel)
+        assert np.array_equal(g["h"], [1.0]) and g["hu"][0] == 0 and g["hv"][0] == 0
     for nx in (1, 2, 129):                       # 2, 4 and 258 cells (one block plus a tail)
         w2 = W.dam_break_1d(nx, 1, float(nx), 1.0, 1.0, 0.5, x_dam=nx / 2.0 + 0.1)
         o = run_oracle(w2, "muscl", steps=3)
-        g2 = run_gpu(w2, "muscl", dt=o["dts"])
-        assert max(state_errors(g2, o)) <= 1e-12
+        for kernel in KERNELS:
+            g2 = run_gpu(w2, "muscl", dt=o["dts"], kernel=kernel)
+            assert max(state_errors(g2, o)) <= 1e-12, (nx, kernel)
 
 
 def test_non_finite_input_is_reported():

@@ -45,7 +45,8 @@ enum {
     SWE_ERR_CUDA = -3,       /* a CUDA runtime call failed */
     SWE_ERR_DRY = -4,        /* CFL rule: no wet cell, no time step defined */
     SWE_ERR_NONFINITE = -5,  /* a non-finite depth or discharge was produced */
-    SWE_ERR_NOMEM = -7       /* host or device allocation failed (-6 is unused) */
+    SWE_ERR_TIMEOUT = -6,    /* a bounded device wait (a bulk copy into shared memory) gave up */
+    SWE_ERR_NOMEM = -7       /* host or device allocation failed */
 };
 
 enum { SWE_WALL = 0, SWE_OPEN = 1, SWE_INFLOW = 2, SWE_LEVEL = 3 };

@@ -66,6 +66,10 @@ struct Alloc {
     int64_t bytes = 0;
 };
 
+// Largest tile of the tile step; per-cell arrays are allocated to a multiple
+// of it so that every tile, the last one included, is copied whole.
+constexpr int64_t kTilePad = 1024;
+
 template <typename T> struct StateT {
     swe_params p{};
     int64_t n = 0;
@@ -118,11 +122,16 @@ template <typename T> struct StateT {
     bool smax_valid = false;
     T qlen[SWE_MAX_GROUPS] = {}, level[SWE_MAX_GROUPS] = {};
 
+    // Device array of `count` elements, zero-filled (on the state's stream).
     template <typename P> P *alloc(size_t count)
     {
         size_t b = count * sizeof(P);
         void *ptr = dev_alloc(b, stream);
-        if (ptr) { mem.blocks.push_back({ptr, b}); mem.bytes += (int64_t)((b + 255) & ~size_t(255)); }
+        if (ptr) {
+            mem.blocks.push_back({ptr, b});
+            mem.bytes += (int64_t)((b + 255) & ~size_t(255));
+            if (cudaMemsetAsync(ptr, 0, b, stream) != cudaSuccess) return nullptr;
+        }
         return (P *)ptr;
     }
     ~StateT()
@@ -216,17 +225,32 @@ template <typename T> struct StateT {
             if (!m || m->n != n) { swe_set_error("the tile step needs the state's mesh"); return SWE_ERR_ARG; }
             TilePlan tp;
             if (swe_build_tile_plan(*m, block, tp) != 0) { swe_set_error("unsupported tile size"); return SWE_ERR_ARG; }
-            const size_t smem = tile_smem_bytes<T>(block, std::max(tp.emax, 1), std::max(tp.xmax, 1));
+            TileArgs t{};
+            t.tile = block;
+            t.n_tiles = tp.n_tiles;
+            t.emax = std::max(tp.emax, 1);
+            t.xmax = std::max(tp.xmax, 1);
+            t.hmax = (std::max(tp.hmax, 1) + 3) & ~3;          // stage alignment (see TileStage)
+            t.h1max = std::max(tp.h1max, 1);
+            t.wmax = (std::max(tp.wmax, 8) + 7) & ~7;
+            const size_t smem = tile_smem_bytes<T>(t);
             if (smem > 227 * 1024) {
                 swe_set_error("tile needs more shared memory than a block has");
                 return SWE_ERR_ARG;
             }
             CK(tile_prepare<T>(p.scheme, smem));
-            ta = TileArgs{};
-            ta.tile = block;
-            ta.n_tiles = tp.n_tiles;
-            ta.emax = std::max(tp.emax, 1);
-            ta.xmax = std::max(tp.xmax, 1);
+            t.grid = tile_grid<T>(p.scheme, block, smem);
+            if (t.grid <= 0) { swe_set_error("the tile kernel cannot be resident with this tile size"); return SWE_ERR_ARG; }
+            release((void *)ta.plan_hdr);
+            release((void *)ta.plan_words);
+            int32_t *hdr = alloc<int32_t>(tp.hdr.size());
+            int32_t *words = alloc<int32_t>(tp.words.size());
+            if (!hdr || !words) { swe_set_error("device allocation failed"); return SWE_ERR_NOMEM; }
+            CK(cudaMemcpy(hdr, tp.hdr.data(), sizeof(int32_t) * tp.hdr.size(), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(words, tp.words.data(), sizeof(int32_t) * tp.words.size(), cudaMemcpyHostToDevice));
+            t.plan_hdr = hdr;
+            t.plan_words = words;
+            ta = t;
             p.kernel = SWE_KERNEL_FUSED;
         } else {
             p.kernel = SWE_KERNEL_SPLIT;
@@ -489,6 +513,7 @@ template <typename T> struct StateT {
         if (s.status & ST_NONFINITE) { swe_set_error("a non-finite depth or discharge was produced"); return SWE_ERR_NONFINITE; }
         if (s.status & ST_DRY) { swe_set_error("CFL rule: no wet cell"); return SWE_ERR_DRY; }
         if (s.status & ST_TILE) { swe_set_error("a tile's edge list exceeded its plan (internal error)"); return SWE_ERR_CUDA; }
+        if (s.status & ST_TIMEOUT) { swe_set_error("a bulk copy into shared memory did not complete in time"); return SWE_ERR_TIMEOUT; }
         return SWE_OK;
     }
 };
@@ -595,7 +620,8 @@ template <typename T> struct EnsembleT {
     int2 *d_blk = nullptr;        // per block of the batched grid: (member, block within the member)
     size_t tab_cap = 0, blk_cap = 0;
     int grid = 0;
-    size_t smem = 0;              // the tile kernel's dynamic shared memory (the members' largest)
+    size_t smem = 0;              // the tile kernel's dynamic shared memory
+    TileArgs room{};              // its shared-memory room (the members' largest)
     // CUDA graphs of kGraphSteps batched steps, keyed by the starting step
     // phase (steps taken mod 6); captured on a private stream, dropped when
     // the table is rebuilt
@@ -621,7 +647,7 @@ template <typename T> struct EnsembleT {
     cudaError_t launch_one(int phase, cudaStream_t s)
     {
         return launch_ensemble<T>(scheme, mem[0]->p.hr_order == 2, built_fused, d_tab, d_blk, phase, grid, built_block,
-                                  smem, s);
+                                  room, s);
     }
 
     // kGraphSteps batched steps through a cached CUDA graph.
@@ -679,6 +705,8 @@ template <typename T> struct EnsembleT {
         const bool fused = mem[0]->fused;
         size_t smem_max = 0;
         const int block = mem[0]->block();
+        TileArgs room_{};
+        room_.tile = block;
         const int lim = ensemble_max_threads<T>(mem[0]->p.scheme, mem[0]->p.hr_order == 2, fused);
         if (block > lim) {
             swe_set_error("block of " + std::to_string(block) + " threads exceeds the batched kernels' limit of " +
@@ -694,12 +722,17 @@ template <typename T> struct EnsembleT {
             const int64_t blocks = fused ? s.ta.n_tiles : (s.n + block - 1) / block;
             if ((int64_t)begin[m] + blocks > INT32_MAX) { swe_set_error("ensemble too large"); return SWE_ERR_ARG; }
             begin[m + 1] = begin[m] + (int)blocks;
-            if (fused) smem_max = std::max(smem_max, tile_smem_bytes<T>(s.ta.tile, s.ta.emax, s.ta.xmax));
+            if (fused) {
+                room_.emax = std::max(room_.emax, s.ta.emax); room_.xmax = std::max(room_.xmax, s.ta.xmax);
+                room_.hmax = std::max(room_.hmax, s.ta.hmax); room_.h1max = std::max(room_.h1max, s.ta.h1max);
+                room_.wmax = std::max(room_.wmax, s.ta.wmax);
+            }
         }
         const size_t nb = (size_t)begin[nm];
         std::vector<int2> blk(nb);
         for (size_t m = 0; m < nm; m++)
             for (int b = begin[m]; b < begin[m + 1]; b++) blk[b] = make_int2((int)m, b - begin[m]);
+        if (fused) smem_max = tile_smem_bytes<T>(room_);
         if (smem_max > 227 * 1024) { swe_set_error("tile needs more shared memory than a block has"); return SWE_ERR_ARG; }
         if (tab_cap < nm) {
             dev_free(d_tab, stream);
@@ -720,6 +753,7 @@ template <typename T> struct EnsembleT {
         clear_graphs();
         grid = begin[nm];
         smem = smem_max;
+        room = room_;
         cfl = cfl_;
         built_fused = fused;
         built_block = block;
@@ -856,16 +890,19 @@ int state_init(StateT<T> &s, const swe_mesh *m, const double *h, const double *h
             s.qlen[g] = m->group_len[g] > 0.0 ? (T)(bc->inflow_q[g] / m->group_len[g]) : T(0);
         for (int g = 0; g < bc->n_level && g < SWE_MAX_GROUPS; g++) s.level[g] = (T)bc->level[g];
     }
-    s.nbr = s.template alloc<int32_t>(3 * n);
+    // per-cell arrays the tile step copies by whole tiles: allocated (and
+    // zero-filled) to a multiple of the largest tile
+    const int64_t np = (n + kTilePad - 1) / kTilePad * kTilePad;
+    s.nbr = s.template alloc<int32_t>(3 * np);
     s.perm = s.template alloc<int32_t>(n);
-    s.ln = s.template alloc<Vec2<T>>(3 * n);
+    s.ln = s.template alloc<Vec2<T>>(3 * np);
     if (s.p.scheme == SWE_SCHEME_WAF) s.dd = s.template alloc<Vec2<T>>(3 * n);   // WAF's centroid distance
-    s.z = s.template alloc<T>(n);
-    if (friction) s.nman = s.template alloc<T>(n);
+    s.z = s.template alloc<T>(np);
+    if (friction) s.nman = s.template alloc<T>(np);
     s.area = s.template alloc<double>(n);
     const int nbuf = s.p.time_scheme == SWE_HEUN ? 3 : 2;
     for (int b = 0; b < nbuf; b++) {
-        s.h[b] = s.template alloc<T>(n); s.hu[b] = s.template alloc<T>(n); s.hv[b] = s.template alloc<T>(n);
+        s.h[b] = s.template alloc<T>(np); s.hu[b] = s.template alloc<T>(np); s.hv[b] = s.template alloc<T>(np);
     }
     s.sc = s.template alloc<DevScalars>(1);
     s.n_part = mass_partials_needed(n);

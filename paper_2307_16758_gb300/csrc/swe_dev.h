@@ -27,11 +27,13 @@ struct DevScalars {
     long long steps;     // steps taken
     double clipped;      // mass added by clipping negative depths
     double bnd_in;       // net mass that entered through the boundary
-    int status;          // bit 0 non-finite value, bit 1 no wet cell, bit 2 a tile's edge list overflowed
+    int status;          // ST_* bits
     int pad;
 };
 
-enum { ST_NONFINITE = 1, ST_DRY = 2, ST_TILE = 4 };
+// Status bits: a non-finite value, no wet cell for the CFL rule, a tile's edge
+// list outgrew its plan, a bulk copy into shared memory did not complete.
+enum { ST_NONFINITE = 1, ST_DRY = 2, ST_TILE = 4, ST_TIMEOUT = 8 };
 enum { MODE_EULER = 0, MODE_STAGE = 1 };
 
 template <typename T> struct DevMesh {
@@ -69,14 +71,17 @@ template <typename T> struct StepArgs {
     T level[SWE_MAX_GROUPS];    // fixed free-surface levels [m]
 };
 
-// One-pass tile step (swe_tile.cu, plan built by swe_tiles.cpp): tile b is
-// the cells [b * tile, min((b + 1) * tile, n)), one per thread; emax and
-// xmax bound one tile's edges inside the tile and its crossing edges (its
-// shared memory).
+// One-pass tile step (swe_tile.cu, plan built by swe_tiles.cpp, layout in
+// swe_tiles.h): tile b is the cells [b * tile, min((b + 1) * tile, n)), one
+// per thread; the maxima over the tiles size the block's shared memory.
 struct TileArgs {
     int64_t n_tiles;
+    const int32_t *plan_hdr;     // [4 n_tiles] per tile: plan-word offset, halo cells, H1 cells, crossing edges
+    const int32_t *plan_words;   // halo ids, H1 neighbour words, far H1 index of each crossing edge
     int tile;
-    int emax, xmax;
+    int emax, xmax;              // room for edges inside a tile and crossing edges
+    int hmax, h1max, wmax;       // room for halo cells, H1 cells and plan words
+    int grid;                    // blocks of the persistent launch (resident blocks on this GPU)
 };
 
 // Launchers (defined in swe_kernels.cu and swe_tile.cu).  All launches go to `stream`.
@@ -103,8 +108,9 @@ cudaError_t launch_convert(int64_t n, const double *src, T *dst, cudaStream_t s)
 
 // The tile step: one launch advances every tile.
 template <typename T> cudaError_t launch_tile(int scheme, const StepArgs<T> &a, const TileArgs &t, cudaStream_t s);
-template <typename T> size_t tile_smem_bytes(int tile, int emax, int xmax);
+template <typename T> size_t tile_smem_bytes(const TileArgs &t);
 template <typename T> int tile_max_threads(int scheme);     // launch limit of the tile kernel (registers)
+template <typename T> int tile_grid(int scheme, int tile, size_t smem);   // resident blocks (persistent grid)
 template <typename T> cudaError_t tile_prepare(int scheme, size_t smem);   // shared-memory attribute, once
 
 // Boundary-first schedule: flux over a list of cells (a.cells, a.n_list), and

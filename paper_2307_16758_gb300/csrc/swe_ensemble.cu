@@ -45,9 +45,9 @@ __global__ void __maxnreg__((sizeof(T) == 4 ? 48 : 255))
 
 template <typename T>
 cudaError_t launch_ensemble(int scheme, bool hr2, bool fused, const EnsEntry<T> *tab, const int2 *blk, int phase,
-                            int grid, int block, size_t smem, cudaStream_t s)
+                            int grid, int block, const TileArgs &room, cudaStream_t s)
 {
-    if (fused) return launch_tile_ensemble<T>(scheme, tab, blk, phase, grid, block, smem, s);
+    if (fused) return launch_tile_ensemble<T>(scheme, tab, blk, phase, grid, block, room, s);
     if (scheme == SWE_SCHEME_MUSCL && hr2) {
         k_prep_ens<T, FLUX_MUSCL_HR2><<<grid, block, 0, s>>>(tab, blk, phase);
         k_flux_ens<T, FLUX_MUSCL_HR2><<<grid, block, 0, s>>>(tab, blk, phase);
@@ -102,8 +102,8 @@ template int ensemble_max_threads<float>(int, bool, bool);
 template int ensemble_max_threads<double>(int, bool, bool);
 
 template cudaError_t launch_ensemble<float>(int, bool, bool, const EnsEntry<float> *, const int2 *, int, int, int,
-                                            size_t, cudaStream_t);
+                                            const TileArgs &, cudaStream_t);
 template cudaError_t launch_ensemble<double>(int, bool, bool, const EnsEntry<double> *, const int2 *, int, int, int,
-                                             size_t, cudaStream_t);
+                                             const TileArgs &, cudaStream_t);
 template cudaError_t ensemble_prepare<float>(int, bool, size_t);
 template cudaError_t ensemble_prepare<double>(int, bool, size_t);

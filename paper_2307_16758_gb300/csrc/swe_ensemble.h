@@ -14,16 +14,16 @@ template <typename T> struct EnsEntry {
 // Block b of a batched launch runs block blk[b].y of member blk[b].x.  One
 // launch (two for the split kernels with a prep pass) advances every member
 // by one step of the given phase.  hr2: the members use the second-order
-// hydrostatic reconstruction (all or none of them).  smem: dynamic shared
-// memory of the tile kernel (the members' largest).
+// hydrostatic reconstruction (all or none of them).  room: the tile kernel's
+// shared-memory room, the members' largest.
 template <typename T>
 cudaError_t launch_ensemble(int scheme, bool hr2, bool fused, const EnsEntry<T> *tab, const int2 *blk, int phase,
-                            int grid, int block, size_t smem, cudaStream_t s);
+                            int grid, int block, const TileArgs &room, cudaStream_t s);
 template <typename T> cudaError_t ensemble_prepare(int scheme, bool fused, size_t smem);
 // The batched tile kernel (swe_tile.cu, beside the single-mesh one so that both run one compiled body).
 template <typename T>
-cudaError_t launch_tile_ensemble(int scheme, const EnsEntry<T> *tab, const int2 *blk, int phase, int grid, int block,
-                                 size_t smem, cudaStream_t s);
+cudaError_t launch_tile_ensemble(int scheme, const EnsEntry<T> *tab, const int2 *blk, int phase, int n_total, int block,
+                                 const TileArgs &room, cudaStream_t s);
 template <typename T> cudaError_t tile_ensemble_prepare(int scheme, size_t smem);
 template <typename T> int tile_ensemble_max_threads(int scheme);
 // The largest block that every batched kernel of this configuration launches with.

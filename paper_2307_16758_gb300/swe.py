@@ -20,7 +20,8 @@ LIB_PATH = os.path.join(HERE, "libswe.so")
 
 SWE_OK = 0
 ERRORS = {-1: "SWE_ERR_ARG", -2: "SWE_ERR_MESH", -3: "SWE_ERR_CUDA", -4: "SWE_ERR_DRY",
-          -5: "SWE_ERR_NONFINITE", -7: "SWE_ERR_NOMEM"}
+          -5: "SWE_ERR_NONFINITE", -6: "SWE_ERR_TIMEOUT",
+          -7: "SWE_ERR_NOMEM"}
 FLAG_CLIPPED, FLAG_NONFINITE, FLAG_DRY = 1, 2, 4
 SWE_WALL, SWE_OPEN, SWE_INFLOW, SWE_LEVEL = 0, 1, 2, 3
 REORDER = {"none": 0, "morton": 1, "rcm": 2}

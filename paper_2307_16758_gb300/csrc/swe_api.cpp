@@ -228,9 +228,7 @@ template <typename T> struct StateT {
             TileArgs t{};
             t.tile = block;
             t.n_tiles = tp.n_tiles;
-            t.emax = std::max(tp.emax, 1);
-            t.xmax = std::max(tp.xmax, 1);
-            t.hmax = (std::max(tp.hmax, 1) + 3) & ~3;          // stage alignment (see TileStage)
+            t.hmax = (std::max(tp.hmax, 1) + 7) & ~7;          // stage alignment (see TileStage)
             t.h1max = std::max(tp.h1max, 1);
             t.wmax = (std::max(tp.wmax, 8) + 7) & ~7;
             const size_t smem = tile_smem_bytes<T>(t);
@@ -723,7 +721,6 @@ template <typename T> struct EnsembleT {
             if ((int64_t)begin[m] + blocks > INT32_MAX) { swe_set_error("ensemble too large"); return SWE_ERR_ARG; }
             begin[m + 1] = begin[m] + (int)blocks;
             if (fused) {
-                room_.emax = std::max(room_.emax, s.ta.emax); room_.xmax = std::max(room_.xmax, s.ta.xmax);
                 room_.hmax = std::max(room_.hmax, s.ta.hmax); room_.h1max = std::max(room_.h1max, s.ta.h1max);
                 room_.wmax = std::max(room_.wmax, s.ta.wmax);
             }

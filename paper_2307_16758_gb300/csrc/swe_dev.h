@@ -76,10 +76,10 @@ template <typename T> struct StepArgs {
 // per thread; the maxima over the tiles size the block's shared memory.
 struct TileArgs {
     int64_t n_tiles;
-    const int32_t *plan_hdr;     // [4 n_tiles] per tile: plan-word offset, halo cells, H1 cells, crossing edges
-    const int32_t *plan_words;   // halo ids, H1 neighbour words, far H1 index of each crossing edge
+    const int32_t *plan_hdr;     // [8 n_tiles] per tile: plan-word offset, halo cells, H1 cells, edges,
+                                 //   crossing edges, plan words
+    const int32_t *plan_words;   // halo ids, edge records, local neighbour words
     int tile;
-    int emax, xmax;              // room for edges inside a tile and crossing edges
     int hmax, h1max, wmax;       // room for halo cells, H1 cells and plan words
     int grid;                    // blocks of the persistent launch (resident blocks on this GPU)
 };

@@ -16,7 +16,7 @@ using namespace swe_dev;
 // Shared-memory room of a launch.
 __host__ __device__ inline TileDims dims_of(const TileArgs &t)
 {
-    return TileDims{t.tile, t.emax, t.xmax, t.hmax, t.h1max, t.wmax};
+    return TileDims{t.tile, t.hmax, t.h1max, t.wmax};
 }
 
 // Tiles of one mesh: g is the tile index.

@@ -107,8 +107,7 @@ def roofline_entry(scheme, n, step_ms, prof, kname, peak, peak_src, traffic):
             "traffic": traffic, "peak_source": peak_src, "algo_bytes_per_cell": per_cell,
             "scope": "whole step (all launches of one time step)", "step_ms": step_ms,
             "kernel": {"name": KERNEL_NAMES.get((kname, dom), dom), "ms": dom_ms, "achieved": dom_ach,
-                       "frac": dom_ach / peak, "launches_per_step": round(prof[dom][1] / max(1, sum(
-                           c for _, c in prof.values()) / len(prof)), 3)},
+                       "frac": dom_ach / peak},
             "per_kernel_ms": {k: v[0] / v[1] for k, v in prof.items()}, "own_bytes": own}
 
 
@@ -271,8 +270,15 @@ def run_reference(args):
     import oracle
     from paper_2307_16758_gb300 import workloads as W
     oracle.build()
-    cells_sample = 200_000
-    nx, ny = W.river_grid_for_cells(cells_sample)
+    # one oracle step per bench step on the full 13M-cell river when the whole run fits in about two
+    # minutes of host time (about 55 M cell-updates/s on 16 cores); for long runs a smaller river of
+    # the same generator, sized to fit
+    full = 2 * RIVER_GRID[0] * RIVER_GRID[1]
+    cells_sample = int(min(full, 120.0 / (args.steps + args.warmup) * 55e6))
+    if cells_sample >= full:
+        nx, ny = RIVER_GRID
+    else:
+        nx, ny = W.river_grid_for_cells(cells_sample)
     w = W.river(nx, ny, seed=SEED)
     om = oracle.Mesh(w.nodes, w.tris, w.bnd_edges, w.bnd_tag)
     cores = os.cpu_count() or 1
@@ -289,15 +295,17 @@ def run_reference(args):
     el = sum(t_steps)
     value = om.n * len(t_steps) / el
     sample = (f"one FP64 MUSCL-HLLC Euler step per bench step on the river generator at {om.n} cells "
-              f"({nx}x{ny} grid, same recipe as the 13M workload), OpenMP over cells")
+              f"({nx}x{ny} grid" + (", the full workload" if om.n == full else ", same recipe as the 13M workload") +
+              "), OpenMP over cells")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / len(t_steps),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"river {RIVER_GRID[0]}x{RIVER_GRID[1]} jittered grid, "
                                f"{2 * RIVER_GRID[0] * RIVER_GRID[1]} triangles, MUSCL-HLLC, Euler, CFL 0.9, "
-                               "Morton order (the FP64 oracle on a bounded sample of the same generator)",
-                   "cells": 2 * RIVER_GRID[0] * RIVER_GRID[1], "sample_cells": om.n, "scheme": "muscl",
+                               "Morton order" + ("" if om.n == full else
+                                                 " (the FP64 oracle on a smaller river of the same generator)"),
+                   "cells": full, "sample_cells": om.n, "same_config": om.n == full, "scheme": "muscl",
                    "precision": "fp64"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -429,12 +437,15 @@ def run_gpu(args):
     if c32 and "dram_bytes_per_cell" in c32:
         out["roofline"]["dram_bytes_per_cell_measured"] = c32["dram_bytes_per_cell"]
     if rank == 0 and not args.quick:
-        out.update(fp64_comparison(args, mesh, w, swe, torch))
+        out.update(fp64_comparison(args, mesh, w, swe, torch, p32))
         out["fp64"]["fp32_speedup"] = out["fp64"]["ms_per_step"] / step_ms
         out["alu_peaks"] = alu_peaks(swe, torch, local, clocks)
         out["fp64"]["roofline"] = fp64_alu_roofline(out["fp64"], out["alu_peaks"], kname, skey, n)
         if ws == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(w, n)
+        if ws == 1 and not args.no_extras:
+            out["river_4m"] = river4m_study(args, swe, torch)
+            out["ensemble_40m"] = ensemble_study(args, swe, torch)
     if rank == 0:
         print(json.dumps(out))
     st.close()
@@ -473,11 +484,14 @@ def fp64_alu_roofline(fp64, peaks, kname, skey, n):
             "peak_source": "measured FP64 FMA rate (swe_fma_peak)", "kernel_ms": ms}
 
 
-def fp64_comparison(args, mesh, w, swe, torch):
-    """FP64 GPU path: its throughput, and the FP32 error against it at matched time."""
+def fp64_comparison(args, mesh, w, swe, torch, p32_timed):
+    """FP64 GPU path: its throughput, and the error of the timed FP32 configuration against it at
+    matched time.  The FP64 run takes the FP32 run's thresholds (h_eps, r_eps: same algorithm, only
+    the precision differs) and config 3's step count; the FP32 run replays its time steps."""
     n = mesh.n
     m_steps = args.fp64_steps
     p64 = swe.swe_params_default(args.scheme, "fp64", kernel=args.kernel, hr_order=args.hr_order)
+    p64.h_eps, p64.r_eps = p32_timed.h_eps, p32_timed.r_eps
     s64 = swe.State.from_workload(mesh, p64, w)
     s64.step(3, args.cfl)
     s64.sync()
@@ -497,40 +511,41 @@ def fp64_comparison(args, mesh, w, swe, torch):
     s64.profile_begin()
     s64.step(10, args.cfl)
     prof64 = s64.profile_end()
-    p32 = swe.swe_params_default(args.scheme, "fp32", kernel=args.kernel, hr_order=args.hr_order)
-    p32.h_eps = p64.h_eps         # same algorithm, precision differs only
-    p32.r_eps = p64.r_eps
-    s32 = swe.State.from_workload(mesh, p32, w)
+    s32 = swe.State.from_workload(mesh, p32_timed, w)
     m0 = s32.mass()[0]
     s32.step_dt(dts)
     h32, hu32, hv32 = s32.get_state()
     mass32 = s32.mass()
-    qs = max(np.abs(hu64).max(), np.abs(hv64).max())
-    # the river starts at rest away from its inflow, and cells still at rest are exact in both
-    # precisions: the error is also stated over the cells the flow has reached, and against
-    # the FP64 change of h since t = 0
-    act = (h64 != w.h) | (hu64 != 0) | (hv64 != 0)
-    dh = np.abs(h64 - w.h)[act].sum()
-    err = {
-        "steps": m_steps, "t_end": float(np.sum(dts)),
-        "l1_h": rel_l1(h32, h64), "linf_h": rel_inf(h32, h64),
-        "l1_hu": rel_l1(hu32, hu64), "linf_hu": float(np.abs(hu32 - hu64).max() / qs),
-        "l1_hv": rel_l1(hv32, hv64), "linf_hv": float(np.abs(hv32 - hv64).max() / qs),
-        "mass_drift_fp32": abs(mass32[0] - m0 - mass32[1] - mass32[2]) / m0,
-        "mass_drift_fp64": abs(mass64[0] - m0 - mass64[1] - mass64[2]) / m0,
-        "h_eps": p64.h_eps,
-        "active_cells": int(act.sum()),
-        "l1_h_active": rel_l1(h32[act], h64[act]) if act.any() else 0.0,
-        "l1_h_vs_change": float(np.abs(h32 - h64)[act].sum() / dh) if dh > 0 else 0.0,
-        "l1_q_active": float((np.abs(hu32 - hu64) + np.abs(hv32 - hv64))[act].sum()
-                             / max((np.abs(hu64) + np.abs(hv64))[act].sum(), 1e-300)),
-    }
+    err = state_error(w, h32, hu32, hv32, h64, hu64, hv64)
+    err.update({"steps": m_steps, "t_end": float(np.sum(dts)), "h_eps": p32_timed.h_eps, "r_eps": p32_timed.r_eps,
+                "thresholds": "the timed FP32 run's h_eps and r_eps on both sides",
+                "mass_drift_fp32": abs(mass32[0] - m0 - mass32[1] - mass32[2]) / m0,
+                "mass_drift_fp64": abs(mass64[0] - m0 - mass64[1] - mass64[2]) / m0})
     s32.close()
     s64.close()
     v64 = n * m_steps / (ms64 / 1e3)
     return {"fp64": {"value": v64, "unit": UNIT, "ms_per_step": ms64 / m_steps, "steps": m_steps,
                      "per_kernel_ms": {k: v[0] / v[1] for k, v in prof64.items()}},
             "error_fp32_vs_fp64": err}
+
+
+def state_error(w, h32, hu32, hv32, h64, hu64, hv64):
+    """Relative L1 / Linf of h and the discharges, first over the cells the flow has reached (a cell
+    still at rest is exact in both precisions, so the whole-mesh figure dilutes the error), then over
+    the mesh; and L1 of h against the FP64 change of h since t = 0."""
+    qs = max(np.abs(hu64).max(), np.abs(hv64).max(), 1e-300)
+    act = (h64 != w.h) | (hu64 != 0) | (hv64 != 0)
+    dh = np.abs(h64 - w.h)[act].sum()
+    return {
+        "active_cells": int(act.sum()),
+        "l1_h_active": rel_l1(h32[act], h64[act]) if act.any() else 0.0,
+        "l1_q_active": float((np.abs(hu32 - hu64) + np.abs(hv32 - hv64))[act].sum()
+                             / max((np.abs(hu64) + np.abs(hv64))[act].sum(), 1e-300)),
+        "l1_h_vs_change": float(np.abs(h32 - h64)[act].sum() / dh) if dh > 0 else 0.0,
+        "l1_h": rel_l1(h32, h64), "linf_h": rel_inf(h32, h64),
+        "l1_hu": rel_l1(hu32, hu64), "linf_hu": float(np.abs(hu32 - hu64).max() / qs),
+        "l1_hv": rel_l1(hv32, hv64), "linf_hv": float(np.abs(hv32 - hv64).max() / qs),
+    }
 
 
 def cpu_baseline(w, n):
@@ -556,17 +571,11 @@ def cpu_baseline(w, n):
                       f"(mesh build excluded), OpenMP over cells"}
 
 
-def run_ensemble(args):
-    """64 river scenarios of uneven size (40M cells in total), MUSCL-HLLC FP32,
-    one batched launch per step (autotuned) against one launch per member."""
-    import torch
-
-    from paper_2307_16758_gb300 import swe
+def ensemble_study(args, swe, torch):
+    """64 river scenarios of uneven size (40M cells in total), MUSCL-HLLC FP32, one batched launch
+    per step (autotuned) against one launch sequence per member; per-member FP32 error against the
+    FP64 path (at the FP32 thresholds) after a bounded number of replayed steps."""
     from paper_2307_16758_gb300 import workloads as W
-    import __graft_entry__
-
-    __graft_entry__.build()
-    swe.load_library()
     stream = torch.cuda.current_stream()
     sizes = W.ensemble_sizes(n_members=args.members, total=int(40_000_000 * args.scale))
     ws = [W.ensemble_member(k, int(c)) for k, c in enumerate(sizes)]
@@ -576,81 +585,144 @@ def run_ensemble(args):
     states = [swe.State.from_workload(m, p, w) for m, w in zip(meshes, ws)]
     ens = swe.Ensemble(states)
     kernel, block, tune_ms = ens.autotune(meshes, trial_steps=4)
+    steps = max(args.steps, 24)
     ens.step(args.warmup, args.cfl)
     ens.sync()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    ens.step(args.steps, args.cfl)
+    ens.step(steps, args.cfl)
     e1.record(stream)
     e1.synchronize()
-    ms_batched = e0.elapsed_time(e1) / args.steps
+    ms_batched = e0.elapsed_time(e1) / steps
     # one launch sequence per member per step
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         for st in states:
             st.step(1, args.cfl)
     e1.record(stream)
     e1.synchronize()
-    ms_separate = e0.elapsed_time(e1) / args.steps
+    ms_separate = e0.elapsed_time(e1) / steps
     ens.sync()
     wet = sum(int((st.get_state()[0] > p.h_eps).sum()) for st in states) / n     # prep's bytes depend on it
-    # per-member FP32 error against the FP64 GPU path at matched time
+    ens.close()
+    for st in states:
+        st.close()
+    # per-member FP32 error against the FP64 GPU path at matched time, same thresholds
     m_steps = min(args.fp64_steps, 200)
     errs = []
     p64 = swe.swe_params_default("muscl", "fp64")
+    p64.h_eps, p64.r_eps = p.h_eps, p.r_eps
     for m, w in zip(meshes, ws):
         s64 = swe.State.from_workload(m, p64, w)
         s64.step(m_steps, args.cfl)
         dts = s64.dt_history(m_steps)
         h64 = s64.get_state()[0]
-        p32 = swe.swe_params_default("muscl", "fp32")
-        p32.h_eps, p32.r_eps = p64.h_eps, p64.r_eps
-        s32 = swe.State.from_workload(m, p32, w)
+        s32 = swe.State.from_workload(m, p, w)
         s32.step_dt(dts)
         h32 = s32.get_state()[0]
-        errs.append(rel_l1(h32, h64))
+        act = (h64 != w.h)
+        errs.append((rel_l1(h32, h64), rel_l1(h32[act], h64[act]) if act.any() else 0.0))
         s64.close()
         s32.close()
-    print(json.dumps({
-        "metric": "cell-updates/s, batched ensemble (MUSCL-HLLC FP32)", "value": n / (ms_batched / 1e3),
-        "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_batched,
-        "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"ensemble of {len(ws)} river scenarios, {n} cells, sizes {int(sizes.min())}"
-                               f"-{int(sizes.max())}", "kernel": kernel, "block": block},
-        "separate_launches": {"value": n / (ms_separate / 1e3), "ms_per_step": ms_separate,
-                              "launches_per_step": len(ws) * 2},
-        "autotune_ms_per_step": tune_ms,
-        "error_fp32_vs_fp64_l1_h": {"steps": m_steps, "max": max(errs), "median": float(np.median(errs))},
-        # the whole batched step against the HBM copy rate: prep's and flux's algorithmic bytes per cell
-        "roofline": ensemble_roofline(kernel, n, ms_batched, wet),
-    }))
-
-
-def split_step_roofline(scheme, kname, st, h_eps, n, step_ms, peak):
-    """The whole step of the split kernels against the HBM copy rate: the sum of the kernels'
-    algorithmic bytes per cell-update (MUSCL prep: 100 B for a wet cell, 56 B for a dry one, at the
-    state's wet fraction) over the step time."""
-    if kname != "split" or scheme not in ("muscl", "muscl_edge"):
-        return None
-    h = st.get_state()[0]
-    wet = float((h > h_eps).mean())
-    per_cell = algo_bytes("flux", scheme, "fp32") + 56.0 + (algo_bytes("prep", scheme, "fp32") - 56.0) * wet
-    achieved = per_cell * n / (step_ms / 1e3) / 1e9
-    return {"algo_bytes_per_cell": per_cell, "wet_fraction": wet, "achieved": achieved, "frac": achieved / peak}
-
-
-def ensemble_roofline(kernel, n, ms, wet):
-    """The batched step's algorithmic bytes per cell-update over its time: flux 116 B; prep 100 B for a
-    wet cell and 56 B for a dry one (which reads only its depth and bed), at the members' wet fraction."""
+    for m in meshes:
+        m.close()
     peak, src = measured_peaks()
-    if kernel == "fused":
-        per_cell = float(algo_bytes("fused", "muscl", "fp32"))
-    else:
-        per_cell = algo_bytes("flux", "muscl", "fp32") + 56.0 + (algo_bytes("prep", "muscl", "fp32") - 56.0) * wet
-    achieved = per_cell * n / (ms / 1e3) / 1e9
-    return {"bound": "hbm", "kernel": "the batched step (all launches)", "achieved": achieved, "peak": peak,
-            "unit": "GB/s", "frac": achieved / peak, "traffic": None, "peak_source": src,
-            "algo_bytes_per_cell": per_cell, "wet_fraction": wet}
+    per_cell = survey_bytes("muscl", "fp32")
+    ach = per_cell * n / (ms_batched / 1e3) / 1e9
+    e = np.array(errs)
+    return {
+        "workload": f"ensemble of {len(ws)} river scenarios, {n} cells, sizes {int(sizes.min())}-{int(sizes.max())}, "
+                    "own inflow, Manning n and initial level each",
+        "cells": n, "steps": steps, "kernel": kernel, "block": block, "autotune_ms_per_step": tune_ms,
+        "batched": {"value": n / (ms_batched / 1e3), "unit": UNIT, "ms_per_step": ms_batched},
+        "separate_launches": {"value": n / (ms_separate / 1e3), "unit": UNIT, "ms_per_step": ms_separate,
+                              "launches_per_step": len(ws) * (2 if kernel == "split" else 1)},
+        "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                     "algo_bytes_per_cell": per_cell, "peak_source": src, "wet_fraction": wet},
+        "error_fp32_vs_fp64": {"steps": m_steps, "h_eps": p.h_eps, "l1_h_active_max": float(e[:, 1].max()),
+                               "l1_h_active_median": float(np.median(e[:, 1])), "l1_h_max": float(e[:, 0].max())},
+    }
+
+
+def run_ensemble(args):
+    """The batched ensemble on its own (one JSON line)."""
+    import torch
+
+    from paper_2307_16758_gb300 import swe
+    import __graft_entry__
+
+    __graft_entry__.build()
+    swe.load_library()
+    r = ensemble_study(args, swe, torch)
+    print(json.dumps({"metric": "cell-updates/s, batched ensemble (MUSCL-HLLC FP32)", "value": r["batched"]["value"],
+                      "unit": UNIT, "n_gpus": 1, "steps": r["steps"], "warmup": args.warmup,
+                      "ms_per_step": r["batched"]["ms_per_step"], "higher_is_better": True, "dtype": "f32",
+                      "data": "synthetic", "config": {"workload": r["workload"], "kernel": r["kernel"],
+                                                      "block": r["block"]},
+                      "ensemble": r}))
+
+
+def river4m_study(args, swe, torch):
+    """WAF-HLLC against MUSCL-HLLC on the 4,000,920-cell river (the 13M generator at 4M cells), FP32
+    with compensated FP64 mass: GPU time per step and its HBM rate, FP32 error and mass drift against
+    the FP64 path at the FP32 thresholds after 2000 replayed steps, wetting front in both precisions."""
+    from paper_2307_16758_gb300 import workloads as W
+    stream = torch.cuda.current_stream()
+    w = W.river(2310, 866)
+    mesh = swe.Mesh.from_workload(w, "morton")
+    n = mesh.n
+    steps = 2000
+    peak, src = measured_peaks()
+    cx = w.centroids()[0]
+    dry0 = w.h <= 0.0
+
+    def front(hh):
+        m = (hh > 1e-3) & dry0
+        return float(cx[m].max()) if m.any() else None
+
+    res = {"workload": "river 2310x866 jittered grid, 4,000,920 triangles", "cells": n, "steps": steps, "schemes": {}}
+    for scheme in ("muscl", "waf"):
+        p32 = swe.swe_params_default(scheme, "fp32")
+        st = swe.State.from_workload(mesh, p32, w)
+        st.step(24, args.cfl)
+        st.sync()
+        st.close()
+        st = swe.State.from_workload(mesh, p32, w)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st.step(steps, args.cfl)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        st.close()
+        p64 = swe.swe_params_default(scheme, "fp64")
+        p64.h_eps, p64.r_eps = p32.h_eps, p32.r_eps
+        s64 = swe.State.from_workload(mesh, p64, w)
+        s64.step(steps, args.cfl)
+        dts = s64.dt_history(steps)
+        h64, hu64, hv64 = s64.get_state()
+        s64.close()
+        s32 = swe.State.from_workload(mesh, p32, w)
+        m0 = s32.mass()[0]
+        s32.step_dt(dts)
+        h32, hu32, hv32 = s32.get_state()
+        mass32 = s32.mass()
+        s32.close()
+        per_cell = survey_bytes(scheme, "fp32")
+        ach = per_cell * n / (ms / 1e3) / 1e9
+        speed = lambda hh, qx, qy: float(np.where(hh > 1e-3, np.hypot(qx, qy) / np.maximum(hh, 1e-300), 0.0).max())
+        err = state_error(w, h32, hu32, hv32, h64, hu64, hv64)
+        err["mass_drift_fp32"] = abs(mass32[0] - m0 - mass32[1] - mass32[2]) / m0
+        res["schemes"][scheme] = {
+            "value": n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+            "hbm": {"achieved": ach, "unit": "GB/s", "frac": ach / peak, "algo_bytes_per_cell": per_cell,
+                    "peak_source": src},
+            "error_fp32_vs_fp64": err, "t_end": float(np.sum(dts)),
+            "front_x": {"fp32": front(h32), "fp64": front(h64), "unit": "m"},
+            "max_speed": {"fp32": speed(h32, hu32, hv32), "fp64": speed(h64, hu64, hv64), "unit": "m/s"},
+        }
+    mesh.close()
+    return res
 
 
 def run_time_error(args):
@@ -828,10 +900,12 @@ def main():
                          "first-order HLLC or WAF-HLLC")
     ap.add_argument("--hr-order", type=int, default=1, choices=[1, 2],
                     help="hydrostatic reconstruction: 1 (cell bed) or 2 (linear bed; LSQ MUSCL only)")
-    ap.add_argument("--fp64-steps", type=int, default=1000)
+    ap.add_argument("--fp64-steps", type=int, default=2000)
     ap.add_argument("--scale", type=float, default=1.0, help="fraction of the 13M-cell mesh (testing only)")
     ap.add_argument("--quick", action="store_true", help="skip the FP64 comparison and the CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the 4M-cell WAF/MUSCL study and the 40M-cell ensemble in the default line")
     ap.add_argument("--ensemble", action="store_true", help="the 64-scenario batched ensemble instead")
     ap.add_argument("--parts", type=int, default=1,
                     help="step with the boundary-first schedule over this many Morton sub-domains")

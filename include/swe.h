@@ -59,10 +59,12 @@ enum { SWE_SCHEME_HLLC = 0, SWE_SCHEME_MUSCL = 1, SWE_SCHEME_WAF = 2, SWE_SCHEME
 enum { SWE_FP64 = 0, SWE_FP32 = 1 };
 enum { SWE_EULER = 0, SWE_HEUN = 1 };
 enum { SWE_WAF_SUPERBEE = 0, SWE_WAF_PHI1 = 1, SWE_WAF_PHI0 = 2 };
-/* Quantity of the WAF ratios r_L, r_R: the depth h as the paper takes it
- * (Sec. 6.2.2), or the free surface eta = h + z (not in the paper: over a
- * steep bed the depth ratio reacts to the bathymetry and WAF-SUPERBEE grows
- * spurious speeds; the surface ratio equals it on a flat bed). */
+/* Quantity of the WAF ratios r_L, r_R (Sec. 6.2.2 takes the depth of the
+ * Riemann problem): SURFACE (default) the free surface eta = h + z, whose
+ * differences are those of the hydrostatically reconstructed depths
+ * h* = eta - z_f of each edge; DEPTH the cell depth h (over a steep bed it
+ * varies with the bathymetry at rest, and WAF-SUPERBEE grows spurious speeds
+ * on river-like beds).  The two are equal on a flat bed. */
 enum { SWE_WAF_RATIO_DEPTH = 0, SWE_WAF_RATIO_SURFACE = 1 };
 enum { SWE_KERNEL_AUTO = 0, SWE_KERNEL_SPLIT = 1, SWE_KERNEL_FUSED = 2 };
 /* CFL rule (Sec. 6.1, d = inscribed radius r): GLOBAL dt = CFL min_i r_i /
@@ -92,7 +94,7 @@ typedef struct {
     int hr_order;     /* hydrostatic reconstruction: 1 on the cell bed (default); 2 (SWE_SCHEME_MUSCL,
                          split kernels) second order, with the linear bed that the reconstructed
                          eta and h imply in each cell -- the paper's future work (Sec. 7) */
-    int waf_ratio;    /* SWE_WAF_RATIO_* (SWE_SCHEME_WAF; SURFACE with the split kernels only) */
+    int waf_ratio;    /* SWE_WAF_RATIO_* (used by SWE_SCHEME_WAF only) */
 } swe_params;
 
 /* Values of the boundary groups (copied at init). */
@@ -107,7 +109,7 @@ const char *swe_last_error(void);
 
 /* Defaults: g = 9.81, h_eps = 1e-6 (FP64) or 1e-4 (FP32),
  * r_eps = 1e-12 (FP64) or 1e-6 (FP32), Euler, SUPERBEE, automatic kernel,
- * global CFL form, muscl_beta = 2, hr_order = 1, waf_ratio = SWE_WAF_RATIO_DEPTH. */
+ * global CFL form, muscl_beta = 2, hr_order = 1, waf_ratio = SWE_WAF_RATIO_SURFACE. */
 int swe_params_default(swe_params *p, int scheme, int precision);
 
 /* Device memory: by default cudaMalloc/cudaFree.  A host program (for example

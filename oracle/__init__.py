@@ -72,7 +72,9 @@ def _p(a):
 
 def opts(scheme="hllc", time_scheme="euler", waf_limiter="superbee", g=9.81, h_eps=1e-6,
          r_eps=1e-12, cfl=0.9, threads=0, cfl_mode="global", beta=2.0, hr_order=1,
-         waf_ratio="depth") -> _Opts:
+         waf_ratio="surface") -> _Opts:
+    """waf_ratio: the quantity of the WAF ratios, "surface" (eta, reading R4, the default) or
+    "depth" (the cell depth h, option R17)."""
     return _Opts(SCHEMES[scheme], {"euler": 0, "heun": 1}[time_scheme],
                  {"superbee": 0, "phi1": 1, "phi0": 2}[waf_limiter], threads,
                  g, h_eps, r_eps, cfl, {"global": 0, "local": 1}[cfl_mode], beta, hr_order,

@@ -27,7 +27,13 @@
  *      sgn(0)=+1.  The weights sum to 1; phi=1 gives the unlimited weights.
  *  R4  WAF on triangles: dx = |c_R - c_L|; r = 0 when the local change is
  *      below r_eps*max(1,|q_L|,|q_R|); a missing upwind cell uses the cell
- *      itself; boundary edges use the first-order HLLC boundary flux.
+ *      itself; boundary edges use the first-order HLLC boundary flux.  The
+ *      ratios' quantity q for the nonlinear waves: the paper takes the depth
+ *      of the Riemann problem; with the hydrostatic reconstruction (Sec.
+ *      6.2.3) that problem is posed on h*_s = eta_s - z_f, whose differences
+ *      are those of the free surface eta (z_f is one value per edge), so the
+ *      ratios are taken on eta (default; on a flat bed it is the cell depth's
+ *      ratio exactly).  The cell depth h itself remains an option (R17).
  *  R5  Dry sides of the Riemann problem (h* <= h_eps): Toro's dry-bed speeds;
  *      both sides dry gives a zero numerical flux.
  *  R6  Bed and hydrostatic reconstruction: piecewise-constant bed per cell;
@@ -73,10 +79,10 @@
  *      the side's cell, the other cell or one of its upwind cells is dry;
  *      boundary edges use the cell-centre values.  HR, Riemann flux and
  *      update are those of the other schemes.
- *  R17 WAF ratio on the free surface (an option; Sec. 6.2.2 takes the depth):
- *      r_L and r_R use eta = h + z for the cell values and the upwind means,
- *      so that the limiter sees waves and not the bed; on a flat bed it is
- *      the depth ratio exactly.
+ *  R17 WAF ratio on the cell depth h (an option; the default of R4 takes
+ *      eta): over a steep bed h varies with the bed even at rest, the limiter
+ *      reacts to the bathymetry, and on the river workload WAF-SUPERBEE grows
+ *      spurious speeds next to the inflow until it blows up (R14).
  */
 #include "swe_oracle.h"
 
@@ -634,7 +640,7 @@ static void face_values(const om_mesh *m, const om_opts *o, const work_t *w, con
 
 /* mean of q and of the velocity over the two other neighbours of cell i
  * (its edges k+1 and k+2); a missing neighbour stands in with cell i (R4).
- * q is the depth h, or the free surface eta with the option of R17. */
+ * q is the free surface eta (R4), or the depth h with the option of R17. */
 static void upwind_means(const om_mesh *m, const work_t *w, const double *q, int64_t i, int k,
                          double *hm, double *um, double *vm)
 {
@@ -772,7 +778,7 @@ static void euler_stage(const om_mesh *m, const om_opts *o, work_t *w,
                 double out[4];
                 if (scheme == 2) {
                     double hma, uma, vma, hmb, umb, vmb;
-                    const double *q = o->waf_surface ? w->eta : h;     /* R17 */
+                    const double *q = o->waf_surface ? w->eta : h;     /* R4 / R17 */
                     upwind_means(m, w, q, a, ka, &hma, &uma, &vma);
                     upwind_means(m, w, q, b, kb, &hmb, &umb, &vmb);
                     double ddx = m->cx[b] - m->cx[a], ddy = m->cy[b] - m->cy[a];

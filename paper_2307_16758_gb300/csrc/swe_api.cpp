@@ -855,8 +855,7 @@ bool valid_params(const swe_params *p)
            (p->scheme != SWE_SCHEME_MUSCL_EDGE || (p->muscl_beta >= 1.0 && p->muscl_beta <= 2.0)) &&
            (p->scheme != SWE_SCHEME_MUSCL_EDGE || p->kernel != SWE_KERNEL_FUSED) &&
            (p->hr_order == 1 || (p->hr_order == 2 && p->scheme == SWE_SCHEME_MUSCL && p->kernel != SWE_KERNEL_FUSED)) &&
-           (p->waf_ratio == SWE_WAF_RATIO_DEPTH ||
-            (p->waf_ratio == SWE_WAF_RATIO_SURFACE && p->scheme == SWE_SCHEME_WAF && p->kernel != SWE_KERNEL_FUSED));
+           (p->waf_ratio == SWE_WAF_RATIO_DEPTH || p->waf_ratio == SWE_WAF_RATIO_SURFACE);
 }
 
 template <typename T>
@@ -968,7 +967,7 @@ int swe_params_default(swe_params *p, int scheme, int precision)
     p->cfl_mode = SWE_CFL_GLOBAL;
     p->muscl_beta = 2.0;
     p->hr_order = 1;
-    p->waf_ratio = SWE_WAF_RATIO_DEPTH;
+    p->waf_ratio = SWE_WAF_RATIO_SURFACE;
     return SWE_OK;
 }
 

@@ -69,16 +69,18 @@ def test_single_process_needs_no_group():
     assert ms == 2.0 and value == pytest.approx(500 * 4 / 2e-3)
 
 
-def test_step_byte_counts_follow_the_wet_fraction():
-    """Host arithmetic of the bench's whole-step figures: the split step moves the flux kernel's
-    116 B plus prep's 56 B (dry) to 100 B (wet) per cell; the fused kernel 68 B."""
+def test_roofline_uses_the_survey_bytes_per_cell_update():
+    """Host arithmetic of the bench's roofline: algorithmic bytes per cell-update are 92 (FP32 MUSCL
+    and WAF), 68 (FP32 first-order HLLC), 172 and 124 in FP64; the line's frac is the whole step at
+    those bytes over the measured copy rate, and the dominant kernel is reported by the same count."""
     import sys
     sys.path.insert(0, ROOT)
     import bench
-    assert bench.algo_bytes("flux", "muscl", "fp32") == 116 and bench.algo_bytes("prep", "muscl", "fp32") == 100
-    assert bench.algo_bytes("fused", "muscl", "fp32") == 68 and bench.algo_bytes("flux", "hllc", "fp32") == 68
-    for wet, per_cell in ((0.0, 172.0), (0.5, 194.0), (1.0, 216.0)):
-        r = bench.ensemble_roofline("split", 1_000_000, 1.0, wet)
-        assert r["algo_bytes_per_cell"] == per_cell
-        assert abs(r["achieved"] - per_cell * 1e6 / 1e-3 / 1e9) < 1e-9 and abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
-    assert bench.ensemble_roofline("fused", 10, 1.0, 0.3)["algo_bytes_per_cell"] == 68.0
+    assert [bench.survey_bytes(s, "fp32") for s in ("muscl", "waf", "hllc")] == [92, 92, 68]
+    assert [bench.survey_bytes(s, "fp64") for s in ("muscl", "hllc")] == [172, 124]
+    prof = {"prep": (0.2 * 10, 10), "flux": (0.3 * 10, 10)}        # (total ms, launches)
+    r = bench.roofline_entry("muscl", 1_000_000, 0.5, prof, "split", 5000.0, "measured", None)
+    assert abs(r["achieved"] - 92 * 1e6 / 0.5e-3 / 1e9) < 1e-9 and abs(r["frac"] - r["achieved"] / 5000.0) < 1e-12
+    assert r["kernel"]["name"] == "k_flux" and abs(r["kernel"]["ms"] - 0.3) < 1e-12
+    assert abs(r["kernel"]["achieved"] - 92 * 1e6 / 0.3e-3 / 1e9) < 1e-9
+    assert r["own_bytes"]["flux"]["bytes_per_cell"] == 116 and r["own_bytes"]["prep"]["bytes_per_cell"] == 100

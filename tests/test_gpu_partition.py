@@ -106,3 +106,21 @@ def test_one_cell_per_part_same_bits(scheme):
     for a, b in zip(got, ref):
         assert np.array_equal(a, b)
     assert t_got == t_ref
+
+
+@pytest.mark.parametrize("scheme", ["hllc", "muscl", "waf"])
+@pytest.mark.parametrize("n_parts", [1, 5, 64])
+def test_schedule_against_the_oracle(scheme, n_parts):
+    """The boundary-first schedule (Sec. 6.4) against the FP64 oracle, not only against the plain
+    schedule: 1e-12 after one step and 1e-9 after 100 steps with the oracle's time steps replayed,
+    on a river with inflow, fixed level, friction and dry banks."""
+    from gpu_common import run_oracle, state_errors
+
+    w = W.river(nx=90, ny=34, seed=13, q_in=2500.0)
+    o1 = run_oracle(w, scheme, steps=1)
+    (g1, _, _), *_ = _run(w, scheme, "fp64", n_parts, dt=o1["dts"])
+    assert max(state_errors(dict(h=g1[0], hu=g1[1], hv=g1[2]), o1)) <= 1e-12
+    o = run_oracle(w, scheme, steps=100)
+    (g, (t, k), _), *_ = _run(w, scheme, "fp64", n_parts, dt=o["dts"])
+    assert max(state_errors(dict(h=g[0], hu=g[1], hv=g[2]), o)) <= 1e-9
+    assert k == 100 and abs(t - o["t"]) <= 1e-12 * o["t"]

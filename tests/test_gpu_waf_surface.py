@@ -1,7 +1,7 @@
-"""WAF with its ratios on the free surface (SWE_WAF_RATIO_SURFACE, reading R17) on the GPU against the
-FP64 oracle, with the same bars as the paper's depth ratio, plus the properties that pin it: the
-same bits as the depth ratio on a flat bed, an exact lake at rest, mass, and a bounded run on a
-river where the depth ratio grows spurious speeds."""
+"""WAF with its ratios on the free surface (SWE_WAF_RATIO_SURFACE, the default reading R4) on the GPU
+against the FP64 oracle, with the same bars as the cell-depth ratio (option R17), plus the properties
+that pin it: the same bits as the depth ratio on a flat bed, an exact lake at rest, mass, and a
+bounded run on a river where the depth ratio grows spurious speeds."""
 import numpy as np
 import pytest
 
@@ -29,14 +29,14 @@ def test_fp64_one_step_and_100_steps(workload):
     o = run_oracle(w, "waf", steps=100, **S)
     g = run_gpu(w, "waf", dt=o["dts"], **S)
     assert max(state_errors(g, o)) <= 1e-9
-    od = run_oracle(w, "waf", dt=o["dts"])
+    od = run_oracle(w, "waf", dt=o["dts"], waf_ratio="depth")
     assert max(state_errors(g, od)) > 1e-7           # over a bed the surface ratio is a different scheme
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_flat_bed_gives_the_depth_ratio_bits(precision):
     w = W.dam_break_1d(120, 8, 10.0, 1.0, 1.0, 0.5, x_dam=5.0)
-    a = run_gpu(w, "waf", precision, steps=150)
+    a = run_gpu(w, "waf", precision, steps=150, waf_ratio="depth")
     b = run_gpu(w, "waf", precision, steps=150, **S)
     for k in ("h", "hu", "hv"):
         assert np.array_equal(a[k], b[k])
@@ -85,8 +85,7 @@ def test_ensemble_members_match_stepping_alone():
         m.close()
 
 
-@pytest.mark.parametrize("kw", [dict(scheme="waf", kernel="fused"), dict(scheme="muscl"), dict(scheme="hllc"),
-                                dict(scheme="waf", waf_ratio=2)])
+@pytest.mark.parametrize("kw", [dict(scheme="waf", kernel="fused"), dict(scheme="waf", waf_ratio=2)])
 def test_unsupported_combinations_are_rejected(kw):
     kw = dict(kw)
     scheme = kw.pop("scheme")
@@ -98,8 +97,9 @@ def test_unsupported_combinations_are_rejected(kw):
 
 
 def test_bounded_speeds_on_a_river():
-    """120,000-cell river, 3000 FP32 CFL steps: the free-surface ratio keeps every speed below
-    10 m/s (the depth ratio passes 10^4 m/s on this run in the oracle by step 1000)."""
+    """120,000-cell river, 3000 FP32 CFL steps: the free-surface ratio (the default reading) keeps
+    every speed below 10 m/s (the cell-depth ratio passes 10^4 m/s on this run in the oracle by
+    step 1000)."""
     w = W.river(400, 150)
     m = swe.Mesh.from_workload(w)
     st = swe.State.from_workload(m, swe.swe_params_default("waf", "fp32", **S), w)

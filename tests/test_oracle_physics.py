@@ -635,7 +635,7 @@ def test_fixed_level_boundary_fills_to_its_level():
 
 
 # --------------------------------------------------------------------------
-# WAF ratio on the free surface (R17, an option next to the paper's depth ratio)
+# WAF ratios on the free surface (the default reading R4) against the cell depth (option R17)
 # --------------------------------------------------------------------------
 
 def test_waf_surface_ratio_is_the_depth_ratio_on_a_flat_bed():
@@ -645,7 +645,7 @@ def test_waf_surface_ratio_is_the_depth_ratio_on_a_flat_bed():
                      (W.circular_dam_break(n=16, radius=6.0, half=16.0), 60)):
         assert not w.z.any()
         m = _mesh(w)
-        a = oracle.run(m, oracle.opts("waf"), w.z, w.nman, w.h, w.hu, w.hv, steps)
+        a = oracle.run(m, oracle.opts("waf", waf_ratio="depth"), w.z, w.nman, w.h, w.hu, w.hv, steps)
         b = oracle.run(m, oracle.opts("waf", waf_ratio="surface"), w.z, w.nman, w.h, w.hu, w.hv, steps)
         for x, y in zip(a[:3], b[:3]):
             assert np.array_equal(x, y)
@@ -669,7 +669,7 @@ def test_waf_surface_ratio_conserves_mass_rotates_and_differs_over_a_bed():
     h, hu, hv, dts, d = oracle.run(m, o, w.z, w.nman, w.h, w.hu, w.hv, 300)
     m0 = m.mass(w.h)
     assert abs(m.mass(h) - m0 - d["clipped"]) <= 1e-13 * m0
-    hd, *_ = oracle.run(m, oracle.opts("waf"), w.z, w.nman, w.h, w.hu, w.hv, 300, dt=dts)
+    hd, *_ = oracle.run(m, oracle.opts("waf", waf_ratio="depth"), w.z, w.nman, w.h, w.hu, w.hv, 300, dt=dts)
     assert np.abs(h - hd).max() > 1e-6                  # over a bed the two ratios differ
     w = W.partial_dam_break(nx=24, ny=12, spacing=1.0, n_gauss=8, seed=5)
     w.hu = 0.1 * w.h

@@ -86,9 +86,12 @@ typedef struct {
     double g;         /* gravity [m/s^2] */
     double h_eps;     /* depth below which a cell counts as dry [m] */
     double r_eps;     /* WAF: relative size of a local change treated as zero */
-    int kernel;       /* SWE_KERNEL_*: split (face values in scratch) or fused tile kernel */
-    int block;        /* threads per block of the flux or fused kernel (0: default; the
-                         split prep kernels use 128 unless swe_autotune picks another) */
+    int kernel;       /* SWE_KERNEL_SPLIT: prep + flux kernels (face values in scratch);
+                         SWE_KERNEL_FUSED: the one-pass tile step (LSQ MUSCL or HLLC, hr_order 1);
+                         SWE_KERNEL_AUTO: the tile step in FP64 where it applies, else split */
+    int block;        /* threads per block of the flux kernel, or cells per tile of the tile step
+                         (a power of two, 32 .. 1024); 0: 256, or 128 for FP64 tiles (the split prep
+                         kernels use 128 unless swe_autotune picks another) */
     int cfl_mode;     /* SWE_CFL_GLOBAL (default) or SWE_CFL_LOCAL */
     double muscl_beta; /* SWE_SCHEME_MUSCL_EDGE limiter, 1 (MINBEE) .. 2 (SUPERBEE, default) */
     int hr_order;     /* hydrostatic reconstruction: 1 on the cell bed (default); 2 (SWE_SCHEME_MUSCL,
@@ -249,11 +252,11 @@ int swe_fma_peak(int precision, int iters, void *stream, double *flops_per_s);
  *     >= 0; stream a cudaStream_t.
  * Outputs h_out, hu_out, hv_out[n]: no output may overlap another output or
  * any input (else SWE_ERR_ARG).
- * The face values (48 bytes per cell) go to a scratch array compiled into
- * the library (about 12.6 MB per GPU, held until the process exits), so
+ * The face values (48 bytes per wet cell) go to a scratch array compiled
+ * into the library (about 12.6 MB per GPU, held until the process exits), so
  * n_cells must not exceed SWE_NOALLOC_MAX_CELLS (else SWE_ERR_ARG).  The
  * first call on a GPU looks the array up (cudaGetSymbolAddress) with that GPU
- * current: make it before any stream capture.  All calls on a GPU share the
+ * current.  All calls on a GPU share the
  * array, so calls that overlap on the GPU race.  Each call enqueues three
  * kernels on `stream` (dt travels as a kernel argument, nothing is copied
  * from the host) and returns without waiting; no status is read back. */
@@ -267,14 +270,15 @@ int swe_muscl_step_noalloc(int64_t n_cells, const int32_t *nbr, const float *ln,
 /* ---- Autotuner ----------------------------------------------------------- */
 
 /* Not in the paper.  Time trial_steps CFL steps of each kernel configuration
- * (split kernels with 128/256/512 threads per block; for MUSCL and WAF also
- * the fused tile kernel with 128/256) on a copy of the current state and keep
- * the fastest; the simulation state, time and step count are left as they
- * were (every configuration computes the same bits).  m is the state's mesh
- * (needed to tile it for the fused kernel; NULL limits the search to the split
- * kernels).  With the split kernels it then times the prep kernel's own
- * block size (64/128/256 threads; 128 until tuned).  Outputs (may be NULL):
- * SWE_KERNEL_*, threads per block of the flux (or fused) kernel, ms per step. */
+ * (split kernels with 128/256/512 threads per block; for LSQ MUSCL and HLLC
+ * with hr_order 1 also the tile step with tiles of 128/256/512 cells) on a
+ * copy of the current state and keep the fastest; the simulation state, time
+ * and step count are left as they were (every configuration computes the
+ * same bits).  m is the state's mesh (needed to plan the tiles; NULL limits
+ * the search to the split kernels).  With the split kernels it then times the
+ * prep kernel's own block size (64/128/256 threads; 128 until tuned).
+ * Outputs (may be NULL): SWE_KERNEL_*, threads per block of the flux kernel
+ * or cells per tile, ms per step. */
 int swe_autotune(swe_state *s, const swe_mesh *m, int trial_steps, double cfl, int *kernel, int *block,
                  double *ms_per_step);
 

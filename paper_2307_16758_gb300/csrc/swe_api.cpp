@@ -10,6 +10,7 @@
 #include <memory>
 #include <string>
 #include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include "swe_dev.h"
@@ -528,7 +529,7 @@ template <typename T> std::vector<Candidate> candidates(const StateT<T> &S, cons
         if (b <= ls) c.push_back({false, b});
     if (S.tile_capable() && m && !S.sched) {
         const int lf = tile_max_threads<T>(S.p.scheme);
-        for (int b : {256, 512})
+        for (int b : {128, 256, 512})
             if (b <= lf) c.push_back({true, b});
     }
     return c;
@@ -919,9 +920,15 @@ int state_init(StateT<T> &s, const swe_mesh *m, const double *h, const double *h
     CK(cudaMemcpyAsync(s.area, m->area.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(s.sc, 0, sizeof(DevScalars), st));
     {
-        // kernel choice: the split kernels unless the one-pass tile step is requested
-        const bool want_fused = s.p.kernel == SWE_KERNEL_FUSED;
-        int rc = s.configure(want_fused, s.p.block > 0 ? s.p.block : 256, m);
+        // kernel choice (SWE_KERNEL_AUTO): the one-pass tile step, in tiles of
+        // 128 cells, for FP64, whose time is FP64 arithmetic and which gains
+        // from solving each edge once (13M river, MUSCL: 11.5 against 13.1 ms
+        // per step; HLLC: 9.7 against 13.2); the split kernels for FP32, whose
+        // time is memory traffic and instruction issue at high occupancy
+        const bool want_fused = s.p.kernel == SWE_KERNEL_FUSED ||
+                                (s.p.kernel == SWE_KERNEL_AUTO && s.tile_capable() && std::is_same<T, double>::value);
+        const int bl = s.p.block > 0 ? s.p.block : (want_fused && std::is_same<T, double>::value ? 128 : 256);
+        int rc = s.configure(want_fused, bl, m);
         if (rc) return rc;
     }
     // initial state through the same path as swe_set_state

@@ -1,7 +1,8 @@
-// Device functions shared by the split kernels (swe_kernels.cu) and the fused
-// tile kernel (swe_fused.cu): the Riemann solver of Sec. 6.2, the MUSCL face
-// values, WAF helpers and the block reductions.  Both kernels inline the same
-// code, so a cell gets the same bits whichever kernel computes it.
+// Device functions shared by the split kernels (swe_kernels.cu), the tile
+// step (swe_tile.cu) and the batched ensemble (swe_ensemble.cu): the Riemann
+// solver of Sec. 6.2, the MUSCL face values, WAF helpers and the block
+// reductions.  Every kernel inlines the same code, so a cell gets the same
+// bits whichever kernel computes it.
 #pragma once
 #include <cuda_runtime.h>
 

@@ -94,7 +94,7 @@ def test_fp64_heun(kernel):
 @pytest.mark.parametrize("kernel,block", [("split", 64), ("split", 128), ("split", 512),
                                           ("fused", 64), ("fused", 128), ("fused", 256)])
 def test_fp64_block_sizes(block, kernel):
-    """Block (and, for the fused kernel, tile) sizes; 33x17 squares = 1122 cells, ragged tail."""
+    """Block (and, for the tile step, tile) sizes; 33x17 squares = 1122 cells, ragged tail."""
     w = _pdb(33, 17)
     o = run_oracle(w, "muscl", steps=10)
     g = run_gpu(w, "muscl", dt=o["dts"], block=block, kernel=kernel)

@@ -815,8 +815,8 @@ def run_configs(args):
         (2, "partial dam break over Gaussian bathymetry, 1000x500 jittered grid", lambda: W.partial_dam_break(),
          ["muscl", "waf"], ["fp64"], 1000, 1000),
         (3, "river 4160x1563 jittered grid", lambda: W.river(), ["muscl"], ["fp32", "fp64"], 2000, 20),
-        (4, "river 2310x866 jittered grid", lambda: W.river(2310, 866), ["waf", "waf:surface", "muscl"], ["fp32"],
-         2000, 2000),
+        (4, "river 2310x866 jittered grid", lambda: W.river(2310, 866), ["waf", "waf:depth", "waf:minbee", "muscl"],
+         ["fp32"], 2000, 2000),
     ]
     for cid, name, make, schemes, precisions, steps, o_steps in cfgs:
         if args.config and cid not in args.config:
@@ -826,9 +826,10 @@ def run_configs(args):
         om = oracle.Mesh(w.nodes, w.tris, w.bnd_edges, w.bnd_tag, w.cut_edges)
         n = mesh.n
         for label in schemes:
-            # "waf:surface": WAF with its ratios on the free surface (an option next to the paper's depth)
+            # "waf:depth": WAF with its ratios on the cell depth; "waf:minbee" / "waf:vanleer": another
+            # limiter than SUPERBEE (the default WAF takes the free-surface ratio and SUPERBEE)
             scheme, opt = (label.split(":") + [""])[:2]
-            kw = {"waf_ratio": "surface"} if opt == "surface" else {}
+            kw = {"waf_ratio": "depth"} if opt == "depth" else ({"waf_limiter": opt} if opt else {})
             row = {"config": cid, "workload": name, "cells": n, "scheme": label, "steps": steps, "gpu": {}}
             for precision in precisions:
                 p = swe.swe_params_default(scheme, precision, **kw)

@@ -76,7 +76,7 @@ def opts(scheme="hllc", time_scheme="euler", waf_limiter="superbee", g=9.81, h_e
     """waf_ratio: the quantity of the WAF ratios, "surface" (eta, reading R4, the default) or
     "depth" (the cell depth h, option R17)."""
     return _Opts(SCHEMES[scheme], {"euler": 0, "heun": 1}[time_scheme],
-                 {"superbee": 0, "phi1": 1, "phi0": 2}[waf_limiter], threads,
+                 {"superbee": 0, "phi1": 1, "phi0": 2, "minbee": 3, "vanleer": 4}[waf_limiter], threads,
                  g, h_eps, r_eps, cfl, {"global": 0, "local": 1}[cfl_mode], beta, hr_order,
                  {"depth": 0, "surface": 1}[waf_ratio])
 

@@ -25,6 +25,9 @@
  *      w_L=(1+sgn(c_L)A_L)/2, w_LR=(sgn(c_R)A_R-sgn(c_L)A_L)/2,
  *      w_R=(1-sgn(c_R)A_R)/2, w_L*=(1+sgn(c*)A*)/2, w_R*=(1-sgn(c*)A*)/2,
  *      sgn(0)=+1.  The weights sum to 1; phi=1 gives the unlimited weights.
+ *      A(r,c) = 1 - (1-|c|) phi(r) with phi a classical flux limiter: SUPERBEE
+ *      (the paper's choice, its branch table) or, as options, MINBEE
+ *      phi = max(0, min(1, r)) and van Leer phi = (r + |r|)/(1 + |r|).
  *  R4  WAF on triangles: dx = |c_R - c_L|; r = 0 when the local change is
  *      below r_eps*max(1,|q_L|,|q_R|); a missing upwind cell uses the cell
  *      itself; boundary edges use the first-order HLLC boundary flux.  The
@@ -83,6 +86,15 @@
  *      eta): over a steep bed h varies with the bed even at rest, the limiter
  *      reacts to the bathymetry, and on the river workload WAF-SUPERBEE grows
  *      spurious speeds next to the inflow until it blows up (R14).
+ *  R18 WAF weights need a wet star region between S_L and S_R.  Where the
+ *      Riemann problem has none -- a dry side (h* <= h_eps), or two
+ *      rarefactions that open a dry gap (u_R - u_L >= 2(a_L + a_R), the
+ *      vacuum condition) -- the paper's weights are undefined and the edge
+ *      takes A = 1 for all three waves, i.e. its HLLC flux.  Without this the
+ *      ratio on eta at such an edge is ill-conditioned (the waves carry a large
+ *      velocity jump over a tiny change of eta), SUPERBEE switches between
+ *      A = 1 and A = 2|c| - 1 from one step to the next, and the mass flux
+ *      alternates between about G(U_L) and G(U_R) (R14).
  */
 #include "swe_oracle.h"
 
@@ -427,12 +439,16 @@ static void hll_speeds(double g, double h_eps, double hL, double uL, double hR, 
     *SR = uR + aR * pR;
 }
 
-/* SUPERBEE-type WAF limiter A(r,c) of Sec. 6.2.2 (phi selects the variants). */
+/* WAF limiter A(r,c) of Sec. 6.2.2: SUPERBEE's branch table as printed, the
+ * phi = 1 / phi = 0 variants, and A = 1 - (1-|c|) phi(r) for MINBEE and van
+ * Leer (R3). */
 static double waf_A(int lim, double r, double c)
 {
     double ac = fabs(c);
     if (lim == 1) return ac;      /* phi = 1: unlimited weights */
     if (lim == 2) return 1.0;     /* phi = 0: upwind */
+    if (lim == 3) return 1.0 - (1.0 - ac) * (r <= 0.0 ? 0.0 : (r < 1.0 ? r : 1.0));
+    if (lim == 4) return 1.0 - (1.0 - ac) * (r <= 0.0 ? 0.0 : 2.0 * r / (1.0 + r));
     if (r <= 0.0) return 1.0;
     if (r <= 0.5) return 1.0 - 2.0 * (1.0 - ac) * r;
     if (r <= 1.0) return ac;
@@ -506,6 +522,10 @@ static void edge_flux(const om_opts *o, int scheme, const double *in, const doub
             double AL = waf_A(o->waf_limiter, rL, cL);
             double AR = waf_A(o->waf_limiter, rR, cR);
             double As = waf_A(o->waf_limiter, rs, cs);
+            /* R18: no wet star region (a dry side, or the vacuum condition) */
+            if (hsL <= h_eps || hsR <= h_eps || uR - uL >= 2.0 * (sqrt(g * hsL) + sqrt(g * hsR))) {
+                AL = 1.0; AR = 1.0; As = 1.0;
+            }
             double wL = (1.0 + sgL * AL) / 2.0;
             double wLR = (sgR * AR - sgL * AL) / 2.0;
             double wR = (1.0 - sgR * AR) / 2.0;

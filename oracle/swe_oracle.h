@@ -53,7 +53,7 @@ typedef struct {
     int scheme;        /* 0 first-order HLLC, 1 MUSCL (LSQ + Barth-Jespersen) + HLLC, 2 WAF,
                           3 the paper's MUSCL (edge-upwind slopes, beta-limiter) + HLLC */
     int time_scheme;   /* 0 explicit Euler, 1 Heun (SSP-RK2, order studies only) */
-    int waf_limiter;   /* 0 SUPERBEE, 1 phi = 1 (no limiting), 2 phi = 0 */
+    int waf_limiter;   /* 0 SUPERBEE, 1 phi = 1 (no limiting), 2 phi = 0, 3 MINBEE, 4 van Leer */
     int threads;       /* OpenMP threads (0 = default); results do not depend on it */
     double g;
     double h_eps;      /* velocity desingularisation / dry threshold [m] */

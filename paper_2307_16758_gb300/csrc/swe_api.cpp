@@ -850,7 +850,7 @@ bool valid_params(const swe_params *p)
 {
     return p && p->scheme >= 0 && p->scheme <= 3 && (p->precision == SWE_FP64 || p->precision == SWE_FP32) &&
            (p->time_scheme == SWE_EULER || p->time_scheme == SWE_HEUN) && p->waf_limiter >= 0 &&
-           p->waf_limiter <= 2 && p->g > 0 && p->h_eps > 0 && p->r_eps >= 0 && p->kernel >= 0 &&
+           p->waf_limiter <= SWE_WAF_VANLEER && p->g > 0 && p->h_eps > 0 && p->r_eps >= 0 && p->kernel >= 0 &&
            p->kernel <= 2 && p->block >= 0 && p->block <= 1024 && (p->block % 32) == 0 &&
            (p->cfl_mode == SWE_CFL_GLOBAL || p->cfl_mode == SWE_CFL_LOCAL) &&
            (p->scheme != SWE_SCHEME_MUSCL_EDGE || (p->muscl_beta >= 1.0 && p->muscl_beta <= 2.0)) &&

@@ -27,6 +27,18 @@ __device__ __forceinline__ double dpow43(double x) { return x * cbrt(x); }
 __device__ __forceinline__ bool dfinite(float x) { return isfinite(x); }
 __device__ __forceinline__ bool dfinite(double x) { return isfinite(x); }
 
+// Products and sums that the compiler must not fuse, so that an edge's
+// contribution and a cell's sum of contributions have the same bits whether
+// the edge is evaluated by the cell (split kernels) or once per edge (tile step).
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+// A fused multiply-add written out (a*b + c, one rounding): the compiler's own
+// contraction choices can differ between kernels that inline the same code.
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // ---------------------------------------------------------------------------
 // Riemann problem in the rotated frame.  Inputs are the reconstructed depths
 // h*_L, h*_R (after the hydrostatic reconstruction) and the normal (u) and
@@ -56,13 +68,16 @@ __device__ __forceinline__ T waf_ratio(T r_eps, T upw, T qL, T qR)
     return ddiv(upw, loc);
 }
 
-// A(r, c) of Sec. 6.2.2 (SUPERBEE), or its phi = 1 / phi = 0 variants.
+// A(r, c) of Sec. 6.2.2: SUPERBEE's branch table, its phi = 1 / phi = 0
+// variants, and 1 - (1 - |c|) phi(r) for MINBEE and van Leer.
 template <typename T>
 __device__ __forceinline__ T waf_A(int lim, T r, T c)
 {
     T ac = fabs(c);
     if (lim == SWE_WAF_PHI1) return ac;
     if (lim == SWE_WAF_PHI0) return T(1);
+    if (lim == SWE_WAF_MINBEE) return T(1) - (T(1) - ac) * (r <= T(0) ? T(0) : dmin(r, T(1)));
+    if (lim == SWE_WAF_VANLEER) return T(1) - (T(1) - ac) * (r <= T(0) ? T(0) : ddiv(T(2) * r, T(1) + r));
     if (r <= T(0)) return T(1);
     if (r <= T(0.5)) return T(1) - T(2) * (T(1) - ac) * r;
     if (r <= T(1)) return ac;
@@ -75,11 +90,11 @@ __device__ __forceinline__ Flux<T> riemann(T hsL, T uL, T vL, T hsR, T uR, T vR,
                                            const WafIn<T> &w, int lim, T r_eps)
 {
     Flux<T> f;
-    const T half = T(0.5);
-    T GL1 = hsL * uL, GL2 = hsL * uL * uL + half * g * hsL * hsL;
-    T GR1 = hsR * uR, GR2 = hsR * uR * uR + half * g * hsR * hsR;
-    T dU1 = hsR - hsL, dU2 = hsR * uR - hsL * uL;
+    const T half = T(0.5), hg = half * g;
+    T GL1 = hsL * uL, GL2 = fma_rn(GL1, uL, hg * hsL * hsL);
+    T GR1 = hsR * uR, GR2 = fma_rn(GR1, uR, hg * hsR * hsR);
     T dG1 = GR1 - GL1, dG2 = GR2 - GL2;
+    T dU1 = hsR - hsL, dU2 = dG1;              // the momentum jump is the mass-flux jump
     bool dryL = hsL <= h_eps, dryR = hsR <= h_eps;
     if (dryL && dryR) {                    // both sides dry: zero numerical flux
         f.M = T(0); f.Tt = T(0); f.DL2 = -GL2; f.DR2 = -GR2;
@@ -115,8 +130,9 @@ __device__ __forceinline__ Flux<T> riemann(T hsL, T uL, T vL, T hsR, T uR, T vR,
         SL = uL - aL * pL;
         SR = uR + aR * pR;
     }
-    T num = SL * hsR * (uR - SR) - SR * hsL * (uL - SL);
-    T den = hsR * (uR - SR) - hsL * (uL - SL);
+    const T qR = hsR * (uR - SR), qL = hsL * (uL - SL);
+    T num = fma_rn(SL, qR, -(SR * qL));
+    T den = qR - qL;
     T Ss = den != T(0) ? ddiv(num, den) : T(0);
     // HLL (three branches) as differences to G_L and G_R
     T hL1, hL2, hR2;
@@ -126,10 +142,10 @@ __device__ __forceinline__ Flux<T> riemann(T hsL, T uL, T vL, T hsR, T uR, T vR,
     } else if (leftgoing) {
         hL1 = dG1; hL2 = dG2; hR2 = T(0);
     } else {
-        T wd = SR - SL;
-        hL1 = ddiv(SL * (SR * dU1 - dG1), wd);
-        hL2 = ddiv(SL * (SR * dU2 - dG2), wd);
-        hR2 = ddiv(SR * (SL * dU2 - dG2), wd);
+        const T iw = ddiv(T(1), SR - SL);
+        hL1 = SL * fma_rn(SR, dU1, -dG1) * iw;
+        hL2 = SL * fma_rn(SR, dU2, -dG2) * iw;
+        hR2 = SR * fma_rn(SL, dU2, -dG2) * iw;
     }
     if (!WAF) {
         f.M = leftgoing ? GR1 : GL1 + hL1;
@@ -142,6 +158,9 @@ __device__ __forceinline__ Flux<T> riemann(T hsL, T uL, T vL, T hsR, T uR, T vR,
         T rs = waf_ratio(r_eps, Ss >= T(0) ? vL - w.vupL : w.vupR - vR, vL, vR);
         T sgL = cL >= T(0) ? T(1) : T(-1), sgR = cR >= T(0) ? T(1) : T(-1), sgs = cs >= T(0) ? T(1) : T(-1);
         T AL = waf_A(lim, rL, cL), AR = waf_A(lim, rR, cR), As = waf_A(lim, rs, cs);
+        // no wet star region (a dry side, or the vacuum condition): the
+        // weights of Sec. 6.2.2 do not apply, A = 1 gives the HLLC flux
+        if (dryL || dryR || uR - uL >= T(2) * (aL + aR)) { AL = T(1); AR = T(1); As = T(1); }
         T wL = (T(1) + sgL * AL) / T(2);
         T wLR = (sgR * AR - sgL * AL) / T(2);
         T wR = (T(1) - sgR * AR) / T(2);
@@ -156,17 +175,6 @@ __device__ __forceinline__ Flux<T> riemann(T hsL, T uL, T vL, T hsR, T uR, T vR,
     return f;
 }
 
-// Products and sums that the compiler must not fuse, so that an edge's
-// contribution and a cell's sum of contributions have the same bits whether
-// the edge is evaluated by the cell (split kernels) or once per edge (fused).
-__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
-__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
-// A fused multiply-add written out (a*b + c, one rounding): the compiler's own
-// contraction choices can differ between kernels that inline the same code.
-__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 // Offsets from the centroid to the three edge midpoints, from the scaled
 // outward normals: with e_k = (-ln_k.y, ln_k.x) the edge vectors,
@@ -204,6 +212,16 @@ __device__ __forceinline__ Vec2<T> centroid_offset(const Vec2<T> *ln, T oxi, T o
 {
     const int k1 = kj == 2 ? 0 : kj + 1, k2 = kj == 0 ? 2 : kj - 1;
     return centroid_offset_from(oxi, oyi, ln[3 * j + k1], ln[3 * j + k2]);
+}
+
+// Wave speed sqrt(g h) + |u| of a wet cell (the CFL rule of Sec. 6.1): one
+// expression wherever it is evaluated (after an update, after set_state, in
+// Heun's average), so a run resumed from a saved state takes the same steps.
+template <typename T>
+__device__ __forceinline__ T wave_speed(T g, T h, T hu, T hv)
+{
+    const T u = ddiv(hu, h), v = ddiv(hv, h);
+    return dsqrt(g * h) + dsqrt(fma_rn(u, u, mul_rn(v, v)));
 }
 
 template <typename T>
@@ -411,13 +429,13 @@ template <typename T> struct CellOut { T h, hu, hv, smax, clip, bsum; };
 // Edge length and unit normal from the scaled normal (FP32: one rsqrt).
 __device__ __forceinline__ void unit_normal(float lx, float ly, float &L, float &nx, float &ny)
 {
-    const float l2 = lx * lx + ly * ly;
+    const float l2 = fma_rn(lx, lx, mul_rn(ly, ly));
     const float ri = rsqrtf(l2);
     L = l2 * ri; nx = lx * ri; ny = ly * ri;
 }
 __device__ __forceinline__ void unit_normal(double lx, double ly, double &L, double &nx, double &ny)
 {
-    L = sqrt(lx * lx + ly * ly);
+    L = sqrt(fma_rn(lx, lx, mul_rn(ly, ly)));
     nx = lx / L; ny = ly / L;
 }
 
@@ -437,8 +455,8 @@ __device__ __forceinline__ Contrib<T> contribution(T L, T sM, T P, T Tt, T nx, T
 {
     Contrib<T> c;
     c.c0 = mul_rn(L, sM);
-    c.c1 = mul_rn(L, P * nx - Tt * ny);
-    c.c2 = mul_rn(L, P * ny + Tt * nx);
+    c.c1 = mul_rn(L, fma_rn(P, nx, -mul_rn(Tt, ny)));
+    c.c2 = mul_rn(L, fma_rn(P, ny, mul_rn(Tt, nx)));
     return c;
 }
 
@@ -486,8 +504,8 @@ __device__ __forceinline__ void interior_edge(const StepArgs<T> &a, T dt, const 
     const Side<T> &B = own_i ? sj : si;
     const T zf = dmax(si.z, sj.z);
     const T hsA = dmax(A.ef - zf, T(0)), hsB = dmax(B.ef - zf, T(0));
-    const T unA = A.uf * cnx + A.vf * cny, vtA = -A.uf * cny + A.vf * cnx;
-    const T unB = B.uf * cnx + B.vf * cny, vtB = -B.uf * cny + B.vf * cnx;
+    const T unA = fma_rn(A.uf, cnx, mul_rn(A.vf, cny)), vtA = fma_rn(A.vf, cnx, -mul_rn(A.uf, cny));
+    const T unB = fma_rn(B.uf, cnx, mul_rn(B.vf, cny)), vtB = fma_rn(B.vf, cnx, -mul_rn(B.uf, cny));
     Flux<T> fl;
     if (SCHEME == SWE_SCHEME_WAF) {
         WafIn<T> wi;
@@ -505,7 +523,7 @@ __device__ __forceinline__ void interior_edge(const StepArgs<T> &a, T dt, const 
         WafIn<T> wi{};
         fl = riemann<T, false>(hsA, unA, vtA, hsB, unB, vtB, g, h_eps, wi, 0, a.r_eps);
     }
-    const T PA = hsA * unA * unA + fl.DL2, PB = hsB * unB * unB + fl.DR2;
+    const T PA = fma_rn(hsA * unA, unA, fl.DL2), PB = fma_rn(hsB * unB, unB, fl.DR2);
     const T hfi = dmax(si.ef - si.z, T(0));
     const T Pi = (own_i ? PA : PB) + own_pressure<T, SCHEME == FLUX_MUSCL_HR2>(a, hfi, si);
     const T sMi = own_i ? fl.M : -fl.M;
@@ -588,21 +606,20 @@ __device__ __forceinline__ CellOut<T> cell_finish(const StepArgs<T> &a, T dt, T 
     CellOut<T> o;
     const T area = half * (ln[0].x * ln[1].y - ln[0].y * ln[1].x);
     const T r = ddiv(dt, area);
-    T hn = hi - r * R0, hun = hui - r * R1, hvn = hvi - r * R2;
+    T hn = fma_rn(-r, R0, hi), hun = fma_rn(-r, R1, hui), hvn = fma_rn(-r, R2, hvi);
     o.clip = T(0);
     if (hn < T(0)) { o.clip = -hn * area; hn = T(0); }
     if (hn <= h_eps) {
         hun = T(0); hvn = T(0);
     } else if (nm > T(0)) {
-        const T sp = ddiv(dsqrt(hun * hun + hvn * hvn), hn);
+        const T sp = ddiv(dsqrt(fma_rn(hun, hun, mul_rn(hvn, hvn))), hn);
         const T fr = T(1) + ddiv(dt * g * nm * nm * sp, dpow43(hn));
         hun = ddiv(hun, fr); hvn = ddiv(hvn, fr);
     }
     o.h = hn; o.hu = hun; o.hv = hvn;
     o.smax = T(0);
     if (hn > h_eps) {
-        const T u = ddiv(hun, hn), v = ddiv(hvn, hn);
-        o.smax = dsqrt(g * hn) + dsqrt(u * u + v * v);
+        o.smax = wave_speed(g, hn, hun, hvn);
         if (a.cfl_local) o.smax = mul_rn(o.smax, inv_inradius(ln));
     }
     o.bsum = bs * dt;

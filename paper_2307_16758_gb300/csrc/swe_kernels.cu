@@ -101,10 +101,7 @@ __global__ void k_smax(StepArgs<T> a, int slot)
     T s = T(0);
     if (i < a.m.n) {
         T h = a.h[i];
-        if (h > a.h_eps) {
-            T u = a.hu[i] / h, v = a.hv[i] / h;
-            s = cfl_speed(a, i, dsqrt(a.g * h) + dsqrt(u * u + v * v));
-        }
+        if (h > a.h_eps) s = cfl_speed(a, i, wave_speed(a.g, h, a.hu[i], a.hv[i]));
     }
     block_publish<T>(s, T(0), T(0), a.sc, slot, true, 1.0);
 }
@@ -118,10 +115,7 @@ __global__ void k_heun_avg(StepArgs<T> a, const T *h0, const T *hu0, const T *hv
     if (i < a.m.n) {
         T h = T(0.5) * (h0[i] + a.h[i]), hu = T(0.5) * (hu0[i] + a.hu[i]), hv = T(0.5) * (hv0[i] + a.hv[i]);
         a.ho[i] = h; a.huo[i] = hu; a.hvo[i] = hv;
-        if (h > a.h_eps) {
-            T u = hu / h, v = hv / h;
-            s = cfl_speed(a, i, dsqrt(a.g * h) + dsqrt(u * u + v * v));
-        }
+        if (h > a.h_eps) s = cfl_speed(a, i, wave_speed(a.g, h, hu, hv));
     }
     block_publish<T>(s, T(0), T(0), a.sc, a.slot_next, true, 1.0);
     if (blockIdx.x == 0 && threadIdx.x == 0) {

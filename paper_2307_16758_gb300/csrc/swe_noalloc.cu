@@ -6,7 +6,7 @@
 // own the device (or that runs while such an application forbids allocation
 // in its hot loop), or a real-time loop where an allocation could block.
 // Such a caller owns its inputs and outputs; the only scratch this step needs
-// (the face values of every cell, 48 bytes per cell, plus a few scalars)
+// (the face values of the wet cells, 48 bytes per cell, plus a few scalars)
 // lives in the fixed array below, compiled into the library.
 //
 // Limits and sharing rules:
@@ -16,8 +16,7 @@
 //  - every call on a GPU uses the same array: calls that overlap on the GPU
 //    (other streams, other threads) race on it and give wrong results;
 //  - the first call on each GPU looks up the array's device address with
-//    cudaGetSymbolAddress (with that GPU current); make that first call
-//    before any stream capture.
+//    cudaGetSymbolAddress (with that GPU current).
 #include <cuda_runtime.h>
 
 #include <cmath>

@@ -6,6 +6,17 @@
 
 namespace swe_dev {
 
+// The face values of a dry cell (h <= h_eps): its centre values (eta, 0, 0, z)
+// on all three edges, for every MUSCL variant.  The prep kernels store no
+// face values for dry cells; readers take them from the cell's h and z.
+template <typename T>
+__device__ __forceinline__ Vec4<T> dry_face(T h, T z)
+{
+    Vec4<T> f;
+    f.x = h + z; f.y = T(0); f.z = T(0); f.w = z;
+    return f;
+}
+
 // MUSCL face values of cell i (least squares + Barth-Jespersen): f[k] =
 // (eta, u, v, z) at the midpoint of edge k.  NQ = 4: also the limited
 // gradient of h, for the face bed of the second-order hydrostatic
@@ -17,10 +28,10 @@ __device__ __forceinline__ void muscl_cell_faces(const StepArgs<T> &a, int64_t i
     T hi = a.h[i], zi = a.m.z[i];
     if (hi <= h_eps) {
         // a dry cell has a zero gradient and zero velocity: its three face
-        // values are its centre values (eta, 0, 0), as muscl_faces gives them;
-        // the neighbours and the geometry are not needed
+        // values are its centre values, as muscl_faces gives them; the
+        // neighbours and the geometry are not needed
 #pragma unroll
-        for (int k = 0; k < 3; k++) { f[k].x = hi + zi; f[k].y = T(0); f[k].z = T(0); f[k].w = zi; }
+        for (int k = 0; k < 3; k++) f[k] = dry_face(hi, zi);
         return;
     }
     T ui, vi;
@@ -61,6 +72,7 @@ __device__ __forceinline__ void muscl_cell_faces(const StepArgs<T> &a, int64_t i
 template <typename T, int NQ = 3>
 __device__ __forceinline__ void prep_muscl_cell(const StepArgs<T> &a, int i, Vec4<T> *F)
 {
+    if (a.h[i] <= a.h_eps) return;                      // dry: faces implied (dry_face)
     Vec4<T> f[3];
     muscl_cell_faces<T, NQ>(a, i, f);
 #pragma unroll
@@ -94,14 +106,7 @@ __device__ __forceinline__ void prep_muscl_edge_cell(const StepArgs<T> &a, int i
 {
     const T h_eps = a.h_eps;
     const T hi = a.h[i], zi = a.m.z[i];
-    if (hi <= h_eps) {
-        // dry: zero slopes and zero velocity, the face values are the centre values
-        Vec4<T> f;
-        f.x = hi + zi; f.y = T(0); f.z = T(0); f.w = zi;
-#pragma unroll
-        for (int k = 0; k < 3; k++) F[3 * i + k] = f;
-        return;
-    }
+    if (hi <= h_eps) return;                            // dry: zero slopes, faces implied (dry_face)
     T ui, vi;
     primitives(hi, a.hu[i], a.hv[i], h_eps, ui, vi);
     const T qi[3] = {hi + zi, ui, vi};
@@ -197,8 +202,14 @@ __device__ __forceinline__ void prep_waf_cell(const StepArgs<T> &a, int i, Vec4<
 template <typename T> struct GlobalSrc {
     const StepArgs<T> &a;
     int i;
-    __device__ Vec4<T> own_face(int k) const { return a.F[3 * i + k]; }
-    __device__ Vec4<T> nbr_face(const Nb &b) const { return a.F[3 * b.idx + b.kj]; }
+    T hi, zi;                                           // the cell's depth and bed
+    __device__ Vec4<T> own_face(int k) const { return hi <= a.h_eps ? dry_face(hi, zi) : a.F[3 * i + k]; }
+    // The neighbour's face value: stored if it is wet, else dry_face(h_j, z_j).
+    __device__ Vec4<T> nbr_face(const Nb &b) const
+    {
+        const T hj = a.h[b.idx];
+        return hj <= a.h_eps ? dry_face(hj, a.m.z[b.idx]) : a.F[3 * b.idx + b.kj];
+    }
     __device__ Vec4<T> nbr_centre(const Nb &b) const { return a.F[b.idx]; }
     __device__ Vec4<T> own_up(int k) const { return a.U[3 * i + k]; }
     __device__ Vec4<T> nbr_up(const Nb &b) const { return a.U[3 * b.idx + b.kj]; }
@@ -234,8 +245,9 @@ __device__ __forceinline__ void flux_block(const StepArgs<T> &a, int block_index
             if (SCHEME == SWE_SCHEME_WAF) dd[k] = a.m.dd[3 * i + k];
         }
         const T nm = a.m.nman ? a.m.nman[i] : T(0);
-        GlobalSrc<T> src{a, i};
-        o = cell_update<T, SCHEME>(a, dt, a.h[i], a.hu[i], a.hv[i], a.m.z[i], nm, nb, ln, dd, src);
+        const T hi = a.h[i], zi = a.m.z[i];
+        GlobalSrc<T> src{a, i, hi, zi};
+        o = cell_update<T, SCHEME>(a, dt, hi, a.hu[i], a.hv[i], zi, nm, nb, ln, dd, src);
         a.ho[i] = o.h; a.huo[i] = o.hu; a.hvo[i] = o.hv;
         if (!(dfinite(o.h) && dfinite(o.hu) && dfinite(o.hv))) atomicOr(&a.sc->status, ST_NONFINITE);
     }

@@ -28,7 +28,7 @@ REORDER = {"none": 0, "morton": 1, "rcm": 2}
 SCHEME = {"hllc": 0, "muscl": 1, "waf": 2, "muscl_edge": 3}
 PRECISION = {"fp64": 0, "fp32": 1}
 TIME_SCHEME = {"euler": 0, "heun": 1}
-WAF_LIMITER = {"superbee": 0, "phi1": 1, "phi0": 2}
+WAF_LIMITER = {"superbee": 0, "phi1": 1, "phi0": 2, "minbee": 3, "vanleer": 4}
 KERNEL = {"auto": 0, "split": 1, "fused": 2}
 CFL_MODE = {"global": 0, "local": 1}
 WAF_RATIO = {"depth": 0, "surface": 1}

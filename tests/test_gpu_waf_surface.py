@@ -33,6 +33,21 @@ def test_fp64_one_step_and_100_steps(workload):
     assert max(state_errors(g, od)) > 1e-7           # over a bed the surface ratio is a different scheme
 
 
+@pytest.mark.parametrize("limiter", ["minbee", "vanleer", "phi1"])
+def test_other_limiters_match_the_oracle(limiter):
+    """WAF with A(r, c) = 1 - (1 - |c|) phi(r) for MINBEE, van Leer and phi = 1 (Sec. 6.2.2),
+    with the edges that have no wet star region on their HLLC flux (R18): a river with dry banks
+    and an inflow, FP64 against the oracle after 1 and 100 replayed steps."""
+    w = W.river(100, 38, seed=21, q_in=1500.0)
+    g1, o1 = run_gpu(w, "waf", steps=1, waf_limiter=limiter), run_oracle(w, "waf", steps=1, waf_limiter=limiter)
+    assert max(state_errors(g1, o1)) <= 1e-12
+    o = run_oracle(w, "waf", steps=100, waf_limiter=limiter)
+    g = run_gpu(w, "waf", dt=o["dts"], waf_limiter=limiter)
+    assert max(state_errors(g, o)) <= 1e-9
+    osb = run_oracle(w, "waf", dt=o["dts"])
+    assert max(state_errors(g, osb)) > 1e-7              # a different limiter, a different scheme
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_flat_bed_gives_the_depth_ratio_bits(precision):
     w = W.dam_break_1d(120, 8, 10.0, 1.0, 1.0, 0.5, x_dam=5.0)

@@ -222,17 +222,21 @@ def test_rotation_by_90_degrees(scheme):
 
 
 def test_cell_renumbering_does_not_change_the_solution():
-    """The same mesh under another cell numbering gives the same solution (cf. Sec. 6.3.1)."""
+    """The same mesh under another cell numbering gives the same solution (cf. Sec. 6.3.1).  The
+    numbering decides the orientation in which each edge's Riemann problem is solved, which moves
+    the last bits; WAF-SUPERBEE switches branches on such bits where a local change crosses zero
+    (R14), so its bar after 100 steps is 1e-10 instead of 1e-12."""
     w = W.partial_dam_break(nx=24, ny=12, spacing=1.0, n_gauss=8, seed=5)
     m = _mesh(w)
     p = np.random.default_rng(1).permutation(w.n_cells)
     mp = oracle.Mesh(w.nodes, w.tris[p], w.bnd_edges, w.bnd_tag, w.cut_edges)
     for s in ("muscl", "waf", "muscl_edge"):
         o = oracle.opts(s)
+        tol = 1e-10 if s == "waf" else 1e-12
         a = oracle.run(m, o, w.z, w.nman, w.h, w.hu, w.hv, 100)
         b = oracle.run(mp, o, w.z[p], w.nman[p], w.h[p], w.hu[p], w.hv[p], 100)
-        assert np.abs(a[0][p] - b[0]).max() < 1e-12
-        assert np.abs(a[1][p] - b[1]).max() < 1e-12
+        assert np.abs(a[0][p] - b[0]).max() < tol, s
+        assert np.abs(a[1][p] - b[1]).max() < tol, s
 
 
 def test_openmp_thread_count_does_not_change_results():
@@ -684,8 +688,9 @@ def test_waf_surface_ratio_conserves_mass_rotates_and_differs_over_a_bed():
 
 def test_waf_surface_ratio_stays_bounded_where_the_depth_ratio_does_not():
     """River of 30,000 cells, 2000 WAF-SUPERBEE steps: with the paper's depth ratio the limiter
-    reacts to the steep channel banks and the speed next to the inflow passes 20 m/s (about 50 by
-    step 1600); with the free-surface ratio it stays below 10 m/s (about 4) over the whole run."""
+    reacts to the steep channel banks and the speed next to the inflow passes 12 m/s (about 18;
+    about 50 without reading R18); with the free-surface ratio it stays below 6 m/s (about 4.1)
+    over the whole run."""
     w = W.river(200, 75)
     m = _mesh(w)
     worst = {}
@@ -699,7 +704,7 @@ def test_waf_surface_ratio_stays_bounded_where_the_depth_ratio_does_not():
             worst[ratio] = max(worst[ratio], float(u.max()))
             if worst[ratio] > 20.0:
                 break
-    assert worst["depth"] > 20.0 and worst["surface"] < 10.0, worst
+    assert worst["depth"] > 12.0 and worst["surface"] < 6.0, worst
 
 
 # --------------------------------------------------------------------------
@@ -838,6 +843,62 @@ def test_waf_superbee_flux_equals_toro_sum_form():
     for key in hit:
         assert hit[key] == {0, 1, 2, 3, 4}, (key, hit[key])
     assert {("sub", True), ("sub", False), ("right", True), ("left", False)} <= pattern, pattern
+
+
+def _phi_minbee(r):
+    """MINBEE (minmod) as a flux limiter: max(0, min(1, r))."""
+    return max(0.0, min(1.0, r))
+
+
+def _phi_vanleer(r):
+    """Van Leer's limiter: (r + |r|) / (1 + |r|)."""
+    return (r + abs(r)) / (1.0 + abs(r))
+
+
+@pytest.mark.parametrize("name,phi", [("minbee", _phi_minbee), ("vanleer", _phi_vanleer)])
+def test_waf_other_limiters_equal_toro_sum_form(name, phi):
+    """Sec. 6.2.2 builds A(r, c) = 1 - (1 - |c|) phi(r) from a classical flux limiter; the oracle's
+    MINBEE and van Leer options equal Toro's sum form with those limiters written independently
+    (the same states as the SUPERBEE pin), and differ from SUPERBEE on them."""
+    o = oracle.opts("waf", waf_limiter=name)
+    osb = oracle.opts("waf", waf_limiter="superbee")
+    far = 0.0
+    for st, waf in _waf_cases(13, 300):
+        M, PL, PR, T = oracle.edge_flux(o, st, waf)
+        F1, F2, F3, _ = _waf_sum_form(st, waf, phi=phi)
+        scale = max(1.0, abs(F1), abs(F2))
+        assert abs(M - F1) <= 1e-12 * scale, (st, waf, M, F1)
+        assert abs(PL + 0.5 * G * st[1] ** 2 - F2) <= 1e-12 * scale
+        assert abs(T - F3) <= 1e-12 * max(1.0, abs(F3))
+        far = max(far, abs(M - oracle.edge_flux(osb, st, waf)[0]))
+    assert far > 1e-3
+
+
+@pytest.mark.parametrize("limiter", ["superbee", "phi1", "minbee", "vanleer"])
+def test_waf_without_a_wet_star_region_is_hllc(limiter):
+    """Reading R18: where the Riemann problem has no wet star region -- two rarefactions that open
+    a dry gap (u_R - u_L >= 2(a_L + a_R)) or a dry side -- every limiter gives the HLLC flux; a
+    problem just short of the vacuum condition keeps the limited weights."""
+    o = oracle.opts("waf", waf_limiter=limiter)
+    oh = oracle.opts("hllc")
+    rng = np.random.default_rng(5)
+    for _ in range(200):
+        hL, hR = rng.uniform(0.2, 3.0), rng.uniform(0.2, 3.0)
+        gap = 2.0 * (math.sqrt(G * hL) + math.sqrt(G * hR))
+        du = gap * rng.uniform(1.0, 1.6)
+        uL = rng.uniform(-3, 3)
+        vL, vR = rng.uniform(-1, 1), rng.uniform(-1, 1)
+        waf = np.array([rng.uniform(0.001, 0.05), hL + rng.uniform(-0.5, 0.5), hR + rng.uniform(-0.5, 0.5),
+                        vL + rng.uniform(-0.5, 0.5), vR + rng.uniform(-0.5, 0.5), hL, hR, 0.0])
+        vac = _state(hL, uL, vL, hR, uL + du, vR)
+        assert np.array_equal(oracle.edge_flux(o, vac, waf), oracle.edge_flux(oh, vac))
+        dry = _state(hL, uL, vL, 0.0, 0.0, 0.0)
+        assert np.array_equal(oracle.edge_flux(o, dry, waf), oracle.edge_flux(oh, dry))
+    # short of the vacuum condition, a state whose ratios are not zero keeps the WAF weights
+    hL = hR = 1.0
+    wet = _state(hL, -2.0, 0.3, 1.2, 2.0, -0.4)
+    waf = np.array([0.02, 0.9, 1.35, 0.5, -0.9, hL, 1.2, 0.0])
+    assert not np.allclose(oracle.edge_flux(o, wet, waf), oracle.edge_flux(oh, wet), rtol=0, atol=1e-9)
 
 
 def test_waf_pin_has_power_against_plausible_mistakes():

@@ -262,10 +262,11 @@ int swe_fma_peak(int precision, int iters, void *stream, double *flops_per_s);
  * into the library (about 12.6 MB per GPU, held until the process exits), so
  * n_cells must not exceed SWE_NOALLOC_MAX_CELLS (else SWE_ERR_ARG).  The
  * first call on a GPU looks the array up (cudaGetSymbolAddress) with that GPU
- * current.  All calls on a GPU share the
- * array, so calls that overlap on the GPU race.  Each call enqueues three
- * kernels on `stream` (dt travels as a kernel argument, nothing is copied
- * from the host) and returns without waiting; no status is read back. */
+ * current; make that first call before any stream capture.  All calls on a
+ * GPU share the array, so calls that overlap on the GPU race.  Each call
+ * enqueues three kernels on `stream` (dt travels as a kernel argument,
+ * nothing is copied from the host) and returns without waiting; no status is
+ * read back. */
 #define SWE_NOALLOC_MAX_CELLS 262144
 int swe_muscl_step_noalloc(int64_t n_cells, const int32_t *nbr, const float *ln, const float *z,
                            const float *manning_n, const float *h, const float *hu,

@@ -16,7 +16,8 @@
 //  - every call on a GPU uses the same array: calls that overlap on the GPU
 //    (other streams, other threads) race on it and give wrong results;
 //  - the first call on each GPU looks up the array's device address with
-//    cudaGetSymbolAddress (with that GPU current).
+//    cudaGetSymbolAddress (with that GPU current); make that first call
+//    before any stream capture.
 #include <cuda_runtime.h>
 
 #include <cmath>

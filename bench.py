@@ -111,16 +111,17 @@ def roofline_entry(scheme, n, step_ms, prof, kname, peak, peak_src, traffic):
             "per_kernel_ms": {k: v[0] / v[1] for k, v in prof.items()}, "own_bytes": own}
 
 
-# The files the split kernels (k_prep_*, k_flux*) are compiled from: the ncu
-# counters of those kernels stay valid while these hash the same.
-SPLIT_KERNEL_SOURCES = ("paper_2307_16758_gb300/csrc/swe_kernels.cu", "paper_2307_16758_gb300/csrc/swe_split.cuh",
-                        "paper_2307_16758_gb300/csrc/swe_device.cuh", "paper_2307_16758_gb300/csrc/swe_dev.h",
-                        "include/swe.h")
+# The files the split kernels (k_prep_*, k_flux*) and the tile step (k_tile)
+# are compiled from: stored ncu counters stay valid while these hash the same.
+KERNEL_SOURCES = ("paper_2307_16758_gb300/csrc/swe_kernels.cu", "paper_2307_16758_gb300/csrc/swe_split.cuh",
+                  "paper_2307_16758_gb300/csrc/swe_device.cuh", "paper_2307_16758_gb300/csrc/swe_dev.h",
+                  "paper_2307_16758_gb300/csrc/swe_tile.cu", "paper_2307_16758_gb300/csrc/swe_tile.cuh",
+                  "paper_2307_16758_gb300/csrc/swe_async.cuh", "include/swe.h")
 
 
 def kernel_source_sha() -> str:
     h = hashlib.sha256()
-    for p in SPLIT_KERNEL_SOURCES:
+    for p in KERNEL_SOURCES:
         h.update(open(os.path.join(ROOT, p), "rb").read())
     return h.hexdigest()[:16]
 
@@ -440,7 +441,7 @@ def run_gpu(args):
         out.update(fp64_comparison(args, mesh, w, swe, torch, p32))
         out["fp64"]["fp32_speedup"] = out["fp64"]["ms_per_step"] / step_ms
         out["alu_peaks"] = alu_peaks(swe, torch, local, clocks)
-        out["fp64"]["roofline"] = fp64_alu_roofline(out["fp64"], out["alu_peaks"], kname, skey, n)
+        out["fp64"]["roofline"] = fp64_alu_roofline(out["fp64"], out["alu_peaks"], skey, n)
         if ws == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(w, n)
         if ws == 1 and not args.no_extras:
@@ -471,15 +472,20 @@ def alu_peaks(swe, torch, dev, clocks):
             "source": "swe_fma_peak (8 independent FMA chains per thread, 8 x 256 threads per SM)"}
 
 
-def fp64_alu_roofline(fp64, peaks, kname, skey, n):
-    """The FP64 flux kernel against the measured FP64 FMA rate: ncu's FP64 operations per cell
-    (add, mul, 2 x fma) over the kernel's CUDA-event time."""
-    c = ncu_counters(f"{kname}:flux:{skey}:fp64")
-    ms = fp64.get("per_kernel_ms", {}).get("flux")
+def fp64_alu_roofline(fp64, peaks, skey, n):
+    """The FP64 path's dominant kernel against the measured FP64 FMA rate: ncu's FP64 operations per
+    cell (add, mul, 2 x fma) over the kernel's CUDA-event time."""
+    prof = fp64.get("per_kernel_ms", {})
+    if not prof:
+        return None
+    dom = max(prof, key=prof.get)
+    ms = prof[dom]
+    c = ncu_counters(f"{fp64.get('kernel', 'split')}:{dom}:{skey}:fp64")
     if not c or "fp64_flops_per_cell" not in c or not ms:
         return None
     achieved = c["fp64_flops_per_cell"] * n / (ms / 1e3) / 1e12
-    return {"bound": "alu", "kernel": "flux", "achieved": achieved, "peak": peaks["fp64"], "unit": "TFLOP/s",
+    return {"bound": "alu", "kernel": KERNEL_NAMES.get((fp64.get("kernel", "split"), dom), dom),
+            "achieved": achieved, "peak": peaks["fp64"], "unit": "TFLOP/s",
             "frac": achieved / peaks["fp64"], "fp64_flops_per_cell": c["fp64_flops_per_cell"],
             "peak_source": "measured FP64 FMA rate (swe_fma_peak)", "kernel_ms": ms}
 
@@ -497,6 +503,7 @@ def fp64_comparison(args, mesh, w, swe, torch, p32_timed):
     s64.sync()
     s64.close()
     s64 = swe.State.from_workload(mesh, p64, w)
+    kernel64 = {1: "split", 2: "fused"}.get(s64.info()[1], "split")
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -525,7 +532,7 @@ def fp64_comparison(args, mesh, w, swe, torch, p32_timed):
     s64.close()
     v64 = n * m_steps / (ms64 / 1e3)
     return {"fp64": {"value": v64, "unit": UNIT, "ms_per_step": ms64 / m_steps, "steps": m_steps,
-                     "per_kernel_ms": {k: v[0] / v[1] for k, v in prof64.items()}},
+                     "kernel": kernel64, "per_kernel_ms": {k: v[0] / v[1] for k, v in prof64.items()}},
             "error_fp32_vs_fp64": err}
 
 

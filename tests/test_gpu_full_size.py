@@ -149,7 +149,9 @@ def test_river_4m_waf_fp32_against_fp64(river4m):
     round-off guard r_eps of the ratios decides some switches (reading R14): in FP64 alone,
     r_eps = 1e-6 instead of 1e-12 moves the result after 1000 steps by about as much as FP32 does.
     So: FP32's distance from FP64 is at most twice that FP64 sensitivity (and 3e-4); with the
-    limiter off (phi = 1) FP32 follows FP64 to 1e-6; the mass budget closes in both."""
+    limiter off (phi = 1) FP32 follows FP64 to 3e-5 (its only switches are reading R18's tests
+    for a dry side or a vacuum-forming edge, decided in each precision's arithmetic: 7e-6
+    measured, 5e-8 before R18); the mass budget closes in both."""
     w, mesh = river4m
     h64, dts, drift64 = _river_run(mesh, w, "waf", "fp64")
     h64g, _, _ = _river_run(mesh, w, "waf", "fp64", dts=dts, r_eps=1e-6)
@@ -161,7 +163,7 @@ def test_river_4m_waf_fp32_against_fp64(river4m):
     p64, dts1, _ = _river_run(mesh, w, "waf", "fp64", waf_limiter="phi1")
     p32, _, _ = _river_run(mesh, w, "waf", "fp32", dts=dts1, waf_limiter="phi1")
     print(f"4M river waf phi=1: FP32 vs FP64 L1(h) {_l1(p32, p64):.3e}")
-    assert _l1(p32, p64) <= 1e-6
+    assert _l1(p32, p64) <= 3e-5
 
 
 # ---- the 1M partial dam break (1000 x 500 squares): FP64 against the oracle at full size ----

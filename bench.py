@@ -50,13 +50,16 @@ SEED = 20230733
 #   split MUSCL flux : state 3 + z + nbr + normals 6 + own face values 12 + Manning n, writes state 3
 #   fused MUSCL      : state 3 + z + nbr + normals 6 + n, writes state 3 (the whole step)
 #   HLLC flux        : state 3 + z + nbr + normals 6 + n, writes state 3
-def algo_bytes(kind: str, scheme: str, precision: str) -> int:
+def algo_bytes(kind: str, scheme: str, precision: str, wet: float = 1.0) -> float:
+    """Bytes a kernel itself reads and writes per cell; for the split MUSCL kernels a dry cell
+    (h <= h_eps) stores and reads no face values, so their figure is the mix at wet fraction `wet`
+    (prep: wet 100, dry 8 B in FP32; flux: wet 116, dry 68 B)."""
     f = 4 if precision == "fp32" else 8
     nbr = 12
     if scheme in ("muscl", "muscl_edge") and kind == "prep":
-        return 3 * f + f + nbr + 6 * f + 12 * f
+        return wet * (3 * f + f + nbr + 6 * f + 12 * f) + (1.0 - wet) * 2 * f
     if scheme in ("muscl", "muscl_edge") and kind == "flux":
-        return 3 * f + f + nbr + 6 * f + 12 * f + f + 3 * f
+        return wet * (3 * f + f + nbr + 6 * f + 12 * f + f + 3 * f) + (1.0 - wet) * (3 * f + f + nbr + 6 * f + f + 3 * f)
     if kind == "fused":
         return 3 * f + f + nbr + 6 * f + f + 3 * f
     if scheme == "hllc" and kind == "flux":
@@ -87,11 +90,12 @@ def survey_bytes(scheme: str, precision: str) -> int:
 KERNEL_NAMES = {("fused", "fused"): "k_tile", ("split", "flux"): "k_flux", ("split", "prep"): "k_prep"}
 
 
-def roofline_entry(scheme, n, step_ms, prof, kname, peak, peak_src, traffic):
+def roofline_entry(scheme, n, step_ms, prof, kname, peak, peak_src, traffic, wet=1.0):
     """The contract's roofline object: the whole step and its dominant kernel against the measured HBM
     copy rate, each with the algorithmic bytes of survey_bytes() per cell-update (frac is the step's;
     with the one-pass tile step the step is one launch of the dominant kernel); each kernel's own
-    bytes (what it reads and writes, face-value scratch included) under own_bytes."""
+    bytes (what it reads and writes, face-value scratch included, at the state's wet fraction) under
+    own_bytes; traffic is the dominant kernel's DRAM bytes per launch from the stored ncu counters."""
     per_cell = survey_bytes(scheme, "fp32")
     dom = max(prof, key=lambda k: prof[k][0])
     dom_ms = prof[dom][0] / prof[dom][1]
@@ -99,12 +103,19 @@ def roofline_entry(scheme, n, step_ms, prof, kname, peak, peak_src, traffic):
     dom_ach = per_cell * n / (dom_ms / 1e3) / 1e9
     own = {}
     for k, (tot, cnt) in prof.items():
-        b = algo_bytes(k, scheme, "fp32")
+        b = algo_bytes(k, scheme, "fp32", wet)
         if b:
             a = b * n / (tot / cnt / 1e3) / 1e9
             own[k] = {"bytes_per_cell": b, "ms": tot / cnt, "achieved": a, "frac": a / peak}
+    if own:
+        own["wet_fraction"] = wet
+    extra = {}
+    if traffic is not None:
+        extra["traffic_source"] = ("dram__bytes_read.sum + dram__bytes_write.sum of the dominant kernel, ncu on the "
+                                   "3,252,084-cell river of the same generator (profiles/ncu_traffic.json), "
+                                   "scaled to this launch by the cell count")
     return {"bound": "hbm", "achieved": step_ach, "peak": peak, "unit": "GB/s", "frac": step_ach / peak,
-            "traffic": traffic, "peak_source": peak_src, "algo_bytes_per_cell": per_cell,
+            "traffic": traffic, **extra, "peak_source": peak_src, "algo_bytes_per_cell": per_cell,
             "scope": "whole step (all launches of one time step)", "step_ms": step_ms,
             "kernel": {"name": KERNEL_NAMES.get((kname, dom), dom), "ms": dom_ms, "achieved": dom_ach,
                        "frac": dom_ach / peak},
@@ -405,6 +416,18 @@ def run_gpu(args):
     e2e, _ = job_throughput(n, args.steps, (t1 - t0) * 1e3, dist, "cuda")
     h2d = 3 * 8 * n / args.steps
     d2h = (3 * 8 * n + 8 * 3) / args.steps
+    # the same with one call per step and the step's result (its mass budget, 24 bytes) read back
+    # after every step, as a caller that monitors the run would
+    k1 = min(args.steps, 500)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st.set_state(*hin)
+    for _ in range(k1):
+        st.step(1, args.cfl)
+        st.mass()
+    st.get_state(hout)
+    t1 = time.perf_counter()
+    e2e1, _ = job_throughput(n, k1, (t1 - t0) * 1e3, dist, "cuda")
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -421,8 +444,16 @@ def run_gpu(args):
             "parallelism": "replicas" if ws > 1 else "single GPU", "seed": SEED,
             "schedule": f"boundary-first, {args.parts} parts" if args.parts > 1 else "plain",
         },
-        "roofline": roofline_entry(args.scheme, n, step_ms, prof, kname, peak, peak_src, traffic),
-        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "roofline": roofline_entry(args.scheme, n, step_ms, prof, kname, peak, peak_src, traffic,
+                                   float(np.mean(w.h > p32.h_eps))),
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "scope": "swe_set_state from pinned host arrays, swe_step(K), swe_get_state and swe_mass into "
+                         "host memory, all inside the timed region; the state crosses once per run, so the "
+                         "bytes per step are the run's copies over its K steps",
+                "per_step_calls": {"value": e2e1, "unit": UNIT, "steps": k1,
+                                   "h2d_bytes_per_step": 3 * 8 * n / k1, "d2h_bytes_per_step": 24 + 3 * 8 * n / k1,
+                                   "scope": "the same with swe_step(1) and a swe_mass read-back (24 bytes) "
+                                            "after every step"}},
         "gpu_launches": int(launches),
         "clocks": clocks,
     }

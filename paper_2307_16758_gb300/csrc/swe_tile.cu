@@ -81,6 +81,25 @@ template <typename K> int persistent_grid(K kern, int block, size_t smem)
     return per_sm * sms;
 }
 
+// Let kernel `kern` launch with up to the device's opt-in maximum of dynamic
+// shared memory (`smem` bytes are needed).  The limit is a property of the
+// kernel on the current device, shared by every state: it is set to the
+// device maximum, never to one state's own need, so that configuring a state
+// with a smaller tile plan cannot lower what another state launches with.
+// Called when a state or an ensemble is configured, outside any capture.
+template <typename K> cudaError_t allow_dynamic_smem(K kern, size_t smem)
+{
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    if (smem > (size_t)optin) return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    return e;
+}
+
 }  // namespace
 
 template <typename T> size_t tile_smem_bytes(const TileArgs &t)
@@ -95,15 +114,9 @@ template <typename T> int tile_max_threads(int scheme)
     return fa.maxThreadsPerBlock;
 }
 
-// Allow the tile kernel `smem` bytes of dynamic shared memory (called when a
-// state is configured, outside any stream capture).
 template <typename T> cudaError_t tile_prepare(int scheme, size_t smem)
 {
-    auto kern = tile_kernel<T>(scheme);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-    return e;
+    return allow_dynamic_smem(tile_kernel<T>(scheme), smem);
 }
 
 template <typename T> cudaError_t launch_tile(int scheme, const StepArgs<T> &a, const TileArgs &t, cudaStream_t s)
@@ -136,11 +149,7 @@ cudaError_t launch_tile_ensemble(int scheme, const EnsEntry<T> *tab, const int2 
 
 template <typename T> cudaError_t tile_ensemble_prepare(int scheme, size_t smem)
 {
-    auto kern = tile_ens_kernel<T>(scheme);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-    return e;
+    return allow_dynamic_smem(tile_ens_kernel<T>(scheme), smem);
 }
 
 template <typename T> int tile_ensemble_max_threads(int scheme)

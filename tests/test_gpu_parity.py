@@ -221,6 +221,28 @@ def test_all_dry_domain_is_reported():
     assert e.value.code == -4
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_tile_states_with_different_plans_coexist(precision):
+    """Two states on the tile step whose plans need different shared memory (tiles of 512 and of
+    128 cells): configuring the smaller one after the larger must not stop the larger one from
+    launching, and both keep the split kernels' bits."""
+    w = _pdb(60, 30)
+    m = swe.Mesh.from_workload(w)
+    big_tile = 512 if precision == "fp32" else 256
+    big = swe.State.from_workload(m, swe.swe_params_default("muscl", precision, kernel="fused", block=big_tile), w)
+    small = swe.State.from_workload(m, swe.swe_params_default("muscl", precision, kernel="fused", block=128), w)
+    ref = swe.State.from_workload(m, swe.swe_params_default("muscl", precision, kernel="split"), w)
+    for st in (big, small, ref):
+        st.step(12, 0.9)
+    r = ref.get_state()
+    for st in (big, small):
+        for x, y in zip(st.get_state(), r):
+            assert np.array_equal(x, y)
+    for st in (big, small, ref):
+        st.close()
+    m.close()
+
+
 def test_set_state_round_trip_and_resume():
     w = _pdb(40, 20)
     p = swe.swe_params_default("muscl", "fp64")

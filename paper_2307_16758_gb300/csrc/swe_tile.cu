@@ -81,20 +81,24 @@ template <typename K> int persistent_grid(K kern, int block, size_t smem)
     return per_sm * sms;
 }
 
-// Let kernel `kern` launch with up to the device's opt-in maximum of dynamic
-// shared memory (`smem` bytes are needed).  The limit is a property of the
-// kernel on the current device, shared by every state: it is set to the
-// device maximum, never to one state's own need, so that configuring a state
-// with a smaller tile plan cannot lower what another state launches with.
-// Called when a state or an ensemble is configured, outside any capture.
+// Let kernel `kern` launch with as much dynamic shared memory as the device
+// allows a block beside the kernel's static shared memory (`smem` bytes are
+// needed).  The limit is a property of the kernel on the current device,
+// shared by every state: it is set to that maximum, never to one state's own
+// need, so that configuring a state with a smaller tile plan cannot lower
+// what another state launches with.  Called when a state or an ensemble is
+// configured, outside any capture.
 template <typename K> cudaError_t allow_dynamic_smem(K kern, size_t smem)
 {
     int dev = 0, optin = 0;
+    cudaFuncAttributes fa{};
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);
     if (e != cudaSuccess) return e;
-    if (smem > (size_t)optin) return cudaErrorInvalidValue;
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    const size_t room = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+    if (smem > room) return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)room);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     return e;

@@ -59,14 +59,15 @@ __global__ void k_prep_waf(StepArgs<T> a, Vec4<T> *P, Vec4<T> *U)
     if (i < a.m.n) prep_waf_cell(a, i, P, U);
 }
 
-// Register cap of the FP32 flux kernels: 48 registers fit five 256-thread
-// blocks per SM.  MUSCL fits without spills; HLLC (69 registers uncapped,
-// three blocks) spills 4 bytes and runs 0.362 against 0.395 ms on the 13M
-// river, WAF (72) spills 64 bytes and runs 0.515 against 0.606 ms.  The FP64
-// instances are bound by the FP64 units and left to the compiler.
+// Register cap of the FP32 flux kernels.  They wait on memory more than they
+// compute, so resident warps pay: 40 registers fit six 256-thread blocks per
+// SM, 48 five.  LSQ MUSCL and HLLC at 40 (spilling about 30 bytes) run the
+// 13M river's flux in 0.300 and 0.255 ms against 0.326 and 0.290 at 48 (no
+// spills); WAF keeps 48 (72 registers uncapped: 0.606 ms, at 48 0.515).  The
+// FP64 instances are bound by the FP64 units and left to the compiler.
 template <typename T, int SCHEME> constexpr int flux_maxnreg()
 {
-    return sizeof(T) == 4 ? 48 : 255;
+    return sizeof(T) != 4 ? 255 : (SCHEME == SWE_SCHEME_WAF ? 48 : 40);
 }
 
 template <typename T, int SCHEME>

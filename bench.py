@@ -359,6 +359,8 @@ def run_gpu(args):
     mesh = swe.Mesh.from_workload(w, "morton")
     n = mesh.n
     p32 = swe.swe_params_default(args.scheme, "fp32", kernel=args.kernel, hr_order=args.hr_order)
+    if args.block:
+        p32.block = args.block
     st = swe.State.from_workload(mesh, p32, w)
     part = None
     if args.parts > 1:                       # boundary-first schedule over Morton sub-domains
@@ -934,6 +936,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cfl", type=float, default=0.9)
     ap.add_argument("--kernel", default="auto", choices=["auto", "split", "fused"])
+    ap.add_argument("--block", type=int, default=0,
+                    help="threads per block of the flux kernel (cells per tile for the tile step); 0: the default")
     ap.add_argument("--scheme", default="muscl", choices=list(SCHEME_NAMES),
                     help="MUSCL-HLLC with least-squares gradients (default), the paper's edge-upwind MUSCL, "
                          "first-order HLLC or WAF-HLLC")

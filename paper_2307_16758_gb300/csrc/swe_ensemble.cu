@@ -34,7 +34,7 @@ __global__ void __maxnreg__((sizeof(T) != 4 ? 255 : SCHEME == SWE_SCHEME_MUSCL ?
 }
 
 template <typename T, int SCHEME>
-__global__ void __maxnreg__((sizeof(T) != 4 ? 255 : SCHEME == SWE_SCHEME_WAF ? 48 : 40))
+__global__ void __maxnreg__((sizeof(T) != 4 ? 255 : SCHEME == SWE_SCHEME_WAF ? 48 : 32))
     k_flux_ens(const EnsEntry<T> *__restrict__ tab, const int2 *__restrict__ blk, int phase)
 {
     const int2 b = blk[blockIdx.x];

@@ -60,14 +60,16 @@ __global__ void k_prep_waf(StepArgs<T> a, Vec4<T> *P, Vec4<T> *U)
 }
 
 // Register cap of the FP32 flux kernels.  They wait on memory more than they
-// compute, so resident warps pay: 40 registers fit six 256-thread blocks per
-// SM, 48 five.  LSQ MUSCL and HLLC at 40 (spilling about 30 bytes) run the
-// 13M river's flux in 0.300 and 0.255 ms against 0.326 and 0.290 at 48 (no
-// spills); WAF keeps 48 (72 registers uncapped: 0.606 ms, at 48 0.515).  The
+// compute, so resident warps pay more than spills cost: 32 registers fit
+// eight 256-thread blocks per SM (every warp slot), 40 six, 48 five.  On the
+// 13M river the LSQ MUSCL flux kernel runs 0.281 ms at 32 (about 90 bytes of
+// spills), 0.303 at 40, 0.326 at 48 (none); HLLC 0.238, 0.257, 0.290; with
+// the second-order hydrostatic reconstruction 0.283 at 32, 0.297 at 40.  WAF
+// keeps 48 (0.512 ms; 0.530 at 40; uncapped, 72 registers, 0.606).  The
 // FP64 instances are bound by the FP64 units and left to the compiler.
 template <typename T, int SCHEME> constexpr int flux_maxnreg()
 {
-    return sizeof(T) != 4 ? 255 : (SCHEME == SWE_SCHEME_WAF ? 48 : 40);
+    return sizeof(T) != 4 ? 255 : (SCHEME == SWE_SCHEME_WAF ? 48 : 32);
 }
 
 template <typename T, int SCHEME>

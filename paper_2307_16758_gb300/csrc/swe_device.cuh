@@ -100,11 +100,15 @@ __device__ __forceinline__ Flux<T> riemann(T hsL, T uL, T vL, T hsR, T uR, T vR,
         f.M = T(0); f.Tt = T(0); f.DL2 = -GL2; f.DR2 = -GR2;
         return f;
     }
-    if (!WAF && hsL == hsR && uL == uR && vL == vR) {
+    if ((!WAF || lim != SWE_WAF_PHI1) && hsL == hsR && uL == uR && vL == vR) {
         // equal states (a lake at rest, or any uniform flow): whichever wave
         // pattern the speeds give, dU = dG = 0, so the HLL flux is G(U) and
         // the HLLC tangential flux is M v; the solver below would return the
-        // same values (up to the sign of a zero), so its speeds are skipped
+        // same values (up to the sign of a zero), so its speeds are skipped.
+        // WAF too: its weighted sums of G_L, F_HLL and G_R are all G(U), and
+        // the shear wave's local change of v is zero, so its ratio is 0 and
+        // A = 1 (every limiter but phi = 1, which keeps A = |c|): the
+        // tangential weights are exactly 1 and 0, and the flux is M v.
         f.M = GL1 + T(0); f.Tt = f.M * vL; f.DL2 = T(0); f.DR2 = T(0);
         return f;
     }

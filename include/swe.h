@@ -236,6 +236,18 @@ int swe_dt_history(swe_state *s, double *dt, int n);
  * Errors: SWE_ERR_ARG, SWE_ERR_NOMEM, SWE_ERR_CUDA. */
 int swe_fma_peak(int precision, int iters, void *stream, double *flops_per_s);
 
+/* Not in the paper.  A self-check of the bounded waits that every in-kernel
+ * wait of this library uses (the tile step's waits for its bulk copies into
+ * shared memory): one block of 128 threads waits on an mbarrier whose phase
+ * completes only if `arrive` is nonzero (one thread arrives).  With arrive = 0
+ * nothing completes it: the wait gives up after `polls` polls (1 .. 2^22), the
+ * kernel records that and returns, and the context stays usable -- the way a
+ * tile step that loses a copy reports SWE_ERR_TIMEOUT instead of hanging.
+ * *timed_out = 1 if the wait gave up, 0 if the phase completed.  Uses a small
+ * device buffer from the allocator; blocks until the launch ends.
+ * Errors: SWE_ERR_ARG, SWE_ERR_NOMEM, SWE_ERR_CUDA. */
+int swe_probe_bounded_wait(uint32_t polls, int arrive, int *timed_out, void *stream);
+
 /* ---- One step without device allocation ---------------------------------- */
 
 /* The paper has no counterpart to this entry point; it exists for callers

@@ -38,6 +38,12 @@ __device__ __forceinline__ void mbar_arrive_expect(uint64_t *bar, uint32_t bytes
                  : "memory");
 }
 
+// The calling thread arrives once, announcing no copies.
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // Copy `bytes` (a multiple of 16; both addresses 16-byte aligned) from
 // global memory into shared memory; completion is counted on `bar`.
 __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)

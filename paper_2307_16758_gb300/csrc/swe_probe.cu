@@ -7,6 +7,7 @@
 
 #include <string>
 
+#include "swe_async.cuh"
 #include "swe_dev.h"
 
 void swe_set_error(const std::string &msg);
@@ -74,7 +75,51 @@ template <typename T> int fma_peak(int iters, cudaStream_t s, double *flops_per_
     return SWE_OK;
 }
 
+// The bounded wait of the tile step's pipeline (mbar_wait) on an mbarrier
+// whose phase completes only if `arrive` is set: with arrive = 0 nothing ever
+// completes it, the wait must give up after `polls` polls, and the kernel
+// reports that and returns like the tile step does.  Every thread of the
+// block waits, as in the pipeline.
+__global__ void k_wait_probe(uint32_t polls, int arrive, int *timed_out)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        swe_dev::mbar_init(&bar);
+        swe_dev::mbar_init_fence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && arrive) swe_dev::mbar_arrive(&bar);
+    const bool ok = __syncthreads_and(swe_dev::mbar_wait(&bar, 0, polls));
+    if (threadIdx.x == 0) *timed_out = ok ? 0 : 1;
+}
+
 }  // namespace
+
+extern "C" int swe_probe_bounded_wait(uint32_t polls, int arrive, int *timed_out, void *stream)
+{
+    if (!timed_out || polls == 0 || polls > (1u << 22)) {
+        swe_set_error("swe_probe_bounded_wait: bad argument");
+        return SWE_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    int *d = (int *)dev_alloc(sizeof(int), s);
+    if (!d) { swe_set_error("device allocation failed"); return SWE_ERR_NOMEM; }
+    int h = -1;
+    cudaError_t e = cudaMemsetAsync(d, 0xff, sizeof(int), s);
+    if (e == cudaSuccess) {
+        k_wait_probe<<<1, 128, 0, s>>>(polls, arrive ? 1 : 0, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    dev_free(d, s);
+    if (e != cudaSuccess) {
+        swe_set_error(std::string("swe_probe_bounded_wait: ") + cudaGetErrorString(e));
+        return SWE_ERR_CUDA;
+    }
+    *timed_out = h;
+    return SWE_OK;
+}
 
 extern "C" int swe_fma_peak(int precision, int iters, void *stream, double *flops_per_s)
 {

@@ -42,7 +42,7 @@ EXPORTED = [
     "swe_ensemble_sync", "swe_profile_begin", "swe_profile_end", "swe_dt_history",
     "swe_muscl_step_noalloc", "swe_autotune", "swe_ensemble_autotune",
     "swe_partition_create", "swe_partition_destroy", "swe_partition_info", "swe_partition_export",
-    "swe_set_partition", "swe_halo_get", "swe_fma_peak",
+    "swe_set_partition", "swe_halo_get", "swe_fma_peak", "swe_probe_bounded_wait",
 ]
 NOALLOC_MAX_CELLS = 262144
 KERNEL_KINDS = ["prep", "flux", "heun_avg", "smax", "fused", "ensemble", "k6", "k7"]
@@ -118,6 +118,7 @@ def load_library(path: str = LIB_PATH, use_torch_allocator: bool = True):
     lib.swe_set_partition.argtypes = [vp, vp]
     lib.swe_halo_get.argtypes = [vp, i32, vp, vp, vp]
     lib.swe_fma_peak.argtypes = [i32, i32, vp, C.POINTER(dp)]
+    lib.swe_probe_bounded_wait.argtypes = [C.c_uint32, i32, C.POINTER(i32), vp]
     if use_torch_allocator:
         import torch
 
@@ -381,6 +382,13 @@ def swe_halo_get(s, part, n):
     h, hu, hv = np.empty(max(n, 1)), np.empty(max(n, 1)), np.empty(max(n, 1))
     _check(load_library().swe_halo_get(s, int(part), _p(h), _p(hu), _p(hv)))
     return h[:n], hu[:n], hv[:n]
+
+
+def swe_probe_bounded_wait(polls, arrive, stream=None):
+    """Run the bounded-wait self-check; True if the wait gave up (see include/swe.h)."""
+    out = C.c_int(-1)
+    _check(load_library().swe_probe_bounded_wait(int(polls), int(arrive), C.byref(out), stream))
+    return out.value == 1
 
 
 def swe_fma_peak(precision="fp32", iters=None, stream=None):

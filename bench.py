@@ -23,6 +23,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import math
 import os
@@ -131,9 +132,14 @@ KERNEL_SOURCES = ("paper_2307_16758_gb300/csrc/swe_kernels.cu", "paper_2307_1675
 
 
 def kernel_source_sha() -> str:
+    """Hash of the kernel sources' code: comments and blank space do not count, so that
+    stored counters outlive edits of the prose around the code."""
     h = hashlib.sha256()
     for p in KERNEL_SOURCES:
-        h.update(open(os.path.join(ROOT, p), "rb").read())
+        text = open(os.path.join(ROOT, p), encoding="utf-8").read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -65,8 +65,9 @@ __global__ void k_prep_waf(StepArgs<T> a, Vec4<T> *P, Vec4<T> *U)
 // 13M river the LSQ MUSCL flux kernel runs 0.281 ms at 32 (about 90 bytes of
 // spills), 0.303 at 40, 0.326 at 48 (none); HLLC 0.238, 0.257, 0.290; with
 // the second-order hydrostatic reconstruction 0.283 at 32, 0.297 at 40.  WAF
-// keeps 48 (0.512 ms; 0.530 at 40; uncapped, 72 registers, 0.606).  The
-// FP64 instances are bound by the FP64 units and left to the compiler.
+// keeps 48: its limiter state spills (0.394 ms at 48, 0.454 at 40, 0.493 at
+// 32).  The FP64 instances are bound by the FP64 units and left to the
+// compiler.
 template <typename T, int SCHEME> constexpr int flux_maxnreg()
 {
     return sizeof(T) != 4 ? 255 : (SCHEME == SWE_SCHEME_WAF ? 48 : 32);

@@ -84,3 +84,27 @@ def test_roofline_uses_the_survey_bytes_per_cell_update():
     assert r["kernel"]["name"] == "k_flux" and abs(r["kernel"]["ms"] - 0.3) < 1e-12
     assert abs(r["kernel"]["achieved"] - 92 * 1e6 / 0.3e-3 / 1e9) < 1e-9
     assert r["own_bytes"]["flux"]["bytes_per_cell"] == 116 and r["own_bytes"]["prep"]["bytes_per_cell"] == 100
+
+
+def test_own_bytes_follow_the_wet_fraction_and_the_source_hash_ignores_comments(tmp_path, monkeypatch):
+    """A dry cell stores and reads no face values: the split MUSCL kernels' own bytes are the mix
+    at the state's wet fraction (prep 100 B wet / 8 B dry, flux 116 / 68 in FP32); and the hash
+    that keys stored ncu counters changes with the kernel code, not with its comments."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.algo_bytes("prep", "muscl", "fp32", 0.5) == 54 and bench.algo_bytes("flux", "muscl", "fp32", 0.5) == 92
+    assert bench.algo_bytes("prep", "muscl", "fp32") == 100 and bench.algo_bytes("flux", "muscl", "fp32", 0.0) == 68
+    prof = {"prep": (2.0, 10), "flux": (3.0, 10)}
+    r = bench.roofline_entry("muscl", 1_000_000, 0.5, prof, "split", 5000.0, "measured", 123.0, wet=0.5)
+    assert r["own_bytes"]["prep"]["bytes_per_cell"] == 54 and r["own_bytes"]["wet_fraction"] == 0.5
+    assert r["traffic"] == 123.0 and "traffic_source" in r
+    src = tmp_path / "k.cu"
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "KERNEL_SOURCES", ("k.cu",))
+    src.write_text("int f() { return 1; }  // one\n")
+    a = bench.kernel_source_sha()
+    src.write_text("/* prose */\nint f()  {\n  return 1;   // another comment\n}\n")
+    assert bench.kernel_source_sha() == a
+    src.write_text("int f() { return 2; }\n")
+    assert bench.kernel_source_sha() != a

@@ -77,7 +77,7 @@ def step_bytes_ideal(scheme: str, precision: str) -> int:
     return algo_bytes("fused" if scheme != "hllc" else "flux", scheme, precision)
 
 
-def survey_bytes(scheme: str, precision: str) -> int:
+def roofline_bytes(scheme: str, precision: str) -> int:
     """Algorithmic bytes per cell-update of the roofline: every array element touched once per step,
     neighbour gathers assumed to hit in cache, LSQ centroid offsets counted as stored (24 B in FP32):
     FP32 MUSCL / WAF 92 B (state read and written 24, bed and Manning n 8, neighbour words 12, scaled
@@ -93,11 +93,11 @@ KERNEL_NAMES = {("fused", "fused"): "k_tile", ("split", "flux"): "k_flux", ("spl
 
 def roofline_entry(scheme, n, step_ms, prof, kname, peak, peak_src, traffic, wet=1.0):
     """The contract's roofline object: the whole step and its dominant kernel against the measured HBM
-    copy rate, each with the algorithmic bytes of survey_bytes() per cell-update (frac is the step's;
+    copy rate, each with the algorithmic bytes of roofline_bytes() per cell-update (frac is the step's;
     with the one-pass tile step the step is one launch of the dominant kernel); each kernel's own
     bytes (what it reads and writes, face-value scratch included, at the state's wet fraction) under
     own_bytes; traffic is the dominant kernel's DRAM bytes per launch from the stored ncu counters."""
-    per_cell = survey_bytes(scheme, "fp32")
+    per_cell = roofline_bytes(scheme, "fp32")
     dom = max(prof, key=lambda k: prof[k][0])
     dom_ms = prof[dom][0] / prof[dom][1]
     step_ach = per_cell * n / (step_ms / 1e3) / 1e9
@@ -673,7 +673,7 @@ def ensemble_study(args, swe, torch):
     for m in meshes:
         m.close()
     peak, src = measured_peaks()
-    per_cell = survey_bytes("muscl", "fp32")
+    per_cell = roofline_bytes("muscl", "fp32")
     ach = per_cell * n / (ms_batched / 1e3) / 1e9
     e = np.array(errs)
     return {
@@ -754,7 +754,7 @@ def river4m_study(args, swe, torch):
         h32, hu32, hv32 = s32.get_state()
         mass32 = s32.mass()
         s32.close()
-        per_cell = survey_bytes(scheme, "fp32")
+        per_cell = roofline_bytes(scheme, "fp32")
         ach = per_cell * n / (ms / 1e3) / 1e9
         speed = lambda hh, qx, qy: float(np.where(hh > 1e-3, np.hypot(qx, qy) / np.maximum(hh, 1e-300), 0.0).max())
         err = state_error(w, h32, hu32, hv32, h64, hu64, hv64)

@@ -69,15 +69,15 @@ def test_single_process_needs_no_group():
     assert ms == 2.0 and value == pytest.approx(500 * 4 / 2e-3)
 
 
-def test_roofline_uses_the_survey_bytes_per_cell_update():
+def test_roofline_uses_the_roofline_bytes_per_cell_update():
     """Host arithmetic of the bench's roofline: algorithmic bytes per cell-update are 92 (FP32 MUSCL
     and WAF), 68 (FP32 first-order HLLC), 172 and 124 in FP64; the line's frac is the whole step at
     those bytes over the measured copy rate, and the dominant kernel is reported by the same count."""
     import sys
     sys.path.insert(0, ROOT)
     import bench
-    assert [bench.survey_bytes(s, "fp32") for s in ("muscl", "waf", "hllc")] == [92, 92, 68]
-    assert [bench.survey_bytes(s, "fp64") for s in ("muscl", "hllc")] == [172, 124]
+    assert [bench.roofline_bytes(s, "fp32") for s in ("muscl", "waf", "hllc")] == [92, 92, 68]
+    assert [bench.roofline_bytes(s, "fp64") for s in ("muscl", "hllc")] == [172, 124]
     prof = {"prep": (0.2 * 10, 10), "flux": (0.3 * 10, 10)}        # (total ms, launches)
     r = bench.roofline_entry("muscl", 1_000_000, 0.5, prof, "split", 5000.0, "measured", None)
     assert abs(r["achieved"] - 92 * 1e6 / 0.5e-3 / 1e9) < 1e-9 and abs(r["frac"] - r["achieved"] / 5000.0) < 1e-12

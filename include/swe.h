@@ -62,8 +62,9 @@ enum { SWE_EULER = 0, SWE_HEUN = 1 };
  * paper's choice), phi = 1 (no limiting), phi = 0 (the HLLC flux), and two
  * other classical limiters: MINBEE phi = max(0, min(1, r)) and van Leer
  * phi = (r + |r|)/(1 + |r|).  Whatever the limiter, an edge whose Riemann
- * problem has no wet star region (a dry side, or two rarefactions that open
- * a dry gap: u_R - u_L >= 2(a_L + a_R)) takes A = 1, its HLLC flux. */
+ * problem has no wet star region (a dry side: a dry cell or a dry
+ * reconstructed depth; or two rarefactions that open a dry gap:
+ * u_R - u_L >= 2(a_L + a_R)) takes A = 1, its HLLC flux. */
 enum { SWE_WAF_SUPERBEE = 0, SWE_WAF_PHI1 = 1, SWE_WAF_PHI0 = 2, SWE_WAF_MINBEE = 3, SWE_WAF_VANLEER = 4 };
 /* Quantity of the WAF ratios r_L, r_R (Sec. 6.2.2 takes the depth of the
  * Riemann problem): SURFACE (default) the free surface eta = h + z, whose

@@ -87,7 +87,9 @@
  *      reacts to the bathymetry, and on the river workload WAF-SUPERBEE grows
  *      spurious speeds next to the inflow until it blows up (R14).
  *  R18 WAF weights need a wet star region between S_L and S_R.  Where the
- *      Riemann problem has none -- a dry side (h* <= h_eps), or two
+ *      Riemann problem has none -- a dry side (a cell with h <= h_eps, or a
+ *      reconstructed depth h* <= h_eps; with first-order faces h* <= h, so
+ *      the cell test only settles rounding at the threshold), or two
  *      rarefactions that open a dry gap (u_R - u_L >= 2(a_L + a_R), the
  *      vacuum condition) -- the paper's weights are undefined and the edge
  *      takes A = 1 for all three waves, i.e. its HLLC flux.  Without this the
@@ -522,8 +524,10 @@ static void edge_flux(const om_opts *o, int scheme, const double *in, const doub
             double AL = waf_A(o->waf_limiter, rL, cL);
             double AR = waf_A(o->waf_limiter, rR, cR);
             double As = waf_A(o->waf_limiter, rs, cs);
-            /* R18: no wet star region (a dry side, or the vacuum condition) */
-            if (hsL <= h_eps || hsR <= h_eps || uR - uL >= 2.0 * (sqrt(g * hsL) + sqrt(g * hsR))) {
+            /* R18: no wet star region (a dry side: a dry cell or a dry reconstructed
+             * depth; or the vacuum condition) */
+            if (hsL <= h_eps || hsR <= h_eps || hcL <= h_eps || hcR <= h_eps ||
+                uR - uL >= 2.0 * (sqrt(g * hsL) + sqrt(g * hsR))) {
                 AL = 1.0; AR = 1.0; As = 1.0;
             }
             double wL = (1.0 + sgL * AL) / 2.0;

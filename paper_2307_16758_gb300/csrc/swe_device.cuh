@@ -56,7 +56,8 @@ template <typename T> struct WafIn {
     T dtdx;            // dt / |c_R - c_L|
     T hupL, hupR;      // upwind mean depth of each side
     T vupL, vupR;      // upwind mean tangential velocity of each side
-    T hcL, hcR;        // cell-centre depths
+    T hcL, hcR;        // the ratios' cell values (depth or free surface)
+    bool dry_cell;     // a cell on either side is dry (h <= h_eps)
 };
 
 template <typename T>
@@ -162,9 +163,10 @@ __device__ __forceinline__ Flux<T> riemann(T hsL, T uL, T vL, T hsR, T uR, T vR,
         T rs = waf_ratio(r_eps, Ss >= T(0) ? vL - w.vupL : w.vupR - vR, vL, vR);
         T sgL = cL >= T(0) ? T(1) : T(-1), sgR = cR >= T(0) ? T(1) : T(-1), sgs = cs >= T(0) ? T(1) : T(-1);
         T AL = waf_A(lim, rL, cL), AR = waf_A(lim, rR, cR), As = waf_A(lim, rs, cs);
-        // no wet star region (a dry side, or the vacuum condition): the
-        // weights of Sec. 6.2.2 do not apply, A = 1 gives the HLLC flux
-        if (dryL || dryR || uR - uL >= T(2) * (aL + aR)) { AL = T(1); AR = T(1); As = T(1); }
+        // no wet star region (a dry side: a dry cell or a dry reconstructed
+        // depth; or the vacuum condition): the weights of Sec. 6.2.2 do not
+        // apply, A = 1 gives the HLLC flux
+        if (dryL || dryR || w.dry_cell || uR - uL >= T(2) * (aL + aR)) { AL = T(1); AR = T(1); As = T(1); }
         T wL = (T(1) + sgL * AL) / T(2);
         T wLR = (sgR * AR - sgL * AL) / T(2);
         T wR = (T(1) - sgR * AR) / T(2);
@@ -522,6 +524,7 @@ __device__ __forceinline__ void interior_edge(const StepArgs<T> &a, T dt, const 
         // the ratios' cell values: depth, or free surface (eta = h + z)
         wi.hcL = a.waf_surface ? A.hc + A.zc : A.hc;
         wi.hcR = a.waf_surface ? B.hc + B.zc : B.hc;
+        wi.dry_cell = A.hc <= h_eps || B.hc <= h_eps;
         fl = riemann<T, true>(hsA, unA, vtA, hsB, unB, vtB, g, h_eps, wi, a.waf_limiter, a.r_eps);
     } else {
         WafIn<T> wi{};
@@ -666,8 +669,9 @@ __device__ __forceinline__ CellOut<T> cell_update(const StepArgs<T> &a, T dt, T 
             } else if (SCHEME == SWE_SCHEME_WAF) {
                 const Vec4<T> p = src.nbr_centre(nb[k]);
                 sj.hc = p.x; sj.uf = p.y; sj.vf = p.z; sj.z = p.w; sj.ef = p.x + p.w; sj.zc = p.w;
-                Ui = src.own_up(k);
-                Uj = src.nbr_up(nb[k]);
+                // a dry side's upwind means are not stored (and not needed: R18)
+                if (hi > h_eps) Ui = src.own_up(k);
+                if (p.x > h_eps) Uj = src.nbr_up(nb[k]);
                 dlen = dsqrt(fma_rn(dd[k].x, dd[k].x, mul_rn(dd[k].y, dd[k].y)));
             } else {
                 const Vec4<T> q = src.nbr_state(nb[k]);

@@ -165,6 +165,11 @@ __device__ __forceinline__ void prep_muscl_edge_cell(const StepArgs<T> &a, int i
 template <typename T>
 __device__ __forceinline__ void prep_waf_cell(const StepArgs<T> &a, int i, Vec4<T> *P, Vec4<T> *U)
 {
+    // A dry cell stores nothing: its primitives are (h, 0, 0, z), which the
+    // flux kernel builds from h and z, and its upwind means are never used:
+    // every Riemann problem it takes part in has a dry side, where the WAF
+    // weights are A = 1 whatever the ratios (R18).
+    if (a.h[i] <= a.h_eps) return;
     T hi = a.h[i], ui, vi;
     const T zi = a.m.z[i];
     primitives(hi, a.hu[i], a.hv[i], a.h_eps, ui, vi);
@@ -210,7 +215,15 @@ template <typename T> struct GlobalSrc {
         const T hj = a.h[b.idx];
         return hj <= a.h_eps ? dry_face(hj, a.m.z[b.idx]) : a.F[3 * b.idx + b.kj];
     }
-    __device__ Vec4<T> nbr_centre(const Nb &b) const { return a.F[b.idx]; }
+    // WAF: the neighbour's primitives (h, u, v, z), stored if it is wet
+    __device__ Vec4<T> nbr_centre(const Nb &b) const
+    {
+        const T hj = a.h[b.idx];
+        if (hj > a.h_eps) return a.F[b.idx];
+        Vec4<T> p;
+        p.x = hj; p.y = T(0); p.z = T(0); p.w = a.m.z[b.idx];
+        return p;
+    }
     __device__ Vec4<T> own_up(int k) const { return a.U[3 * i + k]; }
     __device__ Vec4<T> nbr_up(const Nb &b) const { return a.U[3 * b.idx + b.kj]; }
     __device__ Vec4<T> nbr_state(const Nb &b) const

@@ -877,8 +877,8 @@ def test_waf_other_limiters_equal_toro_sum_form(name, phi):
 @pytest.mark.parametrize("limiter", ["superbee", "phi1", "minbee", "vanleer"])
 def test_waf_without_a_wet_star_region_is_hllc(limiter):
     """Reading R18: where the Riemann problem has no wet star region -- two rarefactions that open
-    a dry gap (u_R - u_L >= 2(a_L + a_R)) or a dry side -- every limiter gives the HLLC flux; a
-    problem just short of the vacuum condition keeps the limited weights."""
+    a dry gap (u_R - u_L >= 2(a_L + a_R)), a dry reconstructed depth or a dry cell -- every limiter
+    gives the HLLC flux; a problem just short of the vacuum condition keeps the limited weights."""
     o = oracle.opts("waf", waf_limiter=limiter)
     oh = oracle.opts("hllc")
     rng = np.random.default_rng(5)
@@ -894,6 +894,10 @@ def test_waf_without_a_wet_star_region_is_hllc(limiter):
         assert np.array_equal(oracle.edge_flux(o, vac, waf), oracle.edge_flux(oh, vac))
         dry = _state(hL, uL, vL, 0.0, 0.0, 0.0)
         assert np.array_equal(oracle.edge_flux(o, dry, waf), oracle.edge_flux(oh, dry))
+        # a dry cell (h <= h_eps) whose reconstructed depth rounding left above h_eps
+        celldry = _state(hL, uL, vL, hR, uL + 0.1, vR)
+        celldry[7] = 0.5e-6
+        assert np.array_equal(oracle.edge_flux(o, celldry, waf), oracle.edge_flux(oh, celldry))
     # short of the vacuum condition, a state whose ratios are not zero keeps the WAF weights
     hL = hR = 1.0
     wet = _state(hL, -2.0, 0.3, 1.2, 2.0, -0.4)

@@ -50,8 +50,9 @@ template <typename T> struct StepArgs {
     DevMesh<T> m;
     const T *h, *hu, *hv;       // state in
     T *ho, *huo, *hvo;          // state out
-    const Vec4<T> *F;           // MUSCL: face values [3n] (eta, u, v, z); WAF: centre values [n] (h, u, v, z)
-    const Vec4<T> *U;           // WAF: upwind means [3n] (h, u, v, -)
+    const Vec4<T> *F;           // MUSCL: face values [3n] (eta, u, v, z); WAF: centre values [n] (h, u, v, z);
+                                //   written for wet cells only (a dry cell's are built from its h and z)
+    const Vec4<T> *U;           // WAF: upwind means [3n] (h or eta, u, v, -), wet cells only
     DevScalars *sc;
     const double *dtv;          // replayed time step (NULL: CFL rule)
     double *dt_hist;            // ring of the last SWE_DT_HISTORY time steps

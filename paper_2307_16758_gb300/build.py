@@ -57,7 +57,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     nvcc = _nvcc()
     os.makedirs(OBJ, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h") or f.endswith(".cuh")]
-    headers.append(os.path.join(INCLUDE, "swe.h"))
+    headers += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
     jobs, objs = [], []
     for src, extra in SOURCES:
         path = os.path.join(CSRC, src)

@@ -18,6 +18,7 @@
 #include "swe_mesh.h"
 #include "swe_partition.h"
 #include "swe_tiles.h"
+#include "../../include/swe_tile_plan.h"
 
 int swe_mesh_build_host(const double *xy, int64_t n_nodes, const int32_t *tri, int64_t n,
                         const int32_t *bnd, const int32_t *bnd_tag, int64_t n_bnd,
@@ -52,6 +53,14 @@ void dev_free(void *p, cudaStream_t s)
 }
 
 namespace {
+
+// Message for a non-zero return of swe_build_tile_plan.
+std::string tile_plan_error(int rc)
+{
+    if (rc == -1) return "the tile size must be a power of two within 32 .. 1024";
+    if (rc == -2) return "a tile and its halo exceed the plan's 2047 slots: renumber the mesh (Morton or RCM) or take a smaller tile";
+    return "the tile plan exceeds 2^31 words";
+}
 
 #define CK(call)                                                                  \
     do {                                                                          \
@@ -225,7 +234,7 @@ template <typename T> struct StateT {
         if (want_fused) {
             if (!m || m->n != n) { swe_set_error("the tile step needs the state's mesh"); return SWE_ERR_ARG; }
             TilePlan tp;
-            if (swe_build_tile_plan(*m, block, tp) != 0) { swe_set_error("unsupported tile size"); return SWE_ERR_ARG; }
+            if (const int rc = swe_build_tile_plan(*m, block, tp)) { swe_set_error(tile_plan_error(rc)); return SWE_ERR_ARG; }
             TileArgs t{};
             t.tile = block;
             t.n_tiles = tp.n_tiles;
@@ -1413,5 +1422,42 @@ int swe_halo_get(swe_state *s, int part, double *h, double *hu, double *hv)
     if (!s) { swe_set_error("swe_halo_get: bad argument"); return SWE_ERR_ARG; }
     return DISPATCH(s, S.halo_get(part, h, hu, hv));
 }
+
+// ---- the tile step's plan, host side ---------------------------------------
+
+int swe_tile_plan_info(const swe_mesh *m, int tile, int64_t *n_tiles, int32_t *hmax, int32_t *h1max,
+                       int32_t *wmax, int64_t *n_words)
+{
+    if (!m) { swe_set_error("swe_tile_plan_info: bad argument"); return SWE_ERR_ARG; }
+    TilePlan tp;
+    try {
+        if (const int rc = swe_build_tile_plan(*m, tile, tp)) { swe_set_error(tile_plan_error(rc)); return SWE_ERR_ARG; }
+    } catch (const std::bad_alloc &) {
+        swe_set_error("host allocation failed");
+        return SWE_ERR_NOMEM;
+    }
+    if (n_tiles) *n_tiles = tp.n_tiles;
+    if (hmax) *hmax = tp.hmax;
+    if (h1max) *h1max = tp.h1max;
+    if (wmax) *wmax = tp.wmax;
+    if (n_words) *n_words = (int64_t)tp.words.size();
+    return SWE_OK;
+}
+
+int swe_tile_plan_export(const swe_mesh *m, int tile, int32_t *hdr, int32_t *words)
+{
+    if (!m) { swe_set_error("swe_tile_plan_export: bad argument"); return SWE_ERR_ARG; }
+    TilePlan tp;
+    try {
+        if (const int rc = swe_build_tile_plan(*m, tile, tp)) { swe_set_error(tile_plan_error(rc)); return SWE_ERR_ARG; }
+    } catch (const std::bad_alloc &) {
+        swe_set_error("host allocation failed");
+        return SWE_ERR_NOMEM;
+    }
+    if (hdr) std::copy(tp.hdr.begin(), tp.hdr.end(), hdr);
+    if (words) std::copy(tp.words.begin(), tp.words.end(), words);
+    return SWE_OK;
+}
+
 
 }  // extern "C"

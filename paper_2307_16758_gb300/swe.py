@@ -43,6 +43,7 @@ EXPORTED = [
     "swe_muscl_step_noalloc", "swe_autotune", "swe_ensemble_autotune",
     "swe_partition_create", "swe_partition_destroy", "swe_partition_info", "swe_partition_export",
     "swe_set_partition", "swe_halo_get", "swe_fma_peak", "swe_probe_bounded_wait",
+    "swe_tile_plan_info", "swe_tile_plan_export",
 ]
 NOALLOC_MAX_CELLS = 262144
 KERNEL_KINDS = ["prep", "flux", "heun_avg", "smax", "fused", "ensemble", "k6", "k7"]
@@ -119,6 +120,9 @@ def load_library(path: str = LIB_PATH, use_torch_allocator: bool = True):
     lib.swe_halo_get.argtypes = [vp, i32, vp, vp, vp]
     lib.swe_fma_peak.argtypes = [i32, i32, vp, C.POINTER(dp)]
     lib.swe_probe_bounded_wait.argtypes = [C.c_uint32, i32, C.POINTER(i32), vp]
+    lib.swe_tile_plan_info.argtypes = [vp, i32, C.POINTER(i64), C.POINTER(i32), C.POINTER(i32),
+                                       C.POINTER(i32), C.POINTER(i64)]
+    lib.swe_tile_plan_export.argtypes = [vp, i32, vp, vp]
     if use_torch_allocator:
         import torch
 
@@ -372,6 +376,23 @@ def swe_partition_export(p, part):
     h1, h2, b = (np.empty(max(k, 1), np.int32) for k in (n1, n2, nb))
     _check(load_library().swe_partition_export(p, int(part), _p(h1), _p(h2), _p(b)))
     return h1[:n1], h2[:n2], b[:nb]
+
+
+def swe_tile_plan_info(m, tile):
+    nt, nw = C.c_int64(), C.c_int64()
+    hm, h1, wm = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(load_library().swe_tile_plan_info(m, int(tile), C.byref(nt), C.byref(hm), C.byref(h1), C.byref(wm),
+                                             C.byref(nw)))
+    return {"n_tiles": nt.value, "hmax": hm.value, "h1max": h1.value, "wmax": wm.value, "n_words": nw.value}
+
+
+def swe_tile_plan_export(m, tile):
+    """The tile step's plan of mesh handle m: (info dict, hdr[n_tiles, 8], words)."""
+    info = swe_tile_plan_info(m, tile)
+    hdr = np.empty(max(8 * info["n_tiles"], 1), np.int32)
+    words = np.empty(max(info["n_words"], 1), np.int32)
+    _check(load_library().swe_tile_plan_export(m, int(tile), _p(hdr), _p(words)))
+    return info, hdr[:8 * info["n_tiles"]].reshape(-1, 8), words[:info["n_words"]]
 
 
 def swe_set_partition(s, p):

@@ -27,7 +27,8 @@ def lib():
 
 
 def _declared():
-    txt = open(os.path.join(ROOT, "include", "swe.h")).read()
+    inc = os.path.join(ROOT, "include")
+    txt = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc)) if f.endswith(".h"))
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
     names = set(re.findall(r"\b(swe_[a-z_]+)\s*\(", txt))
     return sorted(n for n in names if not n.endswith("_fn"))

@@ -15,9 +15,9 @@ namespace {
 using namespace swe_dev;
 
 // Register caps as for the single-mesh kernels (swe_kernels.cu): FP32 MUSCL
-// prep at 40 and every FP32 flux kernel at 48 registers.  SCHEME FLUX_MUSCL_HR2 is the LSQ
-// MUSCL scheme with the second-order hydrostatic reconstruction (its prep
-// reconstructs h as well: 48 registers).
+// prep at 40, the FP32 flux kernels at 32 (WAF at 48).  SCHEME
+// FLUX_MUSCL_HR2 is the LSQ MUSCL scheme with the second-order hydrostatic
+// reconstruction (its prep reconstructs h as well: 48 registers).
 template <typename T, int SCHEME>
 __global__ void __maxnreg__((sizeof(T) != 4 ? 255 : SCHEME == SWE_SCHEME_MUSCL ? 40 : SCHEME == FLUX_MUSCL_HR2 ? 48 : 255))
     k_prep_ens(const EnsEntry<T> *__restrict__ tab, const int2 *__restrict__ blk, int phase)

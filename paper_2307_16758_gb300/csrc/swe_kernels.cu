@@ -35,8 +35,8 @@ using namespace swe_dev;
 // Barth-Jespersen limiting at the three edge midpoints.  Zero gradient if the
 // cell or a neighbour is dry or the 2x2 system is singular.  NQ = 4 also
 // reconstructs h (second-order hydrostatic reconstruction).  FP32 register
-// caps: 40 (six 256-thread blocks per SM) and 48 for NQ = 4 (five blocks;
-// at 54 uncapped registers it ran four).
+// caps: 40 (twelve of the default 128-thread blocks per SM) and 48 for
+// NQ = 4 (ten).
 template <typename T, int NQ = 3>
 __global__ void __maxnreg__((sizeof(T) == 4 ? (NQ == 3 ? 40 : 48) : 255)) k_prep_muscl(StepArgs<T> a, Vec4<T> *F)
 {

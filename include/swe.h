@@ -341,8 +341,9 @@ int swe_halo_get(swe_state *s, int part, double *h, double *hu, double *hv);
  * scenarios; cf. the paper's one-sub-domain-per-GPU layout, Sec. 6.4).
  * Members must share precision, scheme, hr_order, Euler time stepping, kernel, block,
  * stream and step phase (steps taken mod 6; freshly initialised states do).
- * Members stay owned by the caller, must outlive the ensemble, and can be
- * queried (swe_get_state, swe_mass, swe_time) as usual. */
+ * Each state may appear once (SWE_ERR_ARG otherwise).  Members stay owned by
+ * the caller, must outlive the ensemble, and can be queried (swe_get_state,
+ * swe_mass, swe_time) as usual. */
 int swe_ensemble_create(swe_state *const *members, int n_members, swe_ensemble **out);
 int swe_ensemble_destroy(swe_ensemble *e);
 /* Advance every member n_steps explicit steps, each with its own CFL time

@@ -1293,6 +1293,15 @@ int swe_ensemble_create(swe_state *const *members, int n_members, swe_ensemble *
             swe_set_error("swe_ensemble_create: members must exist and share the precision");
             return SWE_ERR_ARG;
         }
+    {
+        // a state listed twice would be stepped twice per step, both times from the same old state
+        std::vector<const swe_state *> seen(members, members + n_members);
+        std::sort(seen.begin(), seen.end());
+        if (std::adjacent_find(seen.begin(), seen.end()) != seen.end()) {
+            swe_set_error("swe_ensemble_create: a state is listed more than once");
+            return SWE_ERR_ARG;
+        }
+    }
     auto *e = new swe_ensemble();
     e->precision = members[0]->precision;
     auto fill = [&](auto &E, auto getter) -> int {

@@ -97,6 +97,9 @@ def test_ensemble_rejects_mixed_members():
     c.step(1, 0.9)                    # another step phase
     with pytest.raises(swe.SweError):
         swe.Ensemble([a, c])
+    with pytest.raises(swe.SweError) as e:
+        swe.Ensemble([a, a])          # one state listed twice
+    assert e.value.code == -1
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])

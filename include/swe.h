@@ -124,7 +124,10 @@ int swe_params_default(swe_params *p, int scheme, int precision);
 
 /* Device memory: by default cudaMalloc/cudaFree.  A host program (for example
  * the Python binding, which routes to PyTorch's caching allocator) may install
- * its own pair; ctx is passed back unchanged.  Global to the library. */
+ * its own pair (both or neither; NULL, NULL restores the default); ctx is
+ * passed back unchanged.  Global to the library.  Every block goes back to
+ * the allocator that gave it out, so the pair may be replaced while states
+ * exist; the old pair must stay callable until their memory is freed. */
 typedef void *(*swe_alloc_fn)(size_t bytes, void *stream, void *ctx);
 typedef void (*swe_free_fn)(void *ptr, void *stream, void *ctx);
 int swe_set_allocator(swe_alloc_fn alloc, swe_free_fn free_fn, void *ctx);

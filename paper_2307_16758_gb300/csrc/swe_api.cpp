@@ -8,9 +8,11 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <tuple>
 #include <type_traits>
+#include <unordered_map>
 #include <vector>
 
 #include "swe_dev.h"
@@ -28,9 +30,13 @@ static thread_local std::string g_err;
 void swe_set_error(const std::string &msg) { g_err = msg; }
 
 namespace {
+std::mutex g_alloc_mu;
 swe_alloc_fn g_alloc = nullptr;
 swe_free_fn g_free = nullptr;
 void *g_ctx = nullptr;
+// Blocks that came from an installed allocator, with the free function and
+// context to return them to (the pair may have been replaced since).
+std::unordered_map<void *, std::pair<swe_free_fn, void *>> g_owner;
 }  // namespace
 
 // Device memory through the allocator installed by swe_set_allocator, else
@@ -39,16 +45,41 @@ void *dev_alloc(size_t bytes, cudaStream_t s)
 {
     if (bytes == 0) bytes = 16;
     bytes = (bytes + 255) & ~size_t(255);
-    if (g_alloc) return g_alloc(bytes, (void *)s, g_ctx);
+    swe_alloc_fn alloc;
+    swe_free_fn free_fn;
+    void *ctx;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        alloc = g_alloc; free_fn = g_free; ctx = g_ctx;
+    }
+    if (alloc) {
+        void *p = alloc(bytes, (void *)s, ctx);
+        if (p) {
+            std::lock_guard<std::mutex> lk(g_alloc_mu);
+            g_owner[p] = {free_fn, ctx};
+        }
+        return p;
+    }
     void *p = nullptr;
     if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
     return p;
 }
 
+// Returns a block to whichever allocator gave it out.
 void dev_free(void *p, cudaStream_t s)
 {
     if (!p) return;
-    if (g_free) g_free(p, (void *)s, g_ctx);
+    swe_free_fn free_fn = nullptr;
+    void *ctx = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        auto it = g_owner.find(p);
+        if (it != g_owner.end()) {
+            free_fn = it->second.first; ctx = it->second.second;
+            g_owner.erase(it);
+        }
+    }
+    if (free_fn) free_fn(p, (void *)s, ctx);
     else cudaFree(p);
 }
 
@@ -993,6 +1024,7 @@ int swe_set_allocator(swe_alloc_fn alloc, swe_free_fn free_fn, void *ctx)
         swe_set_error("swe_set_allocator: give both functions or neither");
         return SWE_ERR_ARG;
     }
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
     g_alloc = alloc; g_free = free_fn; g_ctx = ctx;
     return SWE_OK;
 }

@@ -16,12 +16,15 @@ from paper_2307_16758_gb300 import build as B
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-@pytest.mark.skipif(shutil.which("gcc") is None, reason="needs gcc")
-def test_plain_c_program_uses_the_abi(tmp_path):
+@pytest.mark.parametrize("compiler,lang", [("gcc", ["-std=c99"]), ("g++", ["-x", "c++", "-std=c++17"])])
+def test_plain_c_program_uses_the_abi(tmp_path, compiler, lang):
+    """The same program as strict C99 and as C++17 (the headers' extern "C" guards)."""
+    if shutil.which(compiler) is None:
+        pytest.skip(f"needs {compiler}")
     lib = B.build()
     libdir = os.path.dirname(lib)
     exe = str(tmp_path / "c_consumer")
-    cmd = ["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+    cmd = [compiler, *lang, "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
            os.path.join(ROOT, "tests", "c_consumer.c"), "-o", exe, "-L", libdir, "-l:libswe.so",
            "-Wl,-rpath," + libdir]
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -54,7 +54,9 @@ SEED = 20230733
 def algo_bytes(kind: str, scheme: str, precision: str, wet: float = 1.0) -> float:
     """Bytes a kernel itself reads and writes per cell; for the split MUSCL kernels a dry cell
     (h <= h_eps) stores and reads no face values, so their figure is the mix at wet fraction `wet`
-    (prep: wet 100, dry 8 B in FP32; flux: wet 116, dry 68 B)."""
+    (prep: wet 100, dry 8 B in FP32; flux: wet 116, dry 68 B).  The tile step's figure counts the
+    12 B of neighbour words that its plan replaces; the plan itself is 16-18 B per cell on river
+    meshes (swe_tile_plan_info), so the kernel reads about 4-6 B per cell more than this."""
     f = 4 if precision == "fp32" else 8
     nbr = 12
     if scheme in ("muscl", "muscl_edge") and kind == "prep":

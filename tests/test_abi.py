@@ -150,3 +150,39 @@ def test_fma_peak_rejects_bad_arguments_before_any_launch(args):
     with pytest.raises(swe.SweError) as e:
         swe.swe_fma_peak(precision, iters)
     assert e.value.code == -1
+
+
+def _header_constants():
+    """Every enumerator and #define of the public headers, by name."""
+    inc = os.path.join(ROOT, "include")
+    txt = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc)) if f.endswith(".h"))
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    vals = {k: int(v) for k, v in re.findall(r"\b(SWE_[A-Z0-9_]+)\s*=\s*(-?\d+)", txt)}
+    vals.update({k: int(v) for k, v in re.findall(r"#define\s+(SWE_[A-Z0-9_]+)\s+(-?\d+)", txt)})
+    return vals
+
+
+def test_binding_constants_match_the_header():
+    """The binding's name tables carry the header's values (a mismatch would silently select
+    another scheme, limiter or kernel)."""
+    h = _header_constants()
+    for code, name in swe.ERRORS.items():
+        assert h[name] == code, name
+    assert h["SWE_OK"] == swe.SWE_OK
+    tables = {"SWE_REORDER_": swe.REORDER, "SWE_SCHEME_": swe.SCHEME, "SWE_": swe.PRECISION,
+              "SWE_KERNEL_": swe.KERNEL, "SWE_CFL_": swe.CFL_MODE, "SWE_WAF_RATIO_": swe.WAF_RATIO,
+              "SWE_WAF_": swe.WAF_LIMITER}
+    for prefix, table in tables.items():
+        for name, value in table.items():
+            assert h[prefix + name.upper()] == value, (prefix, name)
+    assert h["SWE_EULER"] == swe.TIME_SCHEME["euler"] and h["SWE_HEUN"] == swe.TIME_SCHEME["heun"]
+    assert (h["SWE_WALL"], h["SWE_OPEN"], h["SWE_INFLOW"], h["SWE_LEVEL"]) == (
+        swe.SWE_WALL, swe.SWE_OPEN, swe.SWE_INFLOW, swe.SWE_LEVEL) == (W.WALL, W.OPEN, W.INFLOW, W.LEVEL)
+    assert (h["SWE_FLAG_CLIPPED"], h["SWE_FLAG_NONFINITE"], h["SWE_FLAG_DRY"]) == (
+        swe.FLAG_CLIPPED, swe.FLAG_NONFINITE, swe.FLAG_DRY)
+    assert h["SWE_MAX_GROUPS"] == swe.MAX_GROUPS
+    assert h["SWE_NOALLOC_MAX_CELLS"] == swe.NOALLOC_MAX_CELLS
+    assert h["SWE_K_COUNT"] == len(swe.KERNEL_KINDS)
+    for k, name in enumerate(swe.KERNEL_KINDS):
+        if "SWE_K_" + name.upper() in h:
+            assert h["SWE_K_" + name.upper()] == k, name

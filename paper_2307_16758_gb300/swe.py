@@ -71,6 +71,7 @@ _ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 _FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 _lib = None
 _callbacks = None
+_retired = []
 
 
 def load_library(path: str = LIB_PATH, use_torch_allocator: bool = True):
@@ -165,6 +166,20 @@ def _current_stream():
 
 
 # ---- C-named entry points --------------------------------------------------
+
+def swe_set_allocator(alloc=None, free_fn=None):
+    """Install a device allocator pair: alloc(nbytes, stream, ctx) -> int address or None, and
+    free_fn(ptr, stream, ctx); both None restores cudaMalloc/cudaFree.  Blocks already handed out
+    go back to the pair that gave them.  The callbacks are kept alive here."""
+    global _callbacks
+    lib = load_library()
+    if (alloc is None) != (free_fn is None):
+        raise SweError(-1, "swe_set_allocator: give both functions or neither")
+    pair = (_ALLOC(alloc), _FREE(free_fn)) if alloc is not None else (_ALLOC(), _FREE())
+    _check(lib.swe_set_allocator(pair[0], pair[1], None))
+    _retired.append(_callbacks)          # the old pair may still be called to free its blocks
+    _callbacks = pair
+
 
 def swe_params_default(scheme="muscl", precision="fp32", **over) -> Params:
     lib = load_library()

@@ -186,3 +186,20 @@ def test_binding_constants_match_the_header():
     for k, name in enumerate(swe.KERNEL_KINDS):
         if "SWE_K_" + name.upper() in h:
             assert h["SWE_K_" + name.upper()] == k, name
+
+
+def test_allocator_pair_is_both_or_neither(lib):
+    """swe_set_allocator takes both functions or neither (neither: cudaMalloc/cudaFree); the
+    binding keeps every pair it installed alive.  No device memory is allocated here."""
+    saved = swe._callbacks
+    try:
+        with pytest.raises(swe.SweError) as e:
+            swe.swe_set_allocator(lambda n, s, c: None)
+        assert e.value.code == -1
+        assert lib.swe_set_allocator(swe._ALLOC(lambda n, s, c: None), swe._FREE(), None) == -1
+        swe.swe_set_allocator()
+        assert swe._callbacks is not saved and saved in swe._retired
+    finally:
+        if saved is not None:
+            assert lib.swe_set_allocator(saved[0], saved[1], None) == 0
+        swe._callbacks = saved
